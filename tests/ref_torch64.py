@@ -1,0 +1,97 @@
+"""A second, independently written float64 statement of PVFinder inference, test-only.
+
+Built from PyTorch CPU library routines (F.linear, F.conv1d, F.conv_transpose1d,
+F.max_pool1d, F.softplus, torch.sigmoid) in float64 rather than the oracle's direct
+loops, so that a wiring mistake in one (a transposed weight, a wrong concat order, an
+off-by-one padding) shows up as a disagreement between the two. It follows §2 of the
+paper with the same readings as the oracle. Used only to pin the oracle.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+NBINS = 4000
+
+
+def _t(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float64))
+
+
+def slice_of(z32: np.ndarray) -> np.ndarray:
+    """Slice index from float32 z, float32 round-to-nearest arithmetic; -1 outside."""
+    z32 = np.asarray(z32, dtype=np.float32)
+    with np.errstate(invalid="ignore"):
+        q = (z32 + np.float32(100.0)) / np.float32(10.0)
+        ok = np.isfinite(q) & (q >= 0) & (q < 40)
+    s = np.full(z32.shape, -1, dtype=np.int64)
+    s[ok] = np.floor(q[ok]).astype(np.int64)
+    return s
+
+
+def fc_net(w: dict, x: torch.Tensor) -> torch.Tensor:
+    """x [n, 9] float64 -> [n, 100]."""
+    h = x
+    for i in range(1, 6):
+        W, b = w[f"fc{i}"]
+        h = F.leaky_relu(F.linear(h, _t(W), _t(b)), 0.01)
+    W, b = w["fc6"]
+    return F.softplus(F.linear(h, _t(W), _t(b)), beta=1.0, threshold=20.0)
+
+
+def histogram(w: dict, feats: np.ndarray) -> np.ndarray:
+    """One event's [4000] histogram from float32 features [9, n]."""
+    feats = np.asarray(feats, dtype=np.float32)
+    s = slice_of(feats[2])
+    ok = (s >= 0) & np.all(np.isfinite(feats), axis=0)
+    x = feats[:, ok].astype(np.float64).T.copy()
+    s = s[ok]
+    x[:, 2] = x[:, 2] - (-100.0 + 10.0 * s)
+    out = fc_net(w, _t(x)).numpy() if x.shape[0] else np.zeros((0, 100))
+    hist = np.zeros((40, 100), dtype=np.float64)
+    np.add.at(hist, s, out)
+    return hist.reshape(-1)
+
+
+def unet(w: dict, hist: np.ndarray):
+    """(logit [L], prob [L]) for one event."""
+    def conv(x, name):
+        W, b = w[name]
+        return F.conv1d(x, _t(W), _t(b), padding=2)
+
+    def up(x, name):
+        W, b = w[name]
+        return F.leaky_relu(F.conv_transpose1d(x, _t(W), _t(b), stride=2), 0.01)
+
+    lr = lambda v: F.leaky_relu(v, 0.01)
+    x = _t(hist).reshape(1, 1, -1)
+    e1 = lr(conv(x, "enc1"))
+    e2 = lr(conv(F.max_pool1d(e1, 2), "enc2"))
+    e3 = lr(conv(F.max_pool1d(e2, 2), "enc3"))
+    e4 = lr(conv(F.max_pool1d(e3, 2), "enc4"))
+    d3 = lr(conv(torch.cat([up(e4, "up3"), e3], dim=1), "dec3"))
+    d2 = lr(conv(torch.cat([up(d3, "up2"), e2], dim=1), "dec2"))
+    d1 = lr(conv(torch.cat([up(d2, "up1"), e1], dim=1), "dec1"))
+    f = conv(d1, "final").reshape(-1)
+    return f.numpy(), torch.sigmoid(f).numpy()
+
+
+def peaks(f: np.ndarray, p: np.ndarray, thr: float = 0.01):
+    """Vectorised local-max rule on the logits; returns (bins, z)."""
+    L = f.shape[0]
+    tl = np.log(thr / (1.0 - thr))
+    big = np.full(5, -np.inf)
+    fp = np.concatenate([big, f, big])
+    cand = f > tl
+    for d in range(1, 6):
+        cand &= f > fp[5 - d:5 - d + L]          # left neighbours strictly lower
+        cand &= f >= fp[5 + d:5 + d + L]         # right neighbours not higher
+    bins = np.nonzero(cand)[0]
+    zc = -100.0 + (np.arange(L) + 0.5) * 0.1
+    z = []
+    for i in bins:
+        lo, hi = max(0, i - 3), min(L, i + 4)
+        z.append(np.dot(p[lo:hi], zc[lo:hi]) / p[lo:hi].sum())
+    return bins, np.array(z)

@@ -1,0 +1,380 @@
+"""Pins for the FP64 oracle: each stage checked against something other than itself.
+
+Closed forms, PyTorch/numpy float64 library routines, exact rational arithmetic,
+hand-built cases with hand-derived answers (tests/golden/peaks_handbuilt.json), and
+invariants (permutation invariance of the histogram, translation equivariance of the
+UNet). The cases are chosen so that a dropped term, a wrong sign or index, a
+transposed operand or a swapped concat order fails at least one of them.
+"""
+
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import oracle
+import synth
+from tests import ref_torch64 as ref
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_weights(seed=1, bias_std=0.3, c0=16):
+    return synth.he_weights(seed=seed, bias_std=bias_std, c0=c0)
+
+
+# ----------------------------------------------------------------- slice index
+
+def exact_slice(z32: np.float32):
+    """floor((z + 100) / 10) in exact rational arithmetic (no rounding)."""
+    q = (Fraction(float(z32)) + 100) / 10
+    return math.floor(q)
+
+
+def test_slice_index_hand_cases():
+    # slice s covers [-100 + 10 s, -90 + 10 s): boundaries belong to the upper slice
+    cases = {-100.0: 0, -90.0: 1, -60.0: 4, 0.0: 10, 289.99: 38, 290.0: 39,
+             299.99998: 39, 300.0: -1, -100.00001: -1, 1e30: -1, -1e30: -1,
+             float("nan"): -1, float("inf"): -1, float("-inf"): -1}
+    for z, s in cases.items():
+        assert oracle.slice_index(z)[0] == s, z
+
+
+def test_slice_index_matches_exact_floor_away_from_edges():
+    rng = np.random.default_rng(5)
+    z = rng.uniform(-100, 300, 20000).astype(np.float32)
+    got = oracle.slice_index(z)
+    for zi, si in zip(z, got):
+        e = exact_slice(zi)
+        # float32 rounding may only move a track that sits within a few ulps of an edge
+        edge = -100 + 10 * round((float(zi) + 100) / 10)
+        if abs(float(zi) - edge) > 1e-4:
+            assert si == e, (zi, si, e)
+
+
+def test_slice_index_one_ulp_around_edges():
+    for s_edge in range(1, 40):
+        z_edge = np.float32(-100 + 10 * s_edge)
+        below = np.nextafter(z_edge, np.float32(-1e9))
+        above = np.nextafter(z_edge, np.float32(1e9))
+        assert oracle.slice_index(z_edge)[0] == s_edge
+        assert oracle.slice_index(above)[0] == s_edge
+        # one ulp below the edge: the exact quotient is below s_edge; float32 rounding of
+        # (z + 100) / 10 may round up to s_edge, never to anything else
+        assert oracle.slice_index(below)[0] in (s_edge - 1, s_edge)
+
+
+# ----------------------------------------------------------------- FC network
+
+def test_fc_matches_torch_float64():
+    w = rand_weights(3, 0.2)
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        x = rng.normal(0, 2, 9)
+        got = oracle.fc_track(w, x)
+        want = ref.fc_net(w, torch.as_tensor(x).reshape(1, 9)).numpy()[0]
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def test_fc_zero_weights_closed_form():
+    w = rand_weights(3, 0.0)
+    b6 = np.linspace(-30, 30, 100).astype(np.float32)
+    w = {k: (np.zeros_like(W), np.zeros_like(b)) for k, (W, b) in w.items()}
+    w["fc6"] = (w["fc6"][0], b6)
+    got = oracle.fc_track(w, np.ones(9))
+    # softplus(b) = log(1 + e^b) via numpy's logaddexp(0, b); above 20 the oracle returns b
+    want = np.where(b6 > 20, b6.astype(np.float64), np.logaddexp(0.0, b6.astype(np.float64)))
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=0)
+    assert np.max(np.abs(want - np.logaddexp(0.0, b6.astype(np.float64)))) < 3e-9
+
+
+def test_fc_leaky_slope_single_path():
+    # one unit carries x0 through five LeakyReLUs into every output: x0 = -2 gives
+    # -2 * 0.01^5 before the softplus
+    shapes = synth.layer_shapes()
+    w = {k: (np.zeros(s[0], np.float32), np.zeros(s[1], np.float32)) for k, s in shapes.items()}
+    for name in ("fc1", "fc2", "fc3", "fc4", "fc5"):
+        w[name][0][0, 0] = 1.0
+    w["fc6"][0][:, 0] = 1.0
+    x = np.zeros(9)
+    x[0] = -2.0
+    got = oracle.fc_track(w, x)
+    np.testing.assert_allclose(got, np.logaddexp(0.0, -2.0 * 0.01 ** 5), rtol=1e-15)
+    x[0] = 3.0
+    np.testing.assert_allclose(oracle.fc_track(w, x), np.logaddexp(0.0, 3.0), rtol=1e-15)
+
+
+# ----------------------------------------------------------------- histogram
+
+def test_histogram_closed_form_constant_fc():
+    shapes = synth.layer_shapes()
+    w = {k: (np.zeros(s[0], np.float32), np.zeros(s[1], np.float32)) for k, s in shapes.items()}
+    b6 = np.linspace(-3, 3, 100).astype(np.float32)
+    w["fc6"] = (w["fc6"][0], b6)
+    ev = synth.generate_standard(3, 11)
+    feats = ev.features[:, ev.offsets[1]:ev.offsets[2]]
+    hist, dropped = oracle.event_histogram(w, feats)
+    counts = np.zeros(40)
+    for z in feats[2]:
+        counts[exact_slice(z)] += 1   # generated z are never within ulps of an edge
+    want = (counts[:, None] * np.logaddexp(0.0, b6.astype(np.float64))[None, :]).reshape(-1)
+    np.testing.assert_allclose(hist, want, rtol=1e-13, atol=0)
+    assert dropped == 0
+
+
+def test_histogram_matches_torch_and_is_permutation_invariant():
+    w = rand_weights(4, 0.1)
+    ev = synth.generate_standard(4, 12)
+    for e in range(4):
+        feats = ev.features[:, ev.offsets[e]:ev.offsets[e + 1]]
+        hist, _ = oracle.event_histogram(w, feats)
+        np.testing.assert_allclose(hist, ref.histogram(w, feats), rtol=1e-12, atol=1e-12)
+        perm = np.random.default_rng(e).permutation(feats.shape[1])
+        hist2, _ = oracle.event_histogram(w, feats[:, perm])
+        np.testing.assert_allclose(hist2, hist, rtol=1e-12, atol=1e-12)
+
+
+def test_histogram_slice_relative_z_feature():
+    # two tracks with the same position inside different slices give the same 100-bin
+    # profile, shifted by one slice; a dropped or absolute z would break this
+    w = rand_weights(6, 0.1)
+    f = np.zeros((9, 1), np.float32)
+    f[2, 0] = -95.0           # slice 0, z_rel = 5
+    h0, _ = oracle.event_histogram(w, f)
+    f[2, 0] = -85.0           # slice 1, z_rel = 5
+    h1, _ = oracle.event_histogram(w, f)
+    assert np.all(h0[100:] == 0) and np.all(h1[:100] == 0) and np.all(h1[200:] == 0)
+    np.testing.assert_array_equal(h0[:100], h1[100:200])
+    x = np.zeros(9)
+    x[2] = 5.0
+    np.testing.assert_allclose(h0[:100], oracle.fc_track(w, x), rtol=0, atol=0)
+
+
+def test_histogram_drops_invalid_tracks():
+    w = rand_weights(6, 0.1)
+    f = np.zeros((9, 5), np.float32)
+    f[2] = [-100.5, 300.0, 10.0, 20.0, 30.0]
+    f[4, 3] = np.nan
+    f[7, 4] = np.inf
+    hist, dropped = oracle.event_histogram(w, f)
+    assert dropped == 4
+    only, _ = oracle.event_histogram(w, f[:, 2:3])
+    np.testing.assert_array_equal(hist, only)
+
+
+# ----------------------------------------------------------------- conv pieces
+
+def test_conv1d_matches_numpy_convolve_and_torch():
+    rng = np.random.default_rng(8)
+    cin, cout, L = 3, 4, 17
+    x = rng.normal(size=(cin, L))
+    W = rng.normal(size=(cout, cin, 5))
+    b = rng.normal(size=cout)
+    got = oracle.conv1d_k5(x, W, b)
+    want = np.zeros((cout, L))
+    for co in range(cout):
+        want[co] = b[co]
+        for ci in range(cin):
+            want[co] += np.convolve(x[ci], W[co, ci, ::-1], mode="same")
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    tw = F.conv1d(torch.as_tensor(x)[None], torch.as_tensor(W), torch.as_tensor(b), padding=2)
+    np.testing.assert_allclose(got, tw[0].numpy(), rtol=1e-13, atol=1e-13)
+
+
+def test_conv1d_delta_kernel_is_identity_and_linear():
+    rng = np.random.default_rng(9)
+    C, L = 5, 32
+    x = rng.normal(size=(C, L))
+    W = np.zeros((C, C, 5))
+    for c in range(C):
+        W[c, c, 2] = 1.0
+    np.testing.assert_array_equal(oracle.conv1d_k5(x, W, np.zeros(C)), x)
+    # shifted delta: tap 4 reads x[i + 2]
+    W2 = np.zeros((C, C, 5))
+    for c in range(C):
+        W2[c, c, 4] = 1.0
+    y = oracle.conv1d_k5(x, W2, np.zeros(C))
+    np.testing.assert_array_equal(y[:, :-2], x[:, 2:])
+    np.testing.assert_array_equal(y[:, -2:], 0)
+    Wr = rng.normal(size=(3, C, 5))
+    y1 = rng.normal(size=(C, L))
+    a, bb = 1.7, -0.4
+    lhs = oracle.conv1d_k5(a * x + bb * y1, Wr, np.zeros(3))
+    rhs = a * oracle.conv1d_k5(x, Wr, np.zeros(3)) + bb * oracle.conv1d_k5(y1, Wr, np.zeros(3))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+
+
+def test_convT_matches_torch_and_delta():
+    rng = np.random.default_rng(10)
+    cin, cout, L = 6, 3, 9
+    x = rng.normal(size=(cin, L))
+    W = rng.normal(size=(cin, cout, 2))
+    b = rng.normal(size=cout)
+    got = oracle.convT_k2s2(x, W, b)
+    want = F.conv_transpose1d(torch.as_tensor(x)[None], torch.as_tensor(W), torch.as_tensor(b),
+                              stride=2)[0].numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    # delta: channel c copied into both phases r = 0, 1 (nearest-neighbour upsampling)
+    Wd = np.zeros((3, 3, 2))
+    for c in range(3):
+        Wd[c, c, :] = 1.0
+    xd = rng.normal(size=(3, 8))
+    np.testing.assert_array_equal(oracle.convT_k2s2(xd, Wd, np.zeros(3)), np.repeat(xd, 2, axis=1))
+
+
+def test_maxpool_matches_torch():
+    x = np.random.default_rng(11).normal(size=(4, 22))
+    want = F.max_pool1d(torch.as_tensor(x)[None], 2)[0].numpy()
+    np.testing.assert_array_equal(oracle.maxpool2(x), want)
+
+
+# ----------------------------------------------------------------- UNet
+
+def test_unet_matches_torch_statement_short_sequence():
+    w = rand_weights(12, 0.2)
+    x = np.abs(np.random.default_rng(13).normal(0, 5, 256))
+    f, p, acts = oracle.unet(w, x, return_acts=True)
+    f2, p2 = ref.unet(w, x)
+    np.testing.assert_allclose(f, f2, rtol=1e-11, atol=1e-10)
+    np.testing.assert_allclose(p, p2, rtol=1e-12, atol=1e-14)
+    assert acts["e4"].shape == (128, 32) and acts["d1"].shape == (16, 256)
+
+
+def identity_unet_weights(a=0.5, c=-1.0):
+    """enc1 = delta on channel 0; dec1 = delta on the skip half's channel 0 with every
+    upsampled-path weight 0; final = a * delta + c; everything else 0."""
+    shapes = synth.layer_shapes()
+    w = {k: (np.zeros(s[0], np.float64), np.zeros(s[1], np.float64)) for k, s in shapes.items()}
+    w["enc1"][0][0, 0, 2] = 1.0
+    w["dec1"][0][0, 16 + 0, 2] = 1.0        # concat order [upsampled (0..15), skip (16..31)]
+    w["final"][0][0, 0, 2] = a
+    w["final"][1][0] = c
+    return w
+
+
+def test_unet_identity_closed_form():
+    a, c = 0.5, -1.0
+    w = identity_unet_weights(a, c)
+    h = np.random.default_rng(14).normal(0, 3, 4000)
+    f, p = oracle.unet(w, h)
+    lr = np.where(h > 0, h, 0.01 * h)
+    lr2 = np.where(lr > 0, lr, 0.01 * lr)     # LeakyReLU after enc1 and after dec1
+    np.testing.assert_allclose(f, a * lr2 + c, rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(p, 1.0 / (1.0 + np.exp(-(a * lr2 + c))), rtol=1e-15)
+
+
+def test_unet_concat_order_matters():
+    # the same delta placed on the upsampled half's channel 0 sees the (all-zero) deep path
+    w = identity_unet_weights()
+    w["dec1"][0][0, 16, 2] = 0.0
+    w["dec1"][0][0, 0, 2] = 1.0
+    h = np.abs(np.random.default_rng(15).normal(0, 3, 4000)) + 1
+    f, _ = oracle.unet(w, h)
+    np.testing.assert_array_equal(f, np.full(4000, -1.0))
+
+
+def test_unet_translation_equivariance():
+    w = rand_weights(16, 0.0)
+    rng = np.random.default_rng(17)
+    h = np.zeros(4000)
+    h[1500:2500] = np.abs(rng.normal(0, 5, 1000))
+    f0, _ = oracle.unet(w, h)
+    for shift in (8, 64, 256):
+        hs = np.roll(h, shift)
+        fs, _ = oracle.unet(w, hs)
+        # away from the ends (receptive field is well under 128 bins)
+        np.testing.assert_allclose(fs[128 + shift:4000 - 128], f0[128:4000 - 128 - shift],
+                                   rtol=1e-12, atol=1e-9)
+    # a shift that is not a multiple of 8 breaks the pooling grid: not equivariant
+    fs, _ = oracle.unet(w, np.roll(h, 3))
+    assert np.max(np.abs(fs[131:3872] - f0[128:3869])) > 1e-6
+
+
+# ----------------------------------------------------------------- peaks
+
+def _golden_cases():
+    with open(os.path.join(GOLDEN, "peaks_handbuilt.json")) as fh:
+        return json.load(fh)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+def test_peaks_handbuilt(case):
+    f = np.full(4000, case["background"], dtype=np.float64)
+    for i, v in case["set"]:
+        f[i] = v
+    n, z, bins = oracle.peaks(f)
+    assert n == len(case["bins"])
+    assert list(bins) == case["bins"]
+    for zi, want in zip(z, case["z"]):
+        if want is not None:
+            assert abs(zi - want) < 1e-12
+    with np.errstate(over="ignore"):
+        rb, rz = ref.peaks(f, 1.0 / (1.0 + np.exp(-f)))
+    assert list(rb) == case["bins"]
+    np.testing.assert_allclose(z, rz, rtol=0, atol=1e-12)
+
+
+def test_peaks_truncation_reports_true_count():
+    f = np.full(4000, -30.0)
+    f[10::20] = 3.0                        # 200 isolated peaks
+    n, z, bins = oracle.peaks(f, max_pv=64)
+    assert n == 200 and len(z) == 64
+    assert list(bins) == list(range(10, 10 + 20 * 64, 20))
+    assert np.all(np.diff(z) > 0)
+
+
+def test_peaks_threshold_equivalence_on_probability():
+    # the logit rule p > 0.01 <=> f > ln(0.01/0.99), checked away from the boundary
+    rng = np.random.default_rng(18)
+    f = rng.normal(-4.6, 2.0, 4000)
+    n, _, bins = oracle.peaks(f)
+    p = 1.0 / (1.0 + np.exp(-f))
+    for i in bins:
+        assert p[i] > 0.01
+    rb, _ = ref.peaks(f, p)
+    assert list(rb) == list(bins)
+
+
+# ----------------------------------------------------------------- whole pipeline
+
+def test_infer_matches_torch_statement_two_events():
+    w = rand_weights(20, 0.05)
+    ev = synth.generate_standard(2, 21)
+    r = oracle.infer(w, ev.features, ev.offsets, max_pv=1024, want_hist=True,
+                     want_logit=True, want_prob=True)
+    for e in range(2):
+        feats = ev.features[:, ev.offsets[e]:ev.offsets[e + 1]]
+        h = ref.histogram(w, feats)
+        np.testing.assert_allclose(r["hist"][e], h, rtol=1e-12, atol=1e-12)
+        f, p = ref.unet(w, h)
+        scale = np.max(np.abs(f))
+        np.testing.assert_allclose(r["logit"][e], f, rtol=0, atol=1e-11 * scale)
+        bins, z = ref.peaks(f, p)
+        n = r["pv_count"][e]
+        # decisions can only differ where two logits tie to within rounding
+        assert abs(n - len(bins)) <= 1
+        if n == len(bins):
+            np.testing.assert_allclose(r["pv_z"][e, :n], z, rtol=0, atol=1e-9)
+
+
+def test_infer_bypasses_invalid_events_and_threads_agree():
+    w = rand_weights(22, 0.0)
+    ev = synth.generate_standard(6, 23)
+    off = ev.offsets.copy()
+    off[3] = off[2] - 1                      # event 2 has a negative track count
+    r1 = oracle.infer(w, ev.features, off, max_pv=1024, nthreads=1, want_hist=True)
+    r4 = oracle.infer(w, ev.features, off, max_pv=1024, nthreads=4, want_hist=True)
+    assert r1["pv_count"][2] == -1
+    np.testing.assert_array_equal(r1["pv_count"], r4["pv_count"])
+    np.testing.assert_array_equal(r1["hist"], r4["hist"])
+    ok = [e for e in range(6) if e != 2]
+    np.testing.assert_array_equal(np.nan_to_num(r1["pv_z"][ok]), np.nan_to_num(r4["pv_z"][ok]))
+    # per-event track cap
+    r = oracle.infer(w, ev.features, ev.offsets, max_pv=8, max_tracks_per_event=100)
+    big = ev.tracks_per_event() > 100
+    assert np.all(r["pv_count"][big] == -1) and np.all(r["pv_count"][~big] >= 0)
