@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of PVFinder inference (events/s) on GB300.
+
+Workload: one batch of 1000 synthetic events per GPU (Poisson mean 5.6 PVs, ~155 tracks
+per event; He-initialised weights of the 9-32x5-100 FC net and the 16/32/64/128 UNet),
+the full path per step: FC + histogram, UNet, peak finding. Inputs are resident in HBM
+when a step starts; L2 is flushed (512 MB write) between steps, outside the timed
+events. `value` is device time (CUDA events on the launch stream, max over ranks);
+`e2e` repeats the measurement through the public Python API with pinned host buffers,
+including the host->device copy of the track features and offsets and the
+device->host copy of the PV lists.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16|fp8]
+  python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+With N > 1 (torchrun) every rank runs its own 1000 events (weak scaling, no
+collective on the data path; events are independent).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EVENTS = 1000
+FC_MAC_PER_TRACK = 9 * 32 + 4 * 32 * 32 + 32 * 100
+# multiply-accumulates per event of each UNet layer (M x N x K of the implicit GEMMs)
+LAYER_MAC = {
+    "enc1": 4000 * 16 * 5, "enc2": 2000 * 32 * 80, "enc3": 1000 * 64 * 160,
+    "enc4": 500 * 128 * 320, "up3": 500 * 128 * 128, "dec3": 1000 * 64 * 640,
+    "up2": 1000 * 64 * 64, "dec2": 2000 * 32 * 320, "up1": 2000 * 32 * 32,
+    "dec1": 4000 * 16 * 160, "final": 4000 * 1 * 80,
+}
+# which layers each kernel family computes
+FAMILY_LAYERS = {
+    "front": ["enc1"], "enc2": ["enc2"], "enc3": ["enc3"], "enc4": ["enc4"], "up3": ["up3"],
+    "dec3": ["dec3"], "up2": ["up2"], "dec2": ["dec2"], "up1": ["up1"], "dec1": ["dec1"],
+    "tail": ["final"], "enc4_up3": ["enc4", "up3"], "dec3_up2": ["dec3", "up2"],
+    "dec2_up1": ["dec2", "up1"],
+}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None):
+    """Times the FP64 oracle (as it stands) on a bounded sample of the workload, all cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n0 = min(batch.n_events, cores)
+    sub = batch.subset(0, n0)
+    t0 = time.perf_counter()
+    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores)
+    dt0 = time.perf_counter() - t0
+    n = int(min(batch.n_events, max(n0, n0 * target_s / max(dt0, 1e-3))))
+    if max_events:
+        n = min(n, max_events)
+    n = max(n0, n // cores * cores)
+    sub = batch.subset(0, n)
+    t0 = time.perf_counter()
+    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "events/s", "cores": min(cores, n), "kind": "oracle",
+            "sample": f"first {n} of the {batch.n_events}-event workload, FP64 C oracle, "
+                      f"one event per thread, {dt:.1f} s wall"}
+
+
+def run_reference(args, weights, batch, rank, world):
+    """--impl reference: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    cores = os.cpu_count() or 1
+    per_step = cores
+    n = batch.n_events
+    times = []
+    for step in range(args.warmup + args.steps):
+        a = (step * per_step) % n
+        b = min(n, a + per_step)
+        sub = batch.subset(a, b)
+        t0 = time.perf_counter()
+        oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append((b - a, dt))
+    ev = sum(t[0] for t in times)
+    sec = sum(t[1] for t in times)
+    value = ev / sec
+    line = {
+        "impl": "reference", "metric": "events/s", "value": value, "unit": "events/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sec / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, "f64"),
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} events per step (one per core), rotating through "
+                                   f"the {n}-event workload"},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, dtype):
+    return {"workload": f"PVFinder inference, {args.events} synthetic events per GPU "
+                        f"(~155 tracks/event, Poisson 5.6 PVs), 4000-bin histogram, "
+                        f"16/32/64/128 UNet, {dtype}",
+            "events_per_gpu": args.events, "bins": 4000, "max_pv_per_event": args.max_pv,
+            "l2": "flushed between steps (512 MB write)", "form": args.precision}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--events", type=int, default=N_EVENTS)
+    ap.add_argument("--max-pv", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    import synth
+    rank, world, local = dist_env()
+    weights = synth.he_weights(0)
+    batch = synth.generate_standard(args.events, 1000 + rank)
+
+    if args.impl == "reference":
+        run_reference(args, weights, batch, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2602_19959_gb300 import build, PVFinder
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+
+    dtype = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision]
+    stream = torch.cuda.current_stream()
+    pv = PVFinder(weights, precision=args.precision, max_events=args.events,
+                  max_pv_per_event=args.max_pv)
+    feats_h = torch.from_numpy(batch.features).pin_memory()
+    offs_h = torch.from_numpy(batch.offsets).pin_memory()
+    feats = feats_h.cuda()
+    offs = offs_h.cuda()
+    z, c = pv.alloc_outputs(args.events)
+    z_h = torch.empty(z.shape, dtype=z.dtype).pin_memory()
+    c_h = torch.empty(c.shape, dtype=c.dtype).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step_device():
+        pv.infer(feats, offs, out=(z, c))
+
+    def step_e2e():
+        feats.copy_(feats_h, non_blocking=True)
+        offs.copy_(offs_h, non_blocking=True)
+        pv.infer(feats, offs, out=(z, c))
+        z_h.copy_(z, non_blocking=True)
+        c_h.copy_(c, non_blocking=True)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step_device()
+    torch.cuda.synchronize()
+    status = pv.device_status()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        prof = {}
+        pv.profile_enable(profile)
+        barrier()
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+            if profile:
+                for k, (n, ms) in pv.profile_read().items():
+                    a = prof.setdefault(k, [0, 0.0])
+                    a[0] += n
+                    a[1] += ms
+        barrier()
+        wall = time.perf_counter() - w0
+        pv.profile_enable(False)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        return ms, wall, prof
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    dev_ms, wall, prof = timed(step_device, True)
+    clocks = sampler.stop()
+    e2e_ms, _, _ = timed(step_e2e, False)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    dev_ms = max_over_ranks(dev_ms)
+    e2e_ms = max_over_ranks(e2e_ms)
+    total_events = args.events * world * args.steps
+    value = total_events / (dev_ms / 1000.0)
+    e2e_value = total_events / (e2e_ms / 1000.0)
+
+    # dominant kernel and its roofline (algorithmic work / live launch duration)
+    peaks, peak_src = load_peaks()
+    valid_tracks = int(np.sum(np.diff(batch.offsets)))
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, tot_ms) = dom
+    avg_ms = tot_ms / max(launches, 1)
+    ev_per_launch = args.events   # one launch covers the whole (unchunked) batch
+    mac = sum(LAYER_MAC[l] for l in FAMILY_LAYERS.get(name, [])) * ev_per_launch
+    if name == "front":
+        mac += FC_MAC_PER_TRACK * valid_tracks
+    achieved = 2.0 * mac / (avg_ms / 1000.0) / 1e12
+    if args.precision == "fp32":
+        # CUDA-core float32: 152 SMs x 128 FMA lanes x 2 FLOP x max SM clock
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz of measured peaks"}
+    else:
+        peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "peak_source": f"{peak_src} bf16 burst" + (" x2 nominal fp8 ratio" if args.precision == "fp8" else "")}
+    kernels = {k: {"launches": n, "avg_us": 1000.0 * ms / max(n, 1),
+                   "share": ms / max(sum(v[1] for v in prof.values()), 1e-9)}
+               for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    gpu_launches = int(sum(n for n, _ in prof.values()))
+
+    h2d = batch.features.nbytes + batch.offsets.nbytes
+    d2h = z.numel() * 4 + c.numel() * 4
+    line = {
+        "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": workload_config(args, dtype),
+        "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roof, "kernels": kernels, "gpu_launches": gpu_launches,
+        "clocks": clocks, "wall_s_timed": wall, "device_status": status,
+        "peaks_source": peak_src,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_cpu_baseline(weights, batch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * pvf.h -- C ABI of the GB300 (sm_103a) PVFinder inference library (libpvf.so).
+ *
+ * The library runs the inference hot path of the hybrid PVFinder algorithm of
+ * arXiv 2602.19959 on one GPU, every step in hand-written CUDA kernels:
+ *   1. per-track fully connected network on nine track features        (§2)
+ *   2. deterministic scatter-sum of the track outputs into each event's
+ *      4000-bin z histogram (40 slices x 100 bins over [-100, 300) mm)   (§2)
+ *   3. UNet-style 1D CNN over the histogram                              (§2)
+ *   4. peak finding (local maximum + threshold + centroid)               (§2)
+ * It follows the deployment constraints of §3: zero-copy Structure-of-Arrays
+ * input, one fixed caller-owned device pool bound at creation (nothing is
+ * allocated afterwards), execution on the caller's single stream with no
+ * default-stream work and no device-wide synchronisation inside pvf_infer, and
+ * deterministic results (no floating-point atomics; every per-bin sum has a fixed
+ * order that depends only on the event's own tracks).
+ *
+ * Conventions for every function below:
+ *   - Pointers documented as "device" must point to device memory (or memory the
+ *     device can access); "host" pointers are read on the calling thread.
+ *   - Functions return PVF_OK or an error code and never abort the process.
+ *     Argument errors are detected on the host before any work is enqueued, and
+ *     nothing is enqueued when a function returns an error.
+ *   - Work is enqueued on the given stream and the call returns after enqueueing,
+ *     unless the function says it synchronises.
+ *   - A handle may be used from one thread at a time. Calls that overlap on the
+ *     device (different streams, same handle) race on the handle's pool.
+ */
+#ifndef PVF_H
+#define PVF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PVF_API __attribute__((visibility("default")))
+#else
+#define PVF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA headers. */
+typedef struct CUstream_st *pvf_stream_t;
+
+/* Status codes (§3: "Error handling employs a Status enum enabling graceful
+ * degradation"). Values >= PVF_WARN_EVENTS_SKIPPED are warnings: results were
+ * produced, but some events were bypassed or truncated. */
+typedef enum {
+    PVF_OK = 0,
+    PVF_ERR_INVALID_ARG = 1,     /* null/misaligned pointer, size out of range        */
+    PVF_ERR_POOL_TOO_SMALL = 2,  /* pool smaller than pvf_pool_bytes_required         */
+    PVF_ERR_WEIGHTS = 3,         /* weight blob malformed or of another architecture  */
+    PVF_ERR_CUDA = 4,            /* a CUDA runtime call failed                        */
+    PVF_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up                */
+    PVF_ERR_UNSUPPORTED = 6,     /* feature not available for this configuration      */
+    PVF_WARN_EVENTS_SKIPPED = 16,/* some events were bypassed (count = -1)            */
+    PVF_WARN_TRUNCATED = 17      /* some event had more than max_pv_per_event PVs     */
+} pvf_status;
+
+/* Arithmetic of the FC net and of the UNet convolutions. The histogram, the first
+ * (1 -> c0 channel) convolution, the final convolution, the sigmoid and the
+ * centroids are float32 in every form. */
+typedef enum {
+    PVF_FP32 = 0,      /* CUDA-core float32 ("plain FP32 GPU form")                     */
+    PVF_BF16 = 1,      /* tcgen05 tensor cores, bf16 operands, fp32 accumulation         */
+    PVF_FP8_E4M3 = 2   /* tcgen05 tensor cores, e4m3 operands with per-output-channel
+                          weight scales and per-tensor activation scales, fp32 accum.   */
+} pvf_precision;
+
+/* Creation-time plan (§3: TensorSpec freezing batch dimensions, channels, length and
+ * data type at initialisation). Everything is frozen at pvf_create. */
+typedef struct {
+    int32_t precision;             /* pvf_precision                                        */
+    int32_t max_events;            /* largest n_events of one pvf_infer call, >= 1          */
+    int32_t max_tracks_per_event;  /* 1..8192; larger events are bypassed (count = -1)      */
+    int32_t max_pv_per_event;      /* output slots per event, 1..1024                       */
+    int32_t chunk_events;          /* events whose UNet activations are resident at once;
+                                      0 = max_events. Smaller chunks shrink the pool.       */
+    int32_t reserved[3];           /* must be 0                                             */
+    const float *fp8_act_scales;   /* host, PVF_FP8_E4M3 only: PVF_N_ACT_SCALES per-tensor
+                                      input scales (amax / 448), or NULL to use
+                                      pvf_calibrate before the first pvf_infer              */
+} pvf_config;
+
+#define PVF_N_FEATURES 9
+#define PVF_N_BINS 4000
+#define PVF_N_ACT_SCALES 16
+
+/* Track features, Structure of Arrays (§3: Allen's SoA buffers, read zero-copy).
+ * f[k] points to a device float array of n_tracks entries indexed by global track
+ * number, in the order poca_x, poca_y, poca_z, tx, ty, w1, w2, w3, quality. Events
+ * whose offsets reach past n_tracks are bypassed, never read. */
+typedef struct {
+    const float *f[PVF_N_FEATURES];
+    int64_t n_tracks;
+} pvf_tracks_soa;
+
+typedef struct pvf_handle pvf_handle;
+
+/* Bytes of device pool that pvf_create needs for cfg (weights, per-event state and
+ * activations, with 256-byte alignment slack). Host only; no CUDA call. */
+PVF_API pvf_status pvf_pool_bytes_required(const pvf_config *cfg, size_t *out_bytes);
+
+/* Creates a handle.
+ *   weights_blob  host, blob_bytes bytes: float32 master weights in the "PVFW" v1
+ *                 format (header, layer table, data); copied, caller keeps ownership.
+ *   pool          device, >= pvf_pool_bytes_required(cfg) bytes, 256-byte aligned;
+ *                 caller-owned, never freed by the library, must outlive the handle.
+ *   stream        stream used for the one-time upload; pvf_create synchronises it.
+ * The weights are converted to the chosen precision and laid out in the pool;
+ * no device memory is allocated by the library, now or later.
+ * Errors: PVF_ERR_INVALID_ARG, PVF_ERR_WEIGHTS, PVF_ERR_POOL_TOO_SMALL, PVF_ERR_CUDA. */
+PVF_API pvf_status pvf_create(const void *weights_blob, size_t blob_bytes, void *pool,
+                      size_t pool_bytes, const pvf_config *cfg, pvf_stream_t stream,
+                      pvf_handle **out);
+
+/* Runs the whole path on n_events events (0 <= n_events <= max_events).
+ *   tracks        features of all tracks (device arrays, see pvf_tracks_soa)
+ *   event_offsets device int32[n_events + 1]; event e owns tracks
+ *                 [event_offsets[e], event_offsets[e+1])
+ *   out_pv_z      device float[n_events * max_pv_per_event]: PV z in mm, ascending
+ *                 per event; slots past the event's count are left untouched
+ *   out_pv_count  device int32[n_events]: number of PVs found (may exceed
+ *                 max_pv_per_event: only the first max_pv_per_event z are written),
+ *                 or -1 when the event was bypassed
+ * An event is bypassed (§3: events failing validation bypass ML reconstruction)
+ * when its offsets are negative, decreasing or beyond tracks->n_tracks, or it has
+ * more than max_tracks_per_event tracks. A track is dropped (not an error) when a feature is
+ * not finite or its z lies outside [-100, 300) mm. Warnings are reported by
+ * pvf_last_device_status. Asynchronous on stream. */
+PVF_API pvf_status pvf_infer(pvf_handle *h, const pvf_tracks_soa *tracks,
+                     const int32_t *event_offsets, int32_t n_events, float *out_pv_z,
+                     int32_t *out_pv_count, pvf_stream_t stream);
+
+/* pvf_infer that also copies intermediate results, for parity checks:
+ *   out_hist   device float[n_events * 4000] or NULL: the histogram (step 2)
+ *   out_logit  device float[n_events * 4000] or NULL: the final conv output before
+ *              the sigmoid (step 3); peak decisions are taken on these logits */
+PVF_API pvf_status pvf_infer_ex(pvf_handle *h, const pvf_tracks_soa *tracks,
+                        const int32_t *event_offsets, int32_t n_events, float *out_pv_z,
+                        int32_t *out_pv_count, float *out_hist, float *out_logit,
+                        pvf_stream_t stream);
+
+/* Stage entry points: the same kernels as pvf_infer, one step at a time.
+ * pvf_stage_histogram: steps 1-2 -> out_hist device float[n_events * 4000].
+ * pvf_stage_unet:      step 3 on a given histogram (device float[n_events * 4000])
+ *                      -> out_logit device float[n_events * 4000] (pre-sigmoid).
+ * pvf_stage_peaks:     step 4 on given logits (device float[n_events * 4000]). */
+PVF_API pvf_status pvf_stage_histogram(pvf_handle *h, const pvf_tracks_soa *tracks,
+                               const int32_t *event_offsets, int32_t n_events,
+                               float *out_hist, pvf_stream_t stream);
+PVF_API pvf_status pvf_stage_unet(pvf_handle *h, const float *hist, int32_t n_events,
+                          float *out_logit, pvf_stream_t stream);
+PVF_API pvf_status pvf_stage_peaks(pvf_handle *h, const float *logit, int32_t n_events,
+                           float *out_pv_z, int32_t *out_pv_count, pvf_stream_t stream);
+
+/* Reads and clears the handle's device status word (the worst status raised by
+ * kernels since the last read: PVF_OK, PVF_WARN_*, PVF_ERR_TIMEOUT).
+ * Synchronises stream. */
+PVF_API pvf_status pvf_last_device_status(pvf_handle *h, int32_t *out_status, pvf_stream_t stream);
+
+/* Per-kernel timing (CUDA events recorded around every kernel launch on the launch
+ * stream), for profiling only. pvf_profile_enable(h, 1) creates the events (host-side
+ * driver objects, no device memory) and starts recording; 0 stops. */
+typedef struct {
+    char name[24];       /* kernel family, e.g. "front", "enc2", "dec3", "tail"        */
+    int32_t launches;    /* launches timed since the last read                         */
+    float total_ms;      /* sum of their durations                                     */
+} pvf_kernel_time;
+PVF_API pvf_status pvf_profile_enable(pvf_handle *h, int32_t on);
+/* Synchronises stream, sums the recorded durations per kernel family into out
+ * (at most max_entries, *n_entries set to the number written) and clears them. */
+PVF_API pvf_status pvf_profile_read(pvf_handle *h, pvf_kernel_time *out, int32_t max_entries,
+                                    int32_t *n_entries, pvf_stream_t stream);
+
+/* Frees the handle's host state. The pool stays owned by the caller. NULL is a no-op. */
+PVF_API pvf_status pvf_destroy(pvf_handle *h);
+
+/* Static, never-NULL description of a status code. */
+PVF_API const char *pvf_status_str(pvf_status s);
+
+/* Library version, (major << 16) | minor. */
+PVF_API int32_t pvf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PVF_H */

@@ -1,0 +1,167 @@
+// End of step 3 and step 4 of the path (§2): the final 16 -> 1 channel k5 convolution
+// (float32 in every form) and heuristic peak finding on its output.
+//
+// One CTA per event, 256 threads:
+//   1. f[p] = b + sum_t sum_ci W[t][ci] d1[p + t - 2][ci]  (the logit; prob = sigmoid(f)),
+//      kept in shared memory, optionally copied out;
+//   2. local-maximum rule with a fixed threshold in place of the paper's learned ones:
+//      bin i is a PV iff p[i] > 0.01, p[i] > p[j] for the 5 bins on its left and
+//      p[i] >= p[j] for the 5 bins on its right (clipped at the ends). Because sigmoid
+//      is strictly increasing these decisions are taken exactly on f (the threshold
+//      becomes ln(0.01 / 0.99)), which avoids the float32 saturation of sigmoid
+//      (which rounds to 1 for f > 16.6) turning distinct maxima into ties;
+//   3. z = centroid over bins [i - 3, i + 3] with weights p[j] = sigmoid(f[j]);
+//   4. ordered compaction: each thread owns 16 consecutive bins, a block-wide
+//      exclusive scan of the per-thread counts gives each PV its slot, so PVs are
+//      written in ascending z without atomics. The true count is always reported.
+#include "pvf_internal.cuh"
+
+namespace pvf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPerThread = 16;    // kThreads * kPerThread >= kBins
+// ln(0.01 / 0.99) rounded to float
+constexpr float kThrLogit = -4.59511985013459f;
+
+template <class T>
+__device__ __forceinline__ void load_row16(const T *src, float v[kC0], float scale) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 *s = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float4 x = s[i];
+            v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+        }
+    } else if constexpr (sizeof(T) == 2) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(src);
+        uint4 pk[2] = {s[0], s[1]};
+        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(pk);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float2 f = __bfloat1622float2(b[i]);
+            v[2 * i] = f.x; v[2 * i + 1] = f.y;
+        }
+    } else {
+        uint4 pk = *reinterpret_cast<const uint4 *>(src);
+        const __nv_fp8_e4m3 *b = reinterpret_cast<const __nv_fp8_e4m3 *>(&pk);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = float(b[i]) * scale;
+    }
+}
+
+__device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
+    using T = typename Elem<PREC>::T;
+    __shared__ __align__(16) float sf[kThreads * kPerThread];
+    __shared__ float sw[kFinalFloats];
+    __shared__ int swarp[kThreads / 32];
+
+    const int tid = threadIdx.x;
+    const int e = blockIdx.x;
+    const int ge = a.ev_base + e;
+
+    if (a.logit_in) {
+        const float *src = a.logit_in + (size_t)ge * kBins;
+        for (int p = tid; p < kBins; p += kThreads) sf[p] = src[p];
+    } else {
+        for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
+        __syncthreads();
+        const T *d = reinterpret_cast<const T *>(a.d1) + (size_t)e * padded_rows(kBins) * kC0;
+        for (int p = tid; p < kBins; p += kThreads) {
+            float acc = sw[5 * kC0];
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                float v[kC0];
+                load_row16<T>(d + (size_t)(p + t) * kC0, v, a.d1_scale);   // storage row p + t = position p + t - 2
+#pragma unroll
+                for (int ci = 0; ci < kC0; ++ci) acc = fmaf(sw[t * kC0 + ci], v[ci], acc);
+            }
+            sf[p] = acc;
+        }
+    }
+    __syncthreads();
+    if (a.logit_out) {
+        float *dst = a.logit_out + (size_t)ge * kBins;
+        for (int p = tid; p < kBins; p += kThreads) dst[p] = sf[p];
+    }
+    if (!a.pv_count) return;
+
+    const bool bypass = a.ev_flag && a.ev_flag[ge] != 0;
+    // ---- candidates in this thread's 16 bins
+    const int i0 = tid * kPerThread;
+    unsigned mask = 0;
+    if (!bypass) {
+#pragma unroll 1
+        for (int k = 0; k < kPerThread; ++k) {
+            const int i = i0 + k;
+            if (i >= kBins) break;
+            const float fi = sf[i];
+            if (!(fi > kThrLogit)) continue;
+            bool ok = true;
+            for (int j = max(0, i - kPeakHalfWin); j < i; ++j) ok &= fi > sf[j];
+            for (int j = i + 1; j <= min(kBins - 1, i + kPeakHalfWin); ++j) ok &= fi >= sf[j];
+            if (ok) mask |= 1u << k;
+        }
+    }
+    const int cnt = __popc(mask);
+    // ---- block exclusive scan of cnt
+    const int lane = tid & 31, warp = tid >> 5;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) swarp[warp] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+        const int v = swarp[w];
+        if (w < warp) wbase += v;
+        total += v;
+    }
+    int idx = wbase + incl - cnt;
+    float *zout = a.pv_z + (size_t)ge * a.max_pv;
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (idx < a.max_pv) {
+            const int i = i0 + k;
+            float num = 0.0f, den = 0.0f;
+#pragma unroll
+            for (int d = -kCentroidHalf; d <= kCentroidHalf; ++d) {
+                const int j = i + d;
+                if (j < 0 || j >= kBins) continue;
+                const float pj = sigmoid_f(sf[j]);
+                num = fmaf(pj, (float)d, num);
+                den += pj;
+            }
+            // z = zc(i) + 0.1 * (sum p_j (j - i) / sum p_j), zc(i) = -100 + (i + 0.5) * 0.1
+            zout[idx] = fmaf((float)i + 0.5f + num / den, kBinW, kZLo);
+        }
+        ++idx;
+    }
+    if (tid == 0) {
+        a.pv_count[ge] = bypass ? -1 : total;
+        if (!bypass && total > a.max_pv) raise_status(a.status, PVF_WARN_TRUNCATED);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
+    if (a.n_events <= 0) return cudaSuccess;
+    dim3 grid(a.n_events), block(kThreads);
+    switch (precision) {
+    case PVF_FP32: k_tail<PVF_FP32><<<grid, block, 0, s>>>(a); break;
+    case PVF_BF16: k_tail<PVF_BF16><<<grid, block, 0, s>>>(a); break;
+    default: k_tail<PVF_FP8_E4M3><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pvf

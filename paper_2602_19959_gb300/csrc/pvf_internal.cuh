@@ -1,0 +1,166 @@
+// Internal definitions shared by the libpvf CUDA translation units.
+//
+// Data layout in the device pool (all offsets planned once at pvf_create):
+//   * weights, converted from the float32 master blob into per-kernel layouts;
+//   * per-event state: a bypass flag per event, the histogram rows when requested;
+//   * UNet activations for one chunk of events, channel-last with two zero pad rows on
+//     each side of every event: element (event e, position p, channel c) of a tensor
+//     with L positions and C channels sits at row e * (L + 4) + p + 2, column c.
+//     Producers write their own pad rows, so buffers can be reused by later layers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "pvf.h"
+
+namespace pvf {
+
+// Geometry of the method (§2): 400 mm region, 40 slices (intervals) of 100 bins.
+constexpr int kBins = 4000;
+constexpr int kSlices = 40;
+constexpr int kSliceBins = 100;
+constexpr int kFeatures = 9;
+constexpr int kFcHidden = 32;
+constexpr int kFcOut = 100;
+constexpr int kFcInPad = 12;   // layer-1 input padded to a multiple of 4 floats
+constexpr int kC0 = 16;        // UNet base width; levels have 16, 32, 64, 128 channels
+constexpr int kPad = 2;        // zero rows on each side of an event (k5 "same" padding)
+constexpr float kZLo = -100.0f;
+constexpr float kBinW = 0.1f;
+constexpr float kThreshold = 0.01f;
+constexpr int kPeakHalfWin = 5;
+constexpr int kCentroidHalf = 3;
+
+// FC weights in float32 (the FP32 form and the CUDA-core reference layouts).
+// Layer l: W[out][in] row-major, layer 1 padded to 12 inputs; then all biases.
+constexpr int kFcW1 = kFcHidden * kFcInPad;          // 384
+constexpr int kFcWH = kFcHidden * kFcHidden;         // 1024
+constexpr int kFcW6 = kFcOut * kFcHidden;            // 3200
+constexpr int kFcWTotal = kFcW1 + 4 * kFcWH + kFcW6; // 7680
+constexpr int kFcBTotal = 5 * kFcHidden + kFcOut;    // 260
+constexpr int kFcFloats = kFcWTotal + kFcBTotal;     // 7940
+
+// Offsets inside the packed FC block (floats).
+__host__ __device__ constexpr int fc_w_off(int l) {
+    return l == 0 ? 0 : (l < 5 ? kFcW1 + (l - 1) * kFcWH : kFcW1 + 4 * kFcWH);
+}
+__host__ __device__ constexpr int fc_b_off(int l) {
+    return kFcWTotal + (l < 5 ? l * kFcHidden : 5 * kFcHidden);
+}
+
+// enc1 (1 -> 16, k5) in float32: W[t][co] then b[co].
+constexpr int kEnc1Floats = 5 * kC0 + kC0;
+// final (16 -> 1, k5) in float32: W[t][ci] then b.
+constexpr int kFinalFloats = 5 * kC0 + 1;
+
+// Device status word values are pvf_status codes; kernels raise them with atomicMax
+// (an integer maximum: order-independent).
+__device__ __forceinline__ void raise_status(int32_t *word, int32_t s) {
+    if (word) atomicMax(word, s);
+}
+
+__device__ __forceinline__ float leaky(float x) { return x > 0.0f ? x : 0.01f * x; }
+
+// Storage element of an activation tensor for each precision form.
+template <int PREC> struct Elem;
+template <> struct Elem<PVF_FP32> { using T = float; };
+template <> struct Elem<PVF_BF16> { using T = __nv_bfloat16; };
+template <> struct Elem<PVF_FP8_E4M3> { using T = __nv_fp8_e4m3; };
+
+template <class T> __device__ __forceinline__ T to_elem(float v, float inv_scale);
+template <> __device__ __forceinline__ float to_elem<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_elem<__nv_bfloat16>(float v, float) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __nv_fp8_e4m3 to_elem<__nv_fp8_e4m3>(float v, float inv) {
+    return __nv_fp8_e4m3(v * inv);   // saturating round-to-nearest-even
+}
+template <class T> __device__ __forceinline__ float from_elem(T v, float scale);
+template <> __device__ __forceinline__ float from_elem<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ float from_elem<__nv_bfloat16>(__nv_bfloat16 v, float) {
+    return __bfloat162float(v);
+}
+template <> __device__ __forceinline__ float from_elem<__nv_fp8_e4m3>(__nv_fp8_e4m3 v, float s) {
+    return float(v) * s;
+}
+
+// Rows per event of a padded activation tensor with L positions.
+__host__ __device__ __forceinline__ int64_t padded_rows(int L) { return (int64_t)L + 2 * kPad; }
+
+// ---------------------------------------------------------------- kernel arguments
+
+struct FrontArgs {
+    const float *feat[kFeatures];
+    const int32_t *offsets;      // global offsets array (n_total_events + 1)
+    int64_t n_tracks;            // length of every feature array
+    int32_t n_events;            // events in this launch
+    int32_t ev_base;             // global index of the launch's first event
+    int32_t max_tracks;          // per-event cap
+    const float *fc;             // packed FC block (kFcFloats)
+    const float *enc1;           // kEnc1Floats
+    const float *hist_in;        // non-null: skip steps 1-2, read histograms (global rows)
+    float *hist_out;             // nullable, global rows [ev_base + e]
+    void *e1;                    // chunk-local padded [n][4004][16]
+    void *p1;                    // chunk-local padded [n][2004][16]
+    float e1_inv_scale;          // fp8 only: 1 / scale of e1/p1
+    int32_t *ev_flag;            // global [max_events]: 1 = bypassed
+    int32_t *status;
+};
+
+struct TailArgs {
+    const void *d1;              // chunk-local padded [n][4004][16], or null for logit_in
+    const float *logit_in;       // non-null: peaks only, read logits (global rows)
+    float d1_scale;              // fp8 only
+    const float *final_w;        // kFinalFloats
+    int32_t n_events;
+    int32_t ev_base;
+    const int32_t *ev_flag;      // nullable (all events valid)
+    float *logit_out;            // nullable, global rows
+    float *pv_z;                 // global [n_total][max_pv]
+    int32_t *pv_count;           // global [n_total]
+    int32_t max_pv;
+    int32_t *status;
+};
+
+// Optional per-launch timing hook: begin/end bracket one kernel launch on stream s.
+struct ProfHook {
+    void (*begin)(void *ctx, const char *name, cudaStream_t s);
+    void (*end)(void *ctx, cudaStream_t s);
+    void *ctx;
+};
+struct ProfScope {
+    const ProfHook *h;
+    cudaStream_t s;
+    ProfScope(const ProfHook *hook, const char *name, cudaStream_t st) : h(hook), s(st) {
+        if (h) h->begin(h->ctx, name, s);
+    }
+    ~ProfScope() { if (h) h->end(h->ctx, s); }
+};
+
+// Host-side launchers (defined in the kernel translation units).
+cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem_bytes, cudaStream_t s);
+size_t front_smem_bytes(int max_tracks);
+cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s);
+
+struct ConvF32Weights {
+    const float *w[6], *b[6];     // enc2, enc3, enc4, dec3, dec2, dec1: W[5][Cin][Cout]
+    const float *uw[3], *ub[3];   // up3, up2, up1: W[Cin][2][Cout]
+};
+// Activation slots of one chunk of events, assigned by liveness (layer order: front,
+// enc2, enc3, enc4, up3, dec3, up2, dec2, up1, dec1, tail):
+//   big slots (kBigElems per event):   e1 | e2 | e3 | deep = e4, d3, d2, d1 | up = u3, u2, u1
+//   small slots (kSmallElems per event): s0 = p1, p3 | s1 = p2
+// Inside its slot a tensor is packed with its own per-event stride (L + 4) * C, which is
+// never larger than the slot's per-event size.
+constexpr int64_t kBigElems = 504 * 128;    // largest of (L + 4) * C over the big tensors
+constexpr int64_t kSmallElems = 504 * 64;   // largest over p1, p2, p3
+struct UnetBuffers {
+    void *e1, *e2, *e3, *deep, *up, *s0, *s1;
+};
+cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n_events,
+                            cudaStream_t s, const ProfHook *prof);
+
+}  // namespace pvf

@@ -1,0 +1,249 @@
+"""ctypes binding of libpvf (include/pvf.h): argument marshalling only.
+
+Every step of the inference path runs in the library's CUDA kernels. PyTorch is used
+for device memory (the fixed pool, inputs and outputs) and for the current stream;
+tensors are passed as raw device pointers. If libpvf.so has not been built, loading
+fails loudly: there is no fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .weights import pack_blob
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpvf.so")
+
+PVF_OK = 0
+PVF_ERR_INVALID_ARG = 1
+PVF_ERR_POOL_TOO_SMALL = 2
+PVF_ERR_WEIGHTS = 3
+PVF_ERR_CUDA = 4
+PVF_ERR_TIMEOUT = 5
+PVF_ERR_UNSUPPORTED = 6
+PVF_WARN_EVENTS_SKIPPED = 16
+PVF_WARN_TRUNCATED = 17
+
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+N_BINS = 4000
+N_ACT_SCALES = 16
+
+EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex",
+            "pvf_stage_histogram", "pvf_stage_unet", "pvf_stage_peaks",
+            "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_destroy",
+            "pvf_status_str", "pvf_version")
+
+
+class PvfConfig(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_events", ctypes.c_int32),
+                ("max_tracks_per_event", ctypes.c_int32), ("max_pv_per_event", ctypes.c_int32),
+                ("chunk_events", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("fp8_act_scales", ctypes.c_void_p)]
+
+
+class PvfTracks(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p * 9), ("n_tracks", ctypes.c_int64)]
+
+
+class PvfKernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_float)]
+
+
+class PvfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} ({code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpvf.so and declares the C signatures. Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2602_19959_gb300.build()")
+        lib = ctypes.CDLL(path)
+        P, I32, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+        S = ctypes.c_int
+        sig = {
+            "pvf_pool_bytes_required": (S, [ctypes.POINTER(PvfConfig), ctypes.POINTER(SZ)]),
+            "pvf_create": (S, [P, SZ, P, SZ, ctypes.POINTER(PvfConfig), P, ctypes.POINTER(P)]),
+            "pvf_infer": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P, P]),
+            "pvf_infer_ex": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P, P, P, P]),
+            "pvf_stage_histogram": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P]),
+            "pvf_stage_unet": (S, [P, P, I32, P, P]),
+            "pvf_stage_peaks": (S, [P, P, I32, P, P, P]),
+            "pvf_last_device_status": (S, [P, ctypes.POINTER(I32), P]),
+            "pvf_profile_enable": (S, [P, I32]),
+            "pvf_profile_read": (S, [P, ctypes.POINTER(PvfKernelTime), I32, ctypes.POINTER(I32), P]),
+            "pvf_destroy": (S, [P]),
+            "pvf_status_str": (ctypes.c_char_p, [S]),
+            "pvf_version": (I32, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return load().pvf_status_str(code).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(code: int, where: str, allow_warn: bool = False):
+    if code != PVF_OK and not (allow_warn and code >= PVF_WARN_EVENTS_SKIPPED):
+        raise PvfError(code, where)
+    return code
+
+
+def make_config(precision="fp32", max_events=1, max_tracks_per_event=2048, max_pv_per_event=64,
+                chunk_events=0, fp8_act_scales=None):
+    cfg = PvfConfig()
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.max_events = max_events
+    cfg.max_tracks_per_event = max_tracks_per_event
+    cfg.max_pv_per_event = max_pv_per_event
+    cfg.chunk_events = chunk_events
+    keep = None
+    if fp8_act_scales is not None:
+        keep = np.ascontiguousarray(fp8_act_scales, dtype=np.float32)
+        cfg.fp8_act_scales = keep.ctypes.data
+    return cfg, keep
+
+
+def pool_bytes_required(**cfg_kwargs) -> int:
+    cfg, _ = make_config(**cfg_kwargs)
+    out = ctypes.c_size_t(0)
+    _check(load().pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)), "pvf_pool_bytes_required")
+    return int(out.value)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def tracks_struct(features) -> PvfTracks:
+    """features: CUDA float32 tensor [9, n_tracks] (rows contiguous) or a list of 9."""
+    t = PvfTracks()
+    rows = [features[k] for k in range(9)]
+    t.n_tracks = int(rows[0].numel())
+    for k, r in enumerate(rows):
+        if not r.is_cuda or r.dtype.itemsize != 4 or not r.is_contiguous():
+            raise ValueError("features must be contiguous CUDA float32 rows")
+        if r.numel() != t.n_tracks:
+            raise ValueError("all feature rows must have the same length")
+        t.f[k] = r.data_ptr()
+    return t
+
+
+class PVFinder:
+    """Owns a pool tensor and a pvf_handle; every method maps to one C entry point."""
+
+    def __init__(self, weights: dict, precision="fp32", max_events=1024,
+                 max_tracks_per_event=2048, max_pv_per_event=64, chunk_events=0,
+                 fp8_act_scales=None, device=None, stream=None):
+        import torch
+        self.lib = load()
+        self.device = torch.device(device or "cuda")
+        self.cfg, self._keep = make_config(precision, max_events, max_tracks_per_event,
+                                           max_pv_per_event, chunk_events, fp8_act_scales)
+        need = ctypes.c_size_t(0)
+        _check(self.lib.pvf_pool_bytes_required(ctypes.byref(self.cfg), ctypes.byref(need)),
+               "pvf_pool_bytes_required")
+        self.pool_bytes = int(need.value)
+        self.pool = torch.empty(self.pool_bytes, dtype=torch.uint8, device=self.device)
+        blob = pack_blob(weights)
+        self._blob = ctypes.create_string_buffer(blob, len(blob))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.pvf_create(self._blob, len(blob), self.pool.data_ptr(), self.pool_bytes,
+                                       ctypes.byref(self.cfg), _stream_ptr(stream), ctypes.byref(h)),
+                   "pvf_create")
+        self.handle = h
+        self.max_events = max_events
+        self.max_pv = max_pv_per_event
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pvf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_outputs(self, n_events: int):
+        import torch
+        z = torch.empty((n_events, self.max_pv), dtype=torch.float32, device=self.device)
+        c = torch.empty((n_events,), dtype=torch.int32, device=self.device)
+        return z, c
+
+    def infer(self, features, offsets, n_events=None, out=None, hist=None, logit=None, stream=None):
+        """features CUDA float32 [9, n_tracks]; offsets CUDA int32 [n_events + 1].
+        Returns (pv_z [n, max_pv], pv_count [n]); enqueued on the current stream."""
+        n = int(offsets.numel() - 1) if n_events is None else int(n_events)
+        z, c = out if out is not None else self.alloc_outputs(n)
+        tr = tracks_struct(features)
+        _check(self.lib.pvf_infer_ex(self.handle, ctypes.byref(tr), offsets.data_ptr(), n,
+                                     z.data_ptr(), c.data_ptr(),
+                                     hist.data_ptr() if hist is not None else None,
+                                     logit.data_ptr() if logit is not None else None,
+                                     _stream_ptr(stream)), "pvf_infer_ex")
+        return z, c
+
+    def stage_histogram(self, features, offsets, out_hist, stream=None):
+        tr = tracks_struct(features)
+        n = int(offsets.numel() - 1)
+        _check(self.lib.pvf_stage_histogram(self.handle, ctypes.byref(tr), offsets.data_ptr(), n,
+                                            out_hist.data_ptr(), _stream_ptr(stream)),
+               "pvf_stage_histogram")
+        return out_hist
+
+    def stage_unet(self, hist, out_logit, stream=None):
+        n = int(hist.shape[0])
+        _check(self.lib.pvf_stage_unet(self.handle, hist.data_ptr(), n, out_logit.data_ptr(),
+                                       _stream_ptr(stream)), "pvf_stage_unet")
+        return out_logit
+
+    def stage_peaks(self, logit, out=None, stream=None):
+        n = int(logit.shape[0])
+        z, c = out if out is not None else self.alloc_outputs(n)
+        _check(self.lib.pvf_stage_peaks(self.handle, logit.data_ptr(), n, z.data_ptr(), c.data_ptr(),
+                                        _stream_ptr(stream)), "pvf_stage_peaks")
+        return z, c
+
+    def profile_enable(self, on: bool = True):
+        _check(self.lib.pvf_profile_enable(self.handle, 1 if on else 0), "pvf_profile_enable")
+
+    def profile_read(self, stream=None) -> dict:
+        """{kernel family: (launches, total_ms)} since the last read (synchronises)."""
+        buf = (PvfKernelTime * 64)()
+        n = ctypes.c_int32(0)
+        _check(self.lib.pvf_profile_read(self.handle, buf, 64, ctypes.byref(n), _stream_ptr(stream)),
+               "pvf_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+    def device_status(self, stream=None) -> int:
+        v = ctypes.c_int32(0)
+        _check(self.lib.pvf_last_device_status(self.handle, ctypes.byref(v), _stream_ptr(stream)),
+               "pvf_last_device_status")
+        return int(v.value)

@@ -1,0 +1,102 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every symbol that
+include/pvf.h declares, and rejects bad arguments on the host before any CUDA call."""
+
+import ctypes
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2602_19959_gb300 import builder, pvf as P, weights as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    builder.build()
+    return P.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pvf.h")).read()
+    return sorted(set(re.findall(r"PVF_API\s+[\w\s\*]+?\b(pvf_\w+)\s*\(", src)))
+
+
+def test_header_declares_expected_api():
+    syms = declared_symbols()
+    for s in ("pvf_create", "pvf_infer", "pvf_destroy", "pvf_pool_bytes_required",
+              "pvf_status_str", "pvf_last_device_status"):
+        assert s in syms
+    assert set(syms) == set(P.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_status_strings(lib):
+    assert lib.pvf_status_str(0) == b"ok"
+    assert b"pool" in lib.pvf_status_str(2)
+    assert lib.pvf_status_str(12345)
+    assert lib.pvf_version() >> 16 >= 1
+
+
+def test_pool_bytes_required_and_config_validation(lib):
+    fp32 = P.pool_bytes_required(precision="fp32", max_events=1000)
+    bf16 = P.pool_bytes_required(precision="bf16", max_events=1000)
+    fp8 = P.pool_bytes_required(precision="fp8", max_events=1000)
+    assert fp32 > bf16 > fp8 > 0
+    assert fp32 < 2 * 1024 ** 3                      # the 1000-event plan fits a 2 GB pool
+    chunked = P.pool_bytes_required(precision="fp32", max_events=1000, chunk_events=100)
+    assert chunked < fp32 / 5
+    for bad in (dict(max_events=0), dict(max_tracks_per_event=0), dict(max_tracks_per_event=9000),
+                dict(max_pv_per_event=0), dict(chunk_events=-1), dict(precision=7)):
+        kw = dict(precision="fp32", max_events=10)
+        kw.update(bad)
+        cfg, _ = P.make_config(**kw)
+        out = ctypes.c_size_t(0)
+        assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_arguments_without_cuda(lib):
+    cfg, _ = P.make_config(precision="fp32", max_events=4)
+    h = ctypes.c_void_p()
+    blob = W.pack_blob(synth.he_weights(0))
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    # null pool, misaligned pool: rejected before any CUDA call
+    assert lib.pvf_create(buf, len(blob), None, 1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+    assert lib.pvf_create(buf, len(blob), 0x1001, 1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+    # corrupted blob
+    bad = bytearray(blob)
+    bad[0:4] = b"XXXX"
+    bbuf = ctypes.create_string_buffer(bytes(bad), len(bad))
+    assert lib.pvf_create(bbuf, len(bad), 0x10000, 1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == 3
+    # truncated blob
+    assert lib.pvf_create(buf, 100, 0x10000, 1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == 3
+    # pool too small
+    assert lib.pvf_create(buf, len(blob), 0x10000, 1024, ctypes.byref(cfg), None, ctypes.byref(h)) == 2
+    # non-finite weight
+    wd = synth.he_weights(0)
+    wd["dec3"][0][0, 0, 0] = np.nan
+    nb = W.pack_blob(wd)
+    nbuf = ctypes.create_string_buffer(nb, len(nb))
+    assert lib.pvf_create(nbuf, len(nb), 0x10000, 1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == 3
+    # infer with a null handle
+    assert lib.pvf_infer(None, None, None, 1, None, None, None) == 1
+    assert lib.pvf_destroy(None) == 0
+
+
+def test_blob_layout():
+    blob = W.pack_blob(synth.he_weights(0))
+    magic, ver, c0, hid, out, nl, r0, r1 = struct.unpack_from("<4s7I", blob, 0)
+    assert (magic, ver, c0, hid, out, nl) == (b"PVFW", 1, 16, 32, 100, 17)
+    name, ndim, s0, s1, s2, nb, _, wo, bo = struct.unpack_from("<8s6IQQ", blob, 32 + 48 * 11)
+    assert name.rstrip(b"\0") == b"dec3" and (ndim, s0, s1, s2, nb) == (3, 64, 128, 5, 64)
+    w = np.frombuffer(blob, dtype="<f4", count=64 * 128 * 5, offset=wo).reshape(64, 128, 5)
+    np.testing.assert_array_equal(w, synth.he_weights(0)["dec3"][0])
+    assert wo % 16 == 0 and bo % 16 == 0
