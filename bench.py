@@ -182,19 +182,22 @@ def workload_config(args, dtype):
                         f"(~155 tracks/event, Poisson 5.6 PVs), 4000-bin histogram, "
                         f"16/32/64/128 UNet, {dtype}",
             "events_per_gpu": args.events, "bins": 4000, "max_pv_per_event": args.max_pv,
-            "l2": "flushed between steps (512 MB write)", "form": args.precision}
+            "l2": f"flushed between steps ({args.flush_mb} MB write)" if args.flush_mb >= 256
+                  else "not flushed (profiling run)", "form": args.precision}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--events", type=int, default=N_EVENTS)
-    ap.add_argument("--max-pv", type=int, default=256)
+    ap.add_argument("--max-pv", type=int, default=672)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512,
+                    help="L2 flush buffer written between steps (0: none, for small profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -229,7 +232,7 @@ def main():
     z, c = pv.alloc_outputs(args.events)
     z_h = torch.empty(z.shape, dtype=z.dtype).pin_memory()
     c_h = torch.empty(c.shape, dtype=c.dtype).pin_memory()
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def step_device():
         pv.infer(feats, offs, out=(z, c))

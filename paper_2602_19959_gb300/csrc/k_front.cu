@@ -108,10 +108,13 @@ __device__ __forceinline__ int slice_of(float z) {
     return (int)floorf(q);
 }
 
+// Stores the 16 channels of storage row `row` of event e: channel-last float32 rows for
+// the FP32 form, plane-major rows (two bf16 planes / one e4m3 plane) otherwise.
 template <class T>
-__device__ __forceinline__ void store_row16(T *dst, const float v[kC0], float inv_scale) {
+__device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_e, int64_t row,
+                                            const float v[kC0], float inv_scale) {
     if constexpr (sizeof(T) == 4) {
-        float4 *d = reinterpret_cast<float4 *>(dst);
+        float4 *d = reinterpret_cast<float4 *>(reinterpret_cast<float *>(base) + (e * rows_e + row) * kC0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     } else if constexpr (sizeof(T) == 2) {
@@ -119,24 +122,25 @@ __device__ __forceinline__ void store_row16(T *dst, const float v[kC0], float in
         __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(pk);
 #pragma unroll
         for (int i = 0; i < 8; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        uint4 *d = reinterpret_cast<uint4 *>(dst);
-        d[0] = pk[0];
-        d[1] = pk[1];
+        unsigned char *cb = reinterpret_cast<unsigned char *>(base);
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)) = pk[0];
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 1, 2, rows_e, row)) = pk[1];
     } else {
         uint4 pk;
         __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv_scale);
-        *reinterpret_cast<uint4 *>(dst) = pk;
+        unsigned char *cb = reinterpret_cast<unsigned char *>(base);
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 1, rows_e, row)) = pk;
     }
 }
 
 template <class T>
-__device__ __forceinline__ void zero_row16(T *dst) {
+__device__ __forceinline__ void zero_row16(void *base, int64_t e, int64_t rows_e, int64_t row) {
     float z[kC0];
 #pragma unroll
     for (int i = 0; i < kC0; ++i) z[i] = 0.0f;
-    store_row16<T>(dst, z, 1.0f);
+    store_row16<T>(base, e, rows_e, row, z, 1.0f);
 }
 
 template <int PREC>
@@ -254,8 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     }
 
     // ---- f. e1 = LeakyReLU(conv_k5(hist) + b), p1 = maxpool2(e1)
-    T *e1 = reinterpret_cast<T *>(a.e1) + (size_t)e * padded_rows(kBins) * kC0;
-    T *p1 = reinterpret_cast<T *>(a.p1) + (size_t)e * padded_rows(kBins / 2) * kC0;
+    const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
     for (int q = tid; q < kBins / 2; q += kThreads) {
         float hv[6];
@@ -277,15 +280,15 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
             v1[co] = leaky(a1);
             vp[co] = fmaxf(v0[co], v1[co]);
         }
-        store_row16<T>(e1 + (size_t)(2 * q + kPad) * kC0, v0, inv);
-        store_row16<T>(e1 + (size_t)(2 * q + 1 + kPad) * kC0, v1, inv);
-        store_row16<T>(p1 + (size_t)(q + kPad) * kC0, vp, inv);
+        store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
+        store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
+        store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
     }
     if (tid < 4) {
         const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3
-        zero_row16<T>(e1 + (size_t)r * kC0);
+        zero_row16<T>(a.e1, e, rows1, r);
         const int rp = tid < 2 ? tid : kBins / 2 + tid;
-        zero_row16<T>(p1 + (size_t)rp * kC0);
+        zero_row16<T>(a.p1, e, rows2, rp);
     }
 }
 

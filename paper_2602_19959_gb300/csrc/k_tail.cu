@@ -24,18 +24,23 @@ constexpr int kPerThread = 16;    // kThreads * kPerThread >= kBins
 // ln(0.01 / 0.99) rounded to float
 constexpr float kThrLogit = -4.59511985013459f;
 
+// Loads the 16 channels of storage row `row` of event e (layouts as in the front kernel:
+// channel-last float32, or plane-major bf16 / e4m3).
 template <class T>
-__device__ __forceinline__ void load_row16(const T *src, float v[kC0], float scale) {
+__device__ __forceinline__ void load_row16(const void *base, int64_t e, int64_t rows_e, int64_t row,
+                                           float v[kC0], float scale) {
     if constexpr (sizeof(T) == 4) {
-        const float4 *s = reinterpret_cast<const float4 *>(src);
+        const float4 *s = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(base) +
+                                                           (e * rows_e + row) * kC0);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float4 x = s[i];
             v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
         }
     } else if constexpr (sizeof(T) == 2) {
-        const uint4 *s = reinterpret_cast<const uint4 *>(src);
-        uint4 pk[2] = {s[0], s[1]};
+        const unsigned char *cb = reinterpret_cast<const unsigned char *>(base);
+        uint4 pk[2] = {*reinterpret_cast<const uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)),
+                       *reinterpret_cast<const uint4 *>(cb + planar_off(e, 1, 2, rows_e, row))};
         const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(pk);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -43,7 +48,8 @@ __device__ __forceinline__ void load_row16(const T *src, float v[kC0], float sca
             v[2 * i] = f.x; v[2 * i + 1] = f.y;
         }
     } else {
-        uint4 pk = *reinterpret_cast<const uint4 *>(src);
+        const unsigned char *cb = reinterpret_cast<const unsigned char *>(base);
+        uint4 pk = *reinterpret_cast<const uint4 *>(cb + planar_off(e, 0, 1, rows_e, row));
         const __nv_fp8_e4m3 *b = reinterpret_cast<const __nv_fp8_e4m3 *>(&pk);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = float(b[i]) * scale;
@@ -69,13 +75,13 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
     } else {
         for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
         __syncthreads();
-        const T *d = reinterpret_cast<const T *>(a.d1) + (size_t)e * padded_rows(kBins) * kC0;
+        const int64_t rows1 = padded_rows(kBins);
         for (int p = tid; p < kBins; p += kThreads) {
             float acc = sw[5 * kC0];
 #pragma unroll
             for (int t = 0; t < 5; ++t) {
                 float v[kC0];
-                load_row16<T>(d + (size_t)(p + t) * kC0, v, a.d1_scale);   // storage row p + t = position p + t - 2
+                load_row16<T>(a.d1, e, rows1, p + t, v, a.d1_scale);   // storage row p + t = position p + t - 2
 #pragma unroll
                 for (int ci = 0; ci < kC0; ++ci) acc = fmaf(sw[t * kC0 + ci], v[ci], acc);
             }

@@ -1,16 +1,599 @@
-// Tensor-core (tcgen05) forms of the UNet: placeholder until the kernels land.
+// Step 3 of the path (§2, UNet-style 1D CNN) on the fifth-generation tensor cores:
+// every k5 convolution is an implicit GEMM over channels, M = 128 positions of one
+// event, N = C_out, K = 5 taps x C_in, issued as tcgen05.mma with the accumulator in
+// TMEM. The paper projects the gain of tensor cores and reduced precision (§5, Table 2);
+// here they are the BF16 and FP8 (E4M3) forms.
+//
+// Kernel families (each a persistent, warp-specialised kernel):
+//   enc2      conv 16->32  @2000, epilogue also writes the 2:1 max-pool
+//   enc3      conv 32->64  @1000, + pool
+//   enc4_up3  conv 64->128 @500,  epilogue feeds a second GEMM: ConvT 128->64 (k2 s2)
+//   dec3_up2  conv [64|64]->64 @1000, + ConvT 64->32
+//   dec2_up1  conv [32|32]->32 @2000, + ConvT 32->16
+//   dec1      conv [16|16]->16 @4000
+// The skip concat is never materialised: the two inputs are copied into adjacent
+// K-planes of the same shared-memory tile. Every conv and ConvT output goes through
+// LeakyReLU(0.01) in the epilogue; the fused ConvT reads the conv tile from shared
+// memory, so the deepest level's activations (e4, d3, d2) never reach global memory.
+//
+// Warp roles (192 threads): warp 0 issues the bulk copies (weights once, then one halo'd
+// activation tile per 128 positions into a 2-stage ring); warp 1 allocates TMEM and one
+// thread issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the
+// MMAs of tile i + 1); warps 2-5 are the epilogue, one TMEM lane (= output position) per
+// thread. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
+// drains its own copies and MMAs, frees TMEM and returns.
 #include "pvf_tc.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 
 namespace pvf {
+namespace {
 
-size_t tc_weight_bytes(int) { return 0; }
-bool tc_supported(int) { return false; }
-bool tc_pack_weights(int, const std::vector<LayerF32> &, const float *, std::vector<unsigned char> &,
-                     TcNet *, unsigned char *) {
-    return false;
+using namespace tc;
+
+constexpr int kTileM = 128;
+constexpr int kStages = 2;
+constexpr int kThreadsTc = 192;
+
+enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2 };
+
+__host__ __device__ constexpr int pow2ceil(int x) {
+    int p = 32;
+    while (p < x) p <<= 1;
+    return p;
 }
-cudaError_t launch_unet_tc(const TcNet &, const UnetBuffers &, int, cudaStream_t, const ProfHook *) {
-    return cudaErrorNotSupported;
+__host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_>
+struct Cfg {
+    static constexpr int PREC = PREC_;
+    static constexpr int ES = PREC == PVF_BF16 ? 2 : 1;      // bytes per element
+    static constexpr int PW = 16 / ES;                       // channels per 16-byte plane row
+    static constexpr int CA = CA_, CB = CB_, CIN = CA_ + CB_, COUT = COUT_, L = L_, EPI = EPI_;
+    static constexpr int CUP = CUP_;
+    static constexpr int PA = CA / PW, PB = CB / PW, PIN = PA + PB, POUT = COUT / PW;
+    // A single input plane is half an MMA's K (32 bytes): pair taps (2j, 2j+1) in one MMA
+    // by pointing the K-adjacent core matrix at the next row; a 6th zero tap pads.
+    static constexpr bool PAIR = PIN == 1;
+    static constexpr int TAPS = PAIR ? 6 : 5;
+    static constexpr int ROWS = kTileM + TAPS - 1;           // halo'd tile rows
+    static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
+    static constexpr int TPE = (L + kTileM - 1) / kTileM;    // tiles per event
+    static constexpr int A_STAGE = align_up(PIN * ROWS * 16, 128);
+    static constexpr int W_BYTES = TAPS * PIN * COUT * 16;
+    static constexpr int N2 = EPI == EPI_UP ? 2 * CUP : 0;   // fused ConvT: n = r * CUP + co
+    static constexpr int P2 = COUT / PW;                     // K-planes of the fused GEMM
+    static constexpr int W2_BYTES = EPI == EPI_UP ? P2 * N2 * 16 : 0;
+    static constexpr int A2_BYTES = EPI == EPI_UP ? P2 * kTileM * 16 : 0;
+    static constexpr int COLS_BUF = COUT + N2;
+    static constexpr int TMEM_COLS = pow2ceil(2 * COLS_BUF);
+    static constexpr int OFF_W = 0;
+    static constexpr int OFF_W2 = align_up(OFF_W + W_BYTES, 128);
+    static constexpr int OFF_A = align_up(OFF_W2 + W2_BYTES, 128);
+    static constexpr int OFF_A2 = OFF_A + kStages * A_STAGE;
+    static constexpr int OFF_BAR = align_up(OFF_A2 + 2 * A2_BYTES, 128);
+    static constexpr int SMEM = OFF_BAR + 256;
+    static constexpr uint32_t FMT = PREC == PVF_BF16 ? 1u : 0u;
+    static constexpr uint32_t IDESC1 = idesc_f32acc(kTileM, COUT, FMT);
+    static constexpr uint32_t IDESC2 = idesc_f32acc(kTileM, N2 > 0 ? N2 : 16, FMT);
+    static_assert(COUT % 16 == 0 && COUT <= 256, "MMA N");
+    static_assert(N2 % 16 == 0 && N2 <= 256, "MMA N of the fused GEMM");
+    static_assert(PIN % 2 == 0 || PAIR, "K planes come in pairs");
+    static_assert(EPI != EPI_UP || P2 % 2 == 0, "fused GEMM K planes come in pairs");
+    static_assert(TMEM_COLS <= 512, "TMEM columns");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(COUT % 16 == 0 && CUP % 16 == 0 || EPI != EPI_UP, "16-column epilogue chunks");
+};
+
+struct TcArgs {
+    const unsigned char *inA, *inB;     // plane-major inputs (inB: skip half of the concat)
+    unsigned char *out, *outp;          // conv or ConvT output; pooled output
+    const unsigned char *w, *w2;        // packed weights (shared-memory image)
+    const float *bias, *bias2;          // float32 biases
+    const float *cs, *cs2;              // fp8: per-column dequantisation scales; bf16: null
+    float out_inv, mid_inv;             // fp8: 1 / scale of the stored output and of A2
+    int n_events;
+    int32_t *status;
+};
+
+// Quantises 16 values to the form's element type and stores them as 16 / PW plane rows.
+template <int ES>
+__device__ __forceinline__ void put16(unsigned char *p0, size_t plane_stride, const float (&v)[16],
+                                      float inv) {
+    if constexpr (ES == 2) {
+        uint4 pk[2];
+        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        *reinterpret_cast<uint4 *>(p0) = pk[0];
+        *reinterpret_cast<uint4 *>(p0 + plane_stride) = pk[1];
+    } else {
+        uint4 pk;
+        __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv);
+        *reinterpret_cast<uint4 *>(p0) = pk;
+    }
+}
+
+__device__ __forceinline__ void zero_planes(unsigned char *base, int64_t e, int planes, int64_t rows_e,
+                                            int64_t row) {
+    for (int k = 0; k < planes; ++k)
+        *reinterpret_cast<uint4 *>(base + planar_off(e, k, planes, rows_e, row)) = make_uint4(0, 0, 0, 0);
+}
+
+template <class C>
+__device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, volatile int *abort) {
+    uint64_t *wbar = bar, *full = bar + 1, *empty = bar + 3;
+    const int ntiles = a.n_events * C::TPE;
+    mbar_arrive_expect_tx(wbar, C::W_BYTES + C::W2_BYTES);
+    bulk_g2s(smem + C::OFF_W, a.w, C::W_BYTES, wbar);
+    if (C::W2_BYTES) bulk_g2s(smem + C::OFF_W2, a.w2, C::W2_BYTES, wbar);
+    int i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % kStages;
+        const uint32_t ph = (i / kStages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
+        const int e = t / C::TPE, p0 = (t % C::TPE) * kTileM;
+        const int rows = min(C::ROWS, C::ROWS_E - p0);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(C::PIN * rows * 16));
+        unsigned char *dst = smem + C::OFF_A + s * C::A_STAGE;
+        for (int k = 0; k < C::PA; ++k)
+            bulk_g2s(dst + k * C::ROWS * 16, a.inA + planar_off(e, k, C::PA, C::ROWS_E, p0), rows * 16, &full[s]);
+        for (int k = 0; k < C::PB; ++k)
+            bulk_g2s(dst + (C::PA + k) * C::ROWS * 16, a.inB + planar_off(e, k, C::PB, C::ROWS_E, p0),
+                     rows * 16, &full[s]);
+    }
+    // copies still in flight land before the CTA can exit: wait (bounded) for the last ones
+    for (int j = max(0, i - kStages); j < i; ++j) {
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&full[j % kStages], (j / kStages) & 1))
+            if (globaltimer() - t0 > kWaitLimitNs) break;
+    }
+    if (!mbar_try_wait(wbar, 0)) {
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(wbar, 0)) if (globaltimer() - t0 > kWaitLimitNs) break;
+    }
+    return ok;
+}
+
+template <class C>
+__device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
+                           volatile int *abort) {
+    uint64_t *wbar = bar, *full = bar + 1, *empty = bar + 3, *tfull = bar + 5, *tempty = bar + 7,
+             *a2full = bar + 9, *t2full = bar + 11, *drain = bar + 13;
+    const int ntiles = a.n_events * C::TPE;
+    bool ok = mbar_wait(wbar, 0, abort);
+    tc_fence_after();
+    const uint32_t a_base = smem_u32(smem + C::OFF_A);
+    const uint32_t w_base = smem_u32(smem + C::OFF_W);
+    const uint32_t w2_base = smem_u32(smem + C::OFF_W2);
+    const uint32_t a2_base = smem_u32(smem + C::OFF_A2);
+    int i = 0;
+    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+        const int s = i % kStages, b = i & 1;
+        const uint32_t ph_s = (i / kStages) & 1, ph_b = (i >> 1) & 1;
+        if (!mbar_wait(&tempty[b], ph_b ^ 1, abort) || !mbar_wait(&full[s], ph_s, abort)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + b * C::COLS_BUF;
+        const uint32_t as = a_base + s * C::A_STAGE;
+        if constexpr (C::PAIR) {
+#pragma unroll
+            for (int j = 0; j < C::TAPS / 2; ++j) {
+                const uint64_t ad = smem_desc(as + 2 * j * 16, 16, 128);
+                const uint64_t bd = smem_desc(w_base + 2 * j * C::COUT * 16, C::COUT * 16, 128);
+                if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, j != 0);
+                else mma_fp8(d, ad, bd, C::IDESC1, j != 0);
+            }
+        } else {
+#pragma unroll
+            for (int tap = 0; tap < 5; ++tap)
+#pragma unroll
+                for (int kb = 0; kb < C::PIN / 2; ++kb) {
+                    const uint64_t ad = smem_desc(as + 2 * kb * C::ROWS * 16 + tap * 16, C::ROWS * 16, 128);
+                    const uint64_t bd = smem_desc(w_base + (tap * C::PIN + 2 * kb) * C::COUT * 16,
+                                                  C::COUT * 16, 128);
+                    if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, (tap | kb) != 0);
+                    else mma_fp8(d, ad, bd, C::IDESC1, (tap | kb) != 0);
+                }
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&tfull[b]);
+        if constexpr (C::EPI == EPI_UP) {
+            if (!mbar_wait(&a2full[b], ph_b, abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a2 = a2_base + b * C::A2_BYTES;
+#pragma unroll
+            for (int kb = 0; kb < C::P2 / 2; ++kb) {
+                const uint64_t ad = smem_desc(a2 + 2 * kb * kTileM * 16, kTileM * 16, 128);
+                const uint64_t bd = smem_desc(w2_base + 2 * kb * C::N2 * 16, C::N2 * 16, 128);
+                if constexpr (C::PREC == PVF_BF16) mma_bf16(d + C::COUT, ad, bd, C::IDESC2, kb != 0);
+                else mma_fp8(d + C::COUT, ad, bd, C::IDESC2, kb != 0);
+            }
+            mma_commit(&t2full[b]);
+        }
+    }
+    // every MMA issued above completes before TMEM is released
+    mma_commit(drain);
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(drain, 0)) if (globaltimer() - t0 > kWaitLimitNs) break;
+    return ok;
+}
+
+template <class C>
+__device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
+                         volatile int *abort, int warp, int lane) {
+    uint64_t *tfull = bar + 5, *tempty = bar + 7, *a2full = bar + 9, *t2full = bar + 11;
+    constexpr int ES = C::ES;
+    const int q = warp & 3;                         // TMEM lane quarter of this warp
+    const int m = q * 32 + lane;                    // tile row = output position - p0
+    const uint32_t lane_field = (uint32_t)(q * 32) << 16;
+    const int ntiles = a.n_events * C::TPE;
+    constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
+    constexpr int LO = 2 * C::L;                    // ConvT output length
+    constexpr int64_t ROWS_O = LO + 2 * kPad;
+    constexpr int PUP = C::CUP / C::PW;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        const uint32_t ph_b = (i >> 1) & 1;
+        const int e = t / C::TPE, p0 = (t % C::TPE) * kTileM;
+        const int p = p0 + m;
+        const bool valid = p < C::L;
+        if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
+        tc_fence_after();
+        const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
+#pragma unroll 1
+        for (int c0 = 0; c0 < C::COUT; c0 += 16) {
+            float v[16];
+            tmem_ld16(dcol + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float sc = C::PREC == PVF_BF16 ? 1.0f : __ldg(a.cs + c0 + j);
+                v[j] = leaky(fmaf(v[j], sc, __ldg(a.bias + c0 + j)));
+            }
+            if constexpr (C::EPI == EPI_UP) {
+                unsigned char *a2 = smem + C::OFF_A2 + b * C::A2_BYTES;
+                put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
+            } else {
+                if (valid)
+                    put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
+                              (size_t)C::ROWS_E * 16, v, a.out_inv);
+                if constexpr (C::EPI == EPI_POOL) {
+                    float w[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                    if (valid && (m & 1) == 0)
+                        put16<ES>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
+                                  (size_t)ROWS_P * 16, w, a.out_inv);
+                }
+            }
+        }
+        if constexpr (C::EPI != EPI_UP) {
+            if (p == 0) {
+                zero_planes(a.out, e, C::POUT, C::ROWS_E, 0);
+                zero_planes(a.out, e, C::POUT, C::ROWS_E, 1);
+                if constexpr (C::EPI == EPI_POOL) {
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, 0);
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, 1);
+                }
+            }
+            if (p == C::L - 1) {
+                zero_planes(a.out, e, C::POUT, C::ROWS_E, C::L + kPad);
+                zero_planes(a.out, e, C::POUT, C::ROWS_E, C::L + kPad + 1);
+                if constexpr (C::EPI == EPI_POOL) {
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, C::L / 2 + kPad);
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, C::L / 2 + kPad + 1);
+                }
+            }
+        } else {
+            fence_proxy_async_smem();               // A2 writes -> visible to the tensor core
+            mbar_arrive(&a2full[b]);
+            if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c0 = 0; c0 < C::N2; c0 += 16) {
+                float v[16];
+                tmem_ld16(dcol + C::COUT + c0, v);
+                const int r = c0 / C::CUP, co0 = c0 % C::CUP;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float sc = C::PREC == PVF_BF16 ? 1.0f : __ldg(a.cs2 + c0 + j);
+                    v[j] = leaky(fmaf(v[j], sc, __ldg(a.bias2 + co0 + j)));
+                }
+                if (valid)
+                    put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
+                              (size_t)ROWS_O * 16, v, a.out_inv);
+            }
+            if (p == 0) {
+                zero_planes(a.out, e, PUP, ROWS_O, 0);
+                zero_planes(a.out, e, PUP, ROWS_O, 1);
+            }
+            if (p == C::L - 1) {
+                zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
+                zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
+            }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[b]);
+    }
+    return true;
+}
+
+template <class C>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_conv_tc(TcArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    // bar: 0 weights | 1,2 full | 3,4 empty | 5,6 tmem full | 7,8 tmem empty |
+    //      9,10 A2 full | 11,12 second accumulator full | 13 drain
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 16);
+    volatile int *abort = reinterpret_cast<volatile int *>(bar + 17);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&bar[1 + s], 1);
+            mbar_init(&bar[3 + s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar[5 + b], 1);
+            mbar_init(&bar[7 + b], 128);
+            mbar_init(&bar[9 + b], 128);
+            mbar_init(&bar[11 + b], 1);
+        }
+        mbar_init(&bar[13], 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) ok = producer<C>(a, smem, bar, abort);
+    } else if (warp == 1) {
+        if (lane == 0) ok = mma_issuer<C>(a, smem, bar, tmem, abort);
+    } else {
+        ok = epilogue<C>(a, smem, bar, tmem, abort, warp, lane);
+    }
+    if (!ok) {
+        *abort = 1;
+        raise_status(a.status, PVF_ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <class C>
+cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, const char *name) {
+    if (a.n_events <= 0) return cudaSuccess;
+    // shared memory request padded so that the CTAs resident on one SM never ask for more
+    // than the 512 TMEM columns: tcgen05.alloc would otherwise wait for a neighbour
+    constexpr int kMaxByTmem = 512 / C::TMEM_COLS;
+    constexpr int kSmemPerSm = 228 * 1024;
+    int smem = C::SMEM;
+    const int by_tmem_smem = kSmemPerSm / kMaxByTmem - 1024;
+    if (smem < by_tmem_smem) smem = by_tmem_smem;
+    if (smem > 227 * 1024) smem = 227 * 1024;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(k_conv_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<C>, kThreadsTc, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (per_sm > kMaxByTmem) per_sm = kMaxByTmem;
+    const int ntiles = a.n_events * C::TPE;
+    int grid = sm_count() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    ProfScope ps(prof, name, s);
+    k_conv_tc<C><<<grid, kThreadsTc, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- weight packing (host)
+
+template <int PREC> struct Net {
+    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0>;
+    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0>;
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64>;
+    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32>;
+    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16>;
+    using Dec1 = Cfg<PREC, 16, 16, 16, 4000, EPI_STORE, 0>;
+};
+
+// Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
+const int kBlobIndex[9] = {7, 8, 9, 11, 13, 15, 10, 12, 14};
+
+struct Packer {
+    int prec, es, pw;
+    std::vector<unsigned char> bytes;
+    size_t put_raw(const void *p, size_t n) {
+        size_t off = (bytes.size() + 127) / 128 * 128;
+        bytes.resize(off + n);
+        std::memcpy(bytes.data() + off, p, n);
+        return off;
+    }
+    void enc(float x, unsigned char *dst) const {
+        if (es == 2) {
+            __nv_bfloat16 h = __float2bfloat16_rn(x);
+            std::memcpy(dst, &h, 2);
+        } else {
+            __nv_fp8_e4m3 q(x);
+            std::memcpy(dst, &q, 1);
+        }
+    }
+};
+
+// Per-output-channel fp8 weight scale: amax over the channel / 448.
+float fp8_scale(float amax) { return amax > 0.0f ? amax / 448.0f : 1.0f; }
+
+}  // namespace
+
+size_t tc_weight_bytes(int precision) {
+    if (precision == PVF_FP32) return 0;
+    return 512 * 1024;   // packed weights (< 300 KB) + biases + fp8 column scales
+}
+
+bool tc_supported(int precision) { return precision == PVF_BF16 || precision == PVF_FP8_E4M3; }
+
+// Conv layer W[co][ci][t] -> image [tap][plane][co][PW elements] (6th tap zero when paired).
+// ConvT W[ci][co][r] -> image [plane of ci][n = r * CUP + co][PW elements].
+bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const float *act_scale,
+                     std::vector<unsigned char> &out, TcNet *net, unsigned char *dev_base) {
+    Packer pk{precision, precision == PVF_BF16 ? 2 : 1, precision == PVF_BF16 ? 8 : 16, {}};
+    net->precision = precision;
+    size_t off_w[9], off_b[9], off_s[9];
+    for (int li = 0; li < 9; ++li) {
+        const LayerF32 &Lw = layers[kBlobIndex[li]];
+        const bool up = li >= 6;
+        std::vector<unsigned char> img;
+        std::vector<float> scale;
+        int cout;
+        if (!up) {
+            cout = (int)Lw.shape[0];
+            const int cin = (int)Lw.shape[1];
+            const int pin = cin / pk.pw;
+            const bool pair = pin == 1;
+            const int taps = pair ? 6 : 5;
+            scale.assign(cout, 1.0f);
+            if (precision == PVF_FP8_E4M3)
+                for (int co = 0; co < cout; ++co) {
+                    float amax = 0.0f;
+                    for (int i = 0; i < cin * 5; ++i) amax = std::max(amax, std::fabs(Lw.w[(size_t)co * cin * 5 + i]));
+                    scale[co] = fp8_scale(amax);
+                }
+            img.assign((size_t)taps * pin * cout * 16, 0);
+            for (int t = 0; t < 5; ++t)
+                for (int k = 0; k < pin; ++k)
+                    for (int co = 0; co < cout; ++co)
+                        for (int j = 0; j < pk.pw; ++j) {
+                            const int ci = k * pk.pw + j;
+                            const float w = Lw.w[((size_t)co * cin + ci) * 5 + t] / scale[co];
+                            pk.enc(w, &img[(((size_t)t * pin + k) * cout + co) * 16 + j * pk.es]);
+                        }
+        } else {
+            const int cin = (int)Lw.shape[0];
+            const int cup = (int)Lw.shape[1];
+            const int n2 = 2 * cup;
+            cout = n2;
+            const int p2 = cin / pk.pw;
+            scale.assign(n2, 1.0f);
+            if (precision == PVF_FP8_E4M3)
+                for (int co = 0; co < cup; ++co) {
+                    float amax = 0.0f;
+                    for (int ci = 0; ci < cin; ++ci)
+                        for (int r = 0; r < 2; ++r)
+                            amax = std::max(amax, std::fabs(Lw.w[((size_t)ci * cup + co) * 2 + r]));
+                    scale[co] = scale[cup + co] = fp8_scale(amax);
+                }
+            img.assign((size_t)p2 * n2 * 16, 0);
+            for (int k = 0; k < p2; ++k)
+                for (int n = 0; n < n2; ++n)
+                    for (int j = 0; j < pk.pw; ++j) {
+                        const int ci = k * pk.pw + j, r = n / cup, co = n % cup;
+                        const float w = Lw.w[((size_t)ci * cup + co) * 2 + r] / scale[n];
+                        pk.enc(w, &img[((size_t)k * n2 + n) * 16 + j * pk.es]);
+                    }
+        }
+        off_w[li] = pk.put_raw(img.data(), img.size());
+        const size_t nbias = up ? Lw.shape[1] : Lw.shape[0];
+        off_b[li] = pk.put_raw(Lw.b, nbias * sizeof(float));
+        // fp8 dequantisation scale per accumulator column: input activation scale x weight scale
+        std::vector<float> cs(cout, 1.0f);
+        if (precision == PVF_FP8_E4M3) {
+            // scale of each layer's input tensor
+            const int in_idx[9] = {kScaleL1, kScaleL2, kScaleL3, kScaleL3, kScaleL2, kScaleL1,
+                                   kScaleE4, kScaleD3, kScaleD2};
+            for (int c = 0; c < cout; ++c) cs[c] = act_scale[in_idx[li]] * scale[c];
+        }
+        off_s[li] = pk.put_raw(cs.data(), cs.size() * sizeof(float));
+    }
+    if (pk.bytes.size() > tc_weight_bytes(precision)) return false;
+    for (int li = 0; li < 9; ++li) {
+        net->w[li] = dev_base + off_w[li];
+        net->b[li] = reinterpret_cast<const float *>(dev_base + off_b[li]);
+        net->wscale[li] = reinterpret_cast<const float *>(dev_base + off_s[li]);
+    }
+    for (int i = 0; i < PVF_N_ACT_SCALES; ++i) net->act_scale[i] = act_scale[i];
+    out.swap(pk.bytes);
+    return true;
+}
+
+template <int PREC>
+static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStream_t s,
+                          const ProfHook *prof) {
+    using N = Net<PREC>;
+    const float *sc = n.act_scale;
+    auto inv = [&](int i) { return PREC == PVF_BF16 ? 1.0f : 1.0f / sc[i]; };
+    auto cs = [&](int li) { return PREC == PVF_BF16 ? nullptr : n.wscale[li]; };
+    auto W = [&](int li) { return static_cast<const unsigned char *>(n.w[li]); };
+    auto U = [](void *p) { return static_cast<unsigned char *>(p); };
+    cudaError_t err;
+    TcArgs a{};
+    a.n_events = ne;
+    a.status = n.status;
+    // enc2: p1 (s0) -> e2, p2 (s1)
+    a.inA = U(b.s0); a.inB = nullptr; a.out = U(b.e2); a.outp = U(b.s1);
+    a.w = W(0); a.bias = n.b[0]; a.cs = cs(0); a.out_inv = inv(kScaleL2);
+    if ((err = launch_conv<typename N::Enc2>(a, s, prof, "enc2")) != cudaSuccess) return err;
+    // enc3: p2 (s1) -> e3, p3 (s0)
+    a.inA = U(b.s1); a.out = U(b.e3); a.outp = U(b.s0);
+    a.w = W(1); a.bias = n.b[1]; a.cs = cs(1); a.out_inv = inv(kScaleL3);
+    if ((err = launch_conv<typename N::Enc3>(a, s, prof, "enc3")) != cudaSuccess) return err;
+    // enc4 + up3: p3 (s0) -> u3 (up)
+    a.inA = U(b.s0); a.out = U(b.up); a.outp = nullptr;
+    a.w = W(2); a.bias = n.b[2]; a.cs = cs(2); a.w2 = W(6); a.bias2 = n.b[6]; a.cs2 = cs(6);
+    a.mid_inv = inv(kScaleE4); a.out_inv = inv(kScaleL3);
+    if ((err = launch_conv<typename N::Enc4Up3>(a, s, prof, "enc4_up3")) != cudaSuccess) return err;
+    // dec3 + up2: [u3 (up), e3] -> u2 (deep)
+    a.inA = U(b.up); a.inB = U(b.e3); a.out = U(b.deep);
+    a.w = W(3); a.bias = n.b[3]; a.cs = cs(3); a.w2 = W(7); a.bias2 = n.b[7]; a.cs2 = cs(7);
+    a.mid_inv = inv(kScaleD3); a.out_inv = inv(kScaleL2);
+    if ((err = launch_conv<typename N::Dec3Up2>(a, s, prof, "dec3_up2")) != cudaSuccess) return err;
+    // dec2 + up1: [u2 (deep), e2] -> u1 (up)
+    a.inA = U(b.deep); a.inB = U(b.e2); a.out = U(b.up);
+    a.w = W(4); a.bias = n.b[4]; a.cs = cs(4); a.w2 = W(8); a.bias2 = n.b[8]; a.cs2 = cs(8);
+    a.mid_inv = inv(kScaleD2); a.out_inv = inv(kScaleL1);
+    if ((err = launch_conv<typename N::Dec2Up1>(a, s, prof, "dec2_up1")) != cudaSuccess) return err;
+    // dec1: [u1 (up), e1] -> d1 (deep)
+    a.inA = U(b.up); a.inB = U(b.e1); a.out = U(b.deep); a.w2 = nullptr;
+    a.w = W(5); a.bias = n.b[5]; a.cs = cs(5); a.out_inv = inv(kScaleD1);
+    return launch_conv<typename N::Dec1>(a, s, prof, "dec1");
+}
+
+cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, cudaStream_t s,
+                           const ProfHook *prof) {
+    if (n <= 0) return cudaSuccess;
+    if (net.precision == PVF_BF16) return run_tc<PVF_BF16>(net, b, n, s, prof);
+    return run_tc<PVF_FP8_E4M3>(net, b, n, s, prof);
 }
 
 }  // namespace pvf

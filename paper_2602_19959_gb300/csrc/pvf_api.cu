@@ -331,6 +331,7 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
             views[i].b = layers[i].b.data();
             std::memcpy(views[i].shape, layers[i].shape, sizeof views[i].shape);
         }
+        h->tc.status = reinterpret_cast<int32_t *>(h->pool + plan.status);
         if (!tc_pack_weights(cfg->precision, views, h->act_scale, tcw, &h->tc, h->pool + plan.tcw)) {
             delete h;
             return PVF_ERR_WEIGHTS;
@@ -439,7 +440,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.hist_out = hist_out;
         a.e1 = h->buf.e1;
         a.p1 = h->buf.s0;
-        a.e1_inv_scale = 1.0f / h->act_scale[0];
+        a.e1_inv_scale = 1.0f / h->act_scale[kScaleL1];
         a.ev_flag = flags;
         a.status = status;
         err = launch_front(a, prec, h->front_smem, s);
@@ -455,7 +456,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         TailArgs t{};
         t.d1 = h->buf.deep;
         t.logit_in = logit_in;
-        t.d1_scale = h->act_scale[PVF_N_ACT_SCALES - 1];
+        t.d1_scale = h->act_scale[kScaleD1];
         t.final_w = h->fin;
         t.n_events = n;
         t.ev_base = ev_base;

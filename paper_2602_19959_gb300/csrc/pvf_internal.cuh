@@ -90,6 +90,16 @@ template <> __device__ __forceinline__ float from_elem<__nv_fp8_e4m3>(__nv_fp8_e
 // Rows per event of a padded activation tensor with L positions.
 __host__ __device__ __forceinline__ int64_t padded_rows(int L) { return (int64_t)L + 2 * kPad; }
 
+// Plane-major layout of the tensor-core forms: a tensor with C channels is stored as
+// C / PW planes of 16-byte rows (PW = 16 / element size channels per row):
+//   byte offset of (event e, plane k, storage row r) = ((e * P + k) * rows_per_event + r) * 16
+// so a plane of an event is one contiguous run of rows, which a single bulk copy moves
+// into the shared-memory operand layout of tcgen05.
+__host__ __device__ __forceinline__ size_t planar_off(int64_t e, int k, int planes, int64_t rows_e,
+                                                      int64_t row) {
+    return ((size_t)(e * planes + k) * (size_t)rows_e + (size_t)row) * 16;
+}
+
 // ---------------------------------------------------------------- kernel arguments
 
 struct FrontArgs {

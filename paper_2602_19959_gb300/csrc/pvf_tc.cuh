@@ -14,14 +14,27 @@ struct LayerF32 {
     uint32_t shape[3];
 };
 
+// FP8 per-tensor activation scales (value = stored e4m3 x scale). The two halves of a
+// skip concat feed one accumulator column, so they share a scale:
+enum {
+    kScaleL1 = 0,   // e1, p1, u1 (level 1, 16 channels)
+    kScaleL2 = 1,   // e2, p2, u2
+    kScaleL3 = 2,   // e3, p3, u3
+    kScaleE4 = 3,   // e4 (shared-memory operand of the fused up3 GEMM)
+    kScaleD3 = 4,   // d3 (operand of the fused up2 GEMM)
+    kScaleD2 = 5,   // d2 (operand of the fused up1 GEMM)
+    kScaleD1 = 6,   // d1 (input of the final conv)
+    kNumScales = 7
+};
+
 // Device pointers of the packed tensor-core weights inside the pool.
 struct TcNet {
     int precision;
     const void *w[9];        // enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1 (packed)
     const float *b[9];       // biases, float32
-    const float *wscale[9];  // fp8: per-output-channel weight scales (null for bf16)
-    float in_scale[9];       // fp8: per-tensor scale of each layer's input
-    float out_inv_scale[9];  // fp8: 1 / scale of each layer's stored output
+    const float *wscale[9];  // per-accumulator-column dequantisation scales (fp8)
+    float act_scale[PVF_N_ACT_SCALES];
+    int32_t *status;         // device status word
 };
 
 size_t tc_weight_bytes(int precision);

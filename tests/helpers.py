@@ -55,9 +55,12 @@ def z_to_bin(z: float) -> int:
 def pv_agreement(oracle_z, oracle_n, gpu_z, gpu_n, oracle_logit, eps: float, tol=0.1):
     """Agreement of PV lists, strict and with the near-tie exemption.
 
-    A PV present on one side only is exempt when the oracle's decision at some bin
-    within +-3 bins of it (its local maximum) is within eps of flipping: then either
-    list is a correct result of the same rule under rounding of size eps.
+    PVs are matched one-to-one in z order within tol. A PV present on one side only is
+    exempt when the oracle's decision at some bin within +-4 bins of it is within eps of
+    flipping (a threshold crossing or a tie with a neighbour in the +-5 window): then both
+    lists are correct results of the same rule under rounding of size eps.
+      strict = matched / total,  exempt = 1 - (non-exempt unmatched) / total,
+    with total = sum over events of max(n_oracle, n_gpu).
     Returns dict(strict, exempt, matched, total, unmatched, exempted, max_dz)."""
     matched = total = unmatched = exempted = 0
     max_dz = 0.0
@@ -66,6 +69,8 @@ def pv_agreement(oracle_z, oracle_n, gpu_z, gpu_n, oracle_logit, eps: float, tol
         if na < 0 or nb < 0:
             assert na == nb, (e, na, nb)
             continue
+        # compare the stored (possibly truncated) lists; counts are compared by the caller
+        na, nb = min(na, len(oracle_z[e])), min(nb, len(gpu_z[e]))
         za, zb = oracle_z[e][:na], gpu_z[e][:nb]
         pairs, ua, ub = match_pvs(za, zb, tol)
         matched += len(pairs)
@@ -80,6 +85,6 @@ def pv_agreement(oracle_z, oracle_n, gpu_z, gpu_n, oracle_logit, eps: float, tol
             if m < eps:
                 exempted += 1
     strict = matched / total if total else 1.0
-    exempt = (matched + exempted) / total if total else 1.0
+    exempt = max(0.0, 1.0 - (unmatched - exempted) / total) if total else 1.0
     return dict(strict=strict, exempt=exempt, matched=matched, total=total,
                 unmatched=unmatched, exempted=exempted, max_dz=max_dz)

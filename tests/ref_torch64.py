@@ -95,3 +95,37 @@ def peaks(f: np.ndarray, p: np.ndarray, thr: float = 0.01):
         lo, hi = max(0, i - 3), min(L, i + 4)
         z.append(np.dot(p[lo:hi], zc[lo:hi]) / p[lo:hi].sum())
     return bins, np.array(z)
+
+
+def unet_quantized(w: dict, hist: np.ndarray, q):
+    """The UNet in float64 with q() applied wherever the tensor-core forms store a
+    reduced-precision tensor: every GEMM operand (activations and weights), the fused
+    ConvT operands (e4, d3, d2) and d1. enc1 and the final conv keep float32 weights.
+    Used to check the kernels' wiring tightly, not as the oracle."""
+    def conv(x, name, quant_w=True):
+        W, b = w[name]
+        Wt = _t(W)
+        return F.conv1d(x, q(Wt) if quant_w else Wt, _t(b), padding=2)
+
+    def up(x, name):
+        W, b = w[name]
+        return F.leaky_relu(F.conv_transpose1d(x, q(_t(W)), _t(b), stride=2), 0.01)
+
+    lr = lambda v: F.leaky_relu(v, 0.01)
+    x = _t(hist).reshape(1, 1, -1)
+    e1 = q(lr(conv(x, "enc1", quant_w=False)))
+    e2 = q(lr(conv(F.max_pool1d(e1, 2), "enc2")))
+    e3 = q(lr(conv(F.max_pool1d(e2, 2), "enc3")))
+    e4 = q(lr(conv(F.max_pool1d(e3, 2), "enc4")))
+    u3 = q(up(e4, "up3"))
+    d3 = q(lr(conv(torch.cat([u3, e3], dim=1), "dec3")))
+    u2 = q(up(d3, "up2"))
+    d2 = q(lr(conv(torch.cat([u2, e2], dim=1), "dec2")))
+    u1 = q(up(d2, "up1"))
+    d1 = q(lr(conv(torch.cat([u1, e1], dim=1), "dec1")))
+    f = conv(d1, "final", quant_w=False).reshape(-1)
+    return f.numpy()
+
+
+def q_bf16(t):
+    return t.to(torch.bfloat16).to(torch.float64)

@@ -1,0 +1,127 @@
+"""GPU checks of the tensor-core (tcgen05) forms through the C ABI.
+
+1. Kernel wiring: the BF16 UNet against a float64 emulation that rounds to bf16 at
+   exactly the points where the kernels store bf16 (tests/ref_torch64.unet_quantized):
+   only float32-accumulation differences and the occasional one-ulp rounding flip remain.
+2. Against the FP64 oracle: per-bin error of the logits (reported and bounded) and the
+   PV-list agreement, strict and with the near-tie exemption at the measured error.
+3. Determinism and batch invariance, as for the FP32 form.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import ref_torch64 as ref
+from tests.helpers import pv_agreement, to_cuda
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+NTHREADS = os.cpu_count() or 1
+MAX_PV = 672
+
+
+@pytest.fixture(scope="module")
+def PVFinder():
+    from paper_2602_19959_gb300 import build, PVFinder
+    build()
+    return PVFinder
+
+
+@pytest.fixture(scope="module")
+def weights():
+    return synth.he_weights(0, bias_std=0.05)
+
+
+@pytest.fixture(scope="module")
+def ev16():
+    return synth.generate_standard(16, 0)
+
+
+@pytest.fixture(scope="module")
+def ref16(weights, ev16):
+    return oracle.infer(weights, ev16.features, ev16.offsets, max_pv=MAX_PV, want_hist=True,
+                        want_logit=True, nthreads=NTHREADS)
+
+
+@pytest.fixture(scope="module")
+def bf16(PVFinder, weights):
+    return PVFinder(weights, precision="bf16", max_events=64, max_pv_per_event=MAX_PV)
+
+
+def run_full(pv, batch):
+    feats, offs = to_cuda(batch)
+    n = batch.n_events
+    hist = torch.zeros((n, 4000), dtype=torch.float32, device="cuda")
+    logit = torch.zeros((n, 4000), dtype=torch.float32, device="cuda")
+    z, c = pv.infer(feats, offs, hist=hist, logit=logit)
+    torch.cuda.synchronize()
+    return dict(z=z.cpu().numpy(), count=c.cpu().numpy(), hist=hist.cpu().numpy(),
+                logit=logit.cpu().numpy())
+
+
+def test_bf16_unet_wiring_matches_quantised_emulation(bf16, weights, ref16):
+    h32 = ref16["hist"].astype(np.float32)
+    logit = torch.zeros((16, 4000), dtype=torch.float32, device="cuda")
+    bf16.stage_unet(torch.from_numpy(h32).cuda(), logit)
+    torch.cuda.synchronize()
+    f = logit.cpu().numpy().astype(np.float64)
+    for e in range(4):
+        want = ref.unet_quantized(weights, h32[e].astype(np.float64), ref.q_bf16)
+        scale = np.max(np.abs(want))
+        d = np.abs(f[e] - want) / scale
+        print(f"event {e}: median {np.median(d):.2e} p99 {np.quantile(d, 0.99):.2e} max {d.max():.2e}")
+        assert np.median(d) <= 1e-4
+        assert np.quantile(d, 0.99) <= 2e-3
+        assert d.max() <= 2e-2
+
+
+def test_bf16_histogram_is_the_fp32_histogram(bf16, ev16, ref16):
+    r = run_full(bf16, ev16)
+    for e in range(16):
+        scale = np.max(np.abs(ref16["hist"][e]))
+        assert np.max(np.abs(r["hist"][e] - ref16["hist"][e])) <= 1e-4 * scale
+
+
+def test_bf16_against_oracle(bf16, ev16, ref16):
+    r = run_full(bf16, ev16)
+    rel = [np.max(np.abs(r["logit"][e] - ref16["logit"][e])) / np.max(np.abs(ref16["logit"][e]))
+           for e in range(16)]
+    prob_err = np.max(np.abs(1 / (1 + np.exp(-r["logit"].astype(np.float64))) -
+                             1 / (1 + np.exp(-ref16["logit"]))))
+    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    print("bf16 per-bin logit err / max:", max(rel), "prob err:", prob_err, "agreement:", a)
+    assert max(rel) <= 0.05
+    assert a["max_dz"] <= 0.1
+    assert a["exempt"] >= 0.999
+
+
+def test_bf16_deterministic_and_batch_invariant(bf16, ev16):
+    r1 = run_full(bf16, ev16)
+    r2 = run_full(bf16, ev16)
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(r1[k], r2[k])
+    rs = run_full(bf16, ev16.subset(3, 7))
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(rs[k], r1[k][3:7])
+    rev = synth.concat_batches([ev16.subset(e, e + 1) for e in range(15, -1, -1)])
+    rr = run_full(bf16, rev)
+    np.testing.assert_array_equal(rr["logit"][::-1], r1["logit"])
+
+
+def test_bf16_full_size_sampled(PVFinder, weights):
+    b = synth.generate_standard(1000, 1)
+    pv = PVFinder(weights, precision="bf16", max_events=1000, max_pv_per_event=MAX_PV)
+    r = run_full(pv, b)
+    assert pv.device_status() == 0
+    sample = [0, 999]
+    sb = synth.concat_batches([b.subset(e, e + 1) for e in sample])
+    rr = oracle.infer(weights, sb.features, sb.offsets, max_pv=MAX_PV, want_logit=True,
+                      nthreads=NTHREADS)
+    for i, e in enumerate(sample):
+        assert np.max(np.abs(r["logit"][e] - rr["logit"][i])) <= 0.05 * np.max(np.abs(rr["logit"][i]))
+    assert np.all(r["count"] >= 0)
