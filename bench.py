@@ -35,20 +35,70 @@ sys.path.insert(0, ROOT)
 
 N_EVENTS = 1000
 FC_MAC_PER_TRACK = 9 * 32 + 4 * 32 * 32 + 32 * 100
-# multiply-accumulates per event of each UNet layer (M x N x K of the implicit GEMMs)
-LAYER_MAC = {
-    "enc1": 4000 * 16 * 5, "enc2": 2000 * 32 * 80, "enc3": 1000 * 64 * 160,
-    "enc4": 500 * 128 * 320, "up3": 500 * 128 * 128, "dec3": 1000 * 64 * 640,
-    "up2": 1000 * 64 * 64, "dec2": 2000 * 32 * 320, "up1": 2000 * 32 * 32,
-    "dec1": 4000 * 16 * 160, "final": 4000 * 1 * 80,
-}
-# which layers each kernel family computes
-FAMILY_LAYERS = {
-    "front": ["enc1"], "enc2": ["enc2"], "enc3": ["enc3"], "enc4": ["enc4"], "up3": ["up3"],
-    "dec3": ["dec3"], "up2": ["up2"], "dec2": ["dec2"], "up1": ["up1"], "dec1": ["dec1"],
-    "tail": ["final"], "enc4_up3": ["enc4", "up3"], "dec3_up2": ["dec3", "up2"],
-    "dec2_up1": ["dec2", "up1"],
-}
+
+
+def conv_io(L, cin, cout, pool=False, concat=False):
+    """(MAC, activation elements read, written) per event of a k5 conv layer."""
+    rd = cin * (L + 4)
+    wr = cout * (L + 4) + (cout * (L // 2 + 4) if pool else 0)
+    return L * cout * cin * 5, rd, wr
+
+
+def convT_io(L, cin, cout):
+    return L * 2 * cout * cin, cin * (L + 4), cout * (2 * L + 4)
+
+
+def kernel_table(form):
+    """Algorithmic work per event of each kernel family: (MAC, bytes, compute unit).
+    MACs of the FC depend on the track count and are added by the caller."""
+    es = {"fp32": 4, "bf16": 2, "fp8": 1}[form]
+    t = {}
+    e1 = 16 * 4004 + 16 * 2004               # e1 and p1 written by the front kernel
+    t["front"] = (4000 * 16 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
+    m, r, w = conv_io(2000, 16, 32, pool=True); t["enc2"] = (m, 0, (r + w) * es, None)
+    m, r, w = conv_io(1000, 32, 64, pool=True); t["enc3"] = (m, 0, (r + w) * es, None)
+    if form == "fp32":
+        m, r, w = conv_io(500, 64, 128); t["enc4"] = (m, 0, (r + w) * es, None)
+        m, r, w = convT_io(500, 128, 64); t["up3"] = (m, 0, (r + w) * es, None)
+        m, r, w = conv_io(1000, 128, 64); t["dec3"] = (m, 0, (r + w) * es, None)
+        m, r, w = convT_io(1000, 64, 32); t["up2"] = (m, 0, (r + w) * es, None)
+        m, r, w = conv_io(2000, 64, 32); t["dec2"] = (m, 0, (r + w) * es, None)
+        m, r, w = convT_io(2000, 32, 16); t["up1"] = (m, 0, (r + w) * es, None)
+        m, r, w = conv_io(4000, 32, 16); t["dec1"] = (m, 0, (r + w) * es, None)
+        t["tail"] = (4000 * 16 * 5, 0, 16 * 4004 * es + 16000, "alu")
+    else:
+        m1, r1, _ = conv_io(500, 64, 128); m2, _, w2 = convT_io(500, 128, 64)
+        t["enc4_up3"] = (m1 + m2, 0, (r1 + w2) * es, None)
+        m1, r1, _ = conv_io(1000, 128, 64); m2, _, w2 = convT_io(1000, 64, 32)
+        t["dec3_up2"] = (m1 + m2, 0, (r1 + w2) * es, None)
+        m1, r1, _ = conv_io(2000, 64, 32); m2, _, w2 = convT_io(2000, 32, 16)
+        t["dec2_up1"] = (m1 + m2, 0, (r1 + w2) * es, None)
+        m1, r1, _ = conv_io(4000, 32, 16)
+        t["dec1_final"] = (m1 + 4000 * 16 * 5, 0, r1 * es + 16000, None)
+        t["tail"] = (0, 0, 16000, "hbm")
+    return t
+
+
+def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_launch, peaks):
+    """Roofline of one kernel family from its algorithmic FLOPs and bytes per launch:
+    the bound is whichever of compute and memory needs more time at its peak."""
+    mac, per_track_b, bytes_ev, unit = kernel_table(form)[name]
+    flops = 2.0 * mac * events_per_launch
+    nbytes = bytes_ev * events_per_launch + per_track_b * tracks_per_launch
+    if name == "front":
+        flops += 2.0 * FC_MAC_PER_TRACK * tracks_per_launch
+    sec = tot_ms / max(launches, 1) / 1000.0
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6     # FLOP/s, fp32 lanes
+    tc_peak = peaks["bf16_tflops"] * 1e12 * (2.0 if form == "fp8" else 1.0)
+    cpeak = alu_peak if (unit == "alu" or form == "fp32") else tc_peak
+    hbm = peaks["hbm_gbs"] * 1e9
+    t_c, t_m = flops / cpeak, nbytes / hbm
+    if unit == "hbm" or (unit is None and t_m >= t_c):
+        return {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": nbytes / sec / hbm, "algorithmic_bytes": nbytes}
+    kind = "alu" if cpeak == alu_peak else "tensor"
+    return {"bound": kind, "achieved": flops / sec / 1e12, "peak": cpeak / 1e12, "unit": "TFLOP/s",
+            "frac": flops / sec / cpeak, "algorithmic_flops": flops}
 
 
 def load_peaks():
@@ -223,8 +273,18 @@ def main():
 
     dtype = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision]
     stream = torch.cuda.current_stream()
+    scales = None
+    if args.precision == "fp8":
+        # per-tensor activation scales from the calibration pass (512 seeded events through
+        # a BF16 handle), outside any timed region
+        cal = synth.generate_standard(512, 1)
+        pcal = PVFinder(weights, precision="bf16", max_events=512, max_pv_per_event=8)
+        scales = pcal.calibrate(torch.from_numpy(cal.features).cuda(),
+                                torch.from_numpy(cal.offsets).cuda())
+        pcal.close()
+        del pcal
     pv = PVFinder(weights, precision=args.precision, max_events=args.events,
-                  max_pv_per_event=args.max_pv)
+                  max_pv_per_event=args.max_pv, fp8_act_scales=scales)
     feats_h = torch.from_numpy(batch.features).pin_memory()
     offs_h = torch.from_numpy(batch.offsets).pin_memory()
     feats = feats_h.cuda()
@@ -300,28 +360,17 @@ def main():
     # dominant kernel and its roofline (algorithmic work / live launch duration)
     peaks, peak_src = load_peaks()
     valid_tracks = int(np.sum(np.diff(batch.offsets)))
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (launches, tot_ms) = dom
-    avg_ms = tot_ms / max(launches, 1)
-    ev_per_launch = args.events   # one launch covers the whole (unchunked) batch
-    mac = sum(LAYER_MAC[l] for l in FAMILY_LAYERS.get(name, [])) * ev_per_launch
-    if name == "front":
-        mac += FC_MAC_PER_TRACK * valid_tracks
-    achieved = 2.0 * mac / (avg_ms / 1000.0) / 1e12
-    if args.precision == "fp32":
-        # CUDA-core float32: 152 SMs x 128 FMA lanes x 2 FLOP x max SM clock
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": name,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz of measured peaks"}
-    else:
-        peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": name,
-                "peak_source": f"{peak_src} bf16 burst" + (" x2 nominal fp8 ratio" if args.precision == "fp8" else "")}
-    kernels = {k: {"launches": n, "avg_us": 1000.0 * ms / max(n, 1),
-                   "share": ms / max(sum(v[1] for v in prof.values()), 1e-9)}
-               for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    kernels = {}
+    total_ms = max(sum(v[1] for v in prof.values()), 1e-9)
+    for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks)
+        kernels[k] = {"launches": n, "avg_us": 1000.0 * ms / max(n, 1), "share": ms / total_ms,
+                      "bound": rf["bound"], "frac": rf["frac"]}
+    name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks)
+    roof.update({"kernel": name, "traffic": None,
+                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
+                                "fp32 ALU = 152 SM x 128 lanes x 2 x sm_max_mhz; fp8 = 2 x bf16)"})
     gpu_launches = int(sum(n for n, _ in prof.values()))
 
     h2d = batch.features.nbytes + batch.offsets.nbytes

@@ -157,6 +157,18 @@ PVF_API pvf_status pvf_stage_unet(pvf_handle *h, const float *hist, int32_t n_ev
 PVF_API pvf_status pvf_stage_peaks(pvf_handle *h, const float *logit, int32_t n_events,
                            float *out_pv_z, int32_t *out_pv_count, pvf_stream_t stream);
 
+/* FP8 calibration (the per-tensor activation scales of PVF_FP8_E4M3). Runs steps 1-3
+ * of a PVF_BF16 handle on n_events calibration events while recording max |x| of every
+ * activation tensor that the FP8 form stores, and writes out_scales[i] = amax_i / 448
+ * (1 where amax_i = 0) for i < PVF_N_ACT_SCALES (unused slots = 1): the value to pass as
+ * pvf_config.fp8_act_scales. Slots: 0 e1/p1/u1, 1 e2/p2/u2, 2 e3/p3/u3 (the halves of
+ * each skip concat share a scale), 3 e4, 4 d3, 5 d2, 6 d1.
+ *   out_scales  host float[PVF_N_ACT_SCALES]
+ * Errors: PVF_ERR_UNSUPPORTED unless h is a PVF_BF16 handle. Synchronises stream. */
+PVF_API pvf_status pvf_calibrate(pvf_handle *h, const pvf_tracks_soa *tracks,
+                                 const int32_t *event_offsets, int32_t n_events,
+                                 float *out_scales, pvf_stream_t stream);
+
 /* Reads and clears the handle's device status word (the worst status raised by
  * kernels since the last read: PVF_OK, PVF_WARN_*, PVF_ERR_TIMEOUT).
  * Synchronises stream. */

@@ -9,28 +9,30 @@
 //   b. slice index per track, s = floor((z + 100) / 10) in float32 round-to-nearest;
 //      a track is dropped when a feature is not finite or s is outside [0, 40);
 //   c. stable counting sort of the valid tracks by slice (integer work only);
-//   d. FC net per track, one thread per track, in chunks of 128 sorted tracks;
-//   e. histogram: bin 100 s + j is the sum, in sorted (= input) order within slice s,
-//      of output j of the slice's tracks. Each bin is owned by one thread and added
-//      sequentially, so the order depends only on the event's own track list: results
-//      are bitwise reproducible and identical alone or in any batch. No float atomics.
+//   d. hidden layers 1-5 of the FC net, one thread per track, in chunks of 256 sorted
+//      tracks, into a shared-memory tile of h5 vectors;
+//   e. output layer + histogram, bin-parallel: the thread owning bin j of slice s computes
+//      softplus(W6[j] . h5 + b6[j]) for each of the slice's tracks in sorted (= input)
+//      order and adds it to bin 100 s + j sequentially, so the order depends only on the
+//      event's own track list: results are bitwise reproducible and identical alone or
+//      in any batch. No float atomics.
 //   f. e1 = LeakyReLU(conv_k5(hist)), p1 = maxpool2(e1), stored in the form's precision.
 #include "pvf_internal.cuh"
 
 namespace pvf {
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kChunk = 128;               // tracks per FC chunk = threads
-constexpr int kOutPitch = kFcOut + 1;     // 101: conflict-free row/column access
+constexpr int kThreads = 256;
+constexpr int kChunk = 256;               // tracks per FC chunk = threads
+constexpr int kHPitch = kFcHidden + 1;    // 33: conflict-free per-track rows
 
 struct FrontSmem {
     // byte offsets into dynamic shared memory
     static constexpr size_t fc = 0;                                   // kFcFloats floats
     static constexpr size_t enc1 = fc + sizeof(float) * kFcFloats;    // kEnc1Floats
     static constexpr size_t hist = (enc1 + sizeof(float) * kEnc1Floats + 15) / 16 * 16;
-    static constexpr size_t out = hist + sizeof(float) * kBins;       // kChunk x 101
-    static constexpr size_t cnt = out + sizeof(float) * kChunk * kOutPitch;  // 41 ints
+    static constexpr size_t h5 = hist + sizeof(float) * kBins;        // kChunk x 33
+    static constexpr size_t cnt = h5 + sizeof(float) * kChunk * kHPitch;  // 41 ints
     static constexpr size_t seg = cnt + sizeof(int) * 48;             // 41 ints
     static constexpr size_t run = seg + sizeof(int) * 48;             // 40 ints
     static constexpr size_t sorted = run + sizeof(int) * 48;          // uint16 [max_tracks]
@@ -40,9 +42,9 @@ struct FrontSmem {
 
 __device__ __forceinline__ float softplus_f(float x) { return x > 20.0f ? x : log1pf(expf(x)); }
 
-// FC forward of one track; writes 100 outputs to out_row (shared memory).
-__device__ __forceinline__ void fc_forward(const float *__restrict__ W, const float x[kFcInPad],
-                                           float *out_row) {
+// Hidden layers 1-5 of the FC net for one track; writes h5 (32 floats) to h_row.
+__device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const float x[kFcInPad],
+                                          float *h_row) {
     float h[kFcHidden], g[kFcHidden];
     {
         const float *w1 = W + fc_w_off(0);
@@ -83,22 +85,8 @@ __device__ __forceinline__ void fc_forward(const float *__restrict__ W, const fl
 #pragma unroll
         for (int o = 0; o < kFcHidden; ++o) h[o] = g[o];
     }
-    const float *w6 = W + fc_w_off(5);
-    const float *b6 = W + fc_b_off(5);
-#pragma unroll 4
-    for (int o = 0; o < kFcOut; ++o) {
-        const float4 *wr = reinterpret_cast<const float4 *>(w6 + o * kFcHidden);
-        float acc = b6[o];
 #pragma unroll
-        for (int i4 = 0; i4 < kFcHidden / 4; ++i4) {
-            float4 w = wr[i4];
-            acc = fmaf(w.x, h[4 * i4 + 0], acc);
-            acc = fmaf(w.y, h[4 * i4 + 1], acc);
-            acc = fmaf(w.z, h[4 * i4 + 2], acc);
-            acc = fmaf(w.w, h[4 * i4 + 3], acc);
-        }
-        out_row[o] = softplus_f(acc);
-    }
+    for (int o = 0; o < kFcHidden; ++o) h_row[o] = h[o];
 }
 
 // Slice of a float32 z (round-to-nearest add and divide); -1 when outside [0, 40).
@@ -150,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     float *sfc = reinterpret_cast<float *>(smem + FrontSmem::fc);
     float *senc = reinterpret_cast<float *>(smem + FrontSmem::enc1);
     float *shist = reinterpret_cast<float *>(smem + FrontSmem::hist);
-    float *sout = reinterpret_cast<float *>(smem + FrontSmem::out);
+    float *sh5 = reinterpret_cast<float *>(smem + FrontSmem::h5);
     int *scnt = reinterpret_cast<int *>(smem + FrontSmem::cnt);
     int *sseg = reinterpret_cast<int *>(smem + FrontSmem::seg);
     int *srun = reinterpret_cast<int *>(smem + FrontSmem::run);
@@ -219,7 +207,10 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
         __syncthreads();
         const int nvalid = sseg[kSlices];
 
-        // ---- d/e. FC per track and per-bin sequential sums, chunk by chunk
+        // ---- d/e. hidden layers per track, then output layer + per-bin sequential sums
+        const float *w6t = sfc + fc_w_off(5);
+        const float *b6 = sfc + fc_b_off(5);
+        const int grp = tid / kFcOut, j = tid % kFcOut;   // two groups of 100 bin threads
         for (int c0 = 0; c0 < nvalid; c0 += kChunk) {
             const int r = c0 + tid;
             if (r < nvalid) {
@@ -232,17 +223,26 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
                 x[2] = __fsub_rn(x[2], -100.0f + 10.0f * (float)s);   // slice-relative z (exact offset)
 #pragma unroll
                 for (int k = kFeatures; k < kFcInPad; ++k) x[k] = 0.0f;
-                fc_forward(sfc, x, sout + tid * kOutPitch);
+                fc_hidden(sfc, x, sh5 + tid * kHPitch);
             }
             __syncthreads();
-            if (tid < kFcOut) {
-                const int j = tid;
+            if (grp < 2) {
+                float w[kFcHidden];
+#pragma unroll
+                for (int i = 0; i < kFcHidden; ++i) w[i] = w6t[i * kFcOut + j];
+                const float bj = b6[j];
                 const int c1 = min(c0 + kChunk, nvalid);
-                for (int s = 0; s < kSlices; ++s) {
+                for (int s = grp; s < kSlices; s += 2) {
                     const int lo = max(sseg[s], c0), hi = min(sseg[s + 1], c1);
                     if (lo >= hi) continue;
                     float acc = shist[s * kSliceBins + j];
-                    for (int rr = lo; rr < hi; ++rr) acc = __fadd_rn(acc, sout[(rr - c0) * kOutPitch + j]);
+                    for (int rr = lo; rr < hi; ++rr) {
+                        const float *hr = sh5 + (rr - c0) * kHPitch;
+                        float o = bj;
+#pragma unroll
+                        for (int i = 0; i < kFcHidden; ++i) o = fmaf(w[i], hr[i], o);
+                        acc = __fadd_rn(acc, softplus_f(o));
+                    }
                     shist[s * kSliceBins + j] = acc;
                 }
             }
@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     // ---- f. e1 = LeakyReLU(conv_k5(hist) + b), p1 = maxpool2(e1)
     const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
+    float vmax = 0.0f;
     for (int q = tid; q < kBins / 2; q += kThreads) {
         float hv[6];
 #pragma unroll
@@ -279,10 +280,16 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
             v0[co] = leaky(a0);
             v1[co] = leaky(a1);
             vp[co] = fmaxf(v0[co], v1[co]);
+            vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
         }
         store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
         store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
         store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
+    }
+    if (a.amax) {   // calibration: integer max on the float bits (order-independent)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
     }
     if (tid < 4) {
         const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3

@@ -11,9 +11,10 @@
 //      becomes ln(0.01 / 0.99)), which avoids the float32 saturation of sigmoid
 //      (which rounds to 1 for f > 16.6) turning distinct maxima into ties;
 //   3. z = centroid over bins [i - 3, i + 3] with weights p[j] = sigmoid(f[j]);
-//   4. ordered compaction: each thread owns 16 consecutive bins, a block-wide
-//      exclusive scan of the per-thread counts gives each PV its slot, so PVs are
-//      written in ascending z without atomics. The true count is always reported.
+//   4. ordered compaction: candidate flags are packed into bit masks by warp ballots;
+//      each thread then owns 16 consecutive bins, and a block-wide exclusive scan of
+//      the per-thread counts gives each PV its slot, so PVs are written in ascending z
+//      without atomics. The true count is always reported.
 #include "pvf_internal.cuh"
 
 namespace pvf {
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
     const int ge = a.ev_base + e;
 
     if (a.logit_in) {
-        const float *src = a.logit_in + (size_t)ge * kBins;
+        const float *src = a.logit_in + (size_t)(ge - a.logit_in_base) * kBins;
         for (int p = tid; p < kBins; p += kThreads) sf[p] = src[p];
     } else {
         for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
@@ -96,25 +97,31 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
     if (!a.pv_count) return;
 
     const bool bypass = a.ev_flag && a.ev_flag[ge] != 0;
-    // ---- candidates in this thread's 16 bins
-    const int i0 = tid * kPerThread;
-    unsigned mask = 0;
-    if (!bypass) {
-#pragma unroll 1
-        for (int k = 0; k < kPerThread; ++k) {
-            const int i = i0 + k;
-            if (i >= kBins) break;
+    const int lane = tid & 31, warp = tid >> 5;
+    // ---- candidate flags: consecutive lanes test consecutive bins (conflict-free shared
+    //      reads); a warp ballot packs 32 bins into one mask word
+    __shared__ uint32_t smask[kThreads * kPerThread / 32];
+    for (int i0 = warp * 32; i0 < kThreads * kPerThread; i0 += kThreads) {
+        const int i = i0 + lane;
+        bool c = false;
+        if (!bypass && i < kBins) {
             const float fi = sf[i];
-            if (!(fi > kThrLogit)) continue;
-            bool ok = true;
-            for (int j = max(0, i - kPeakHalfWin); j < i; ++j) ok &= fi > sf[j];
-            for (int j = i + 1; j <= min(kBins - 1, i + kPeakHalfWin); ++j) ok &= fi >= sf[j];
-            if (ok) mask |= 1u << k;
+            c = fi > kThrLogit;
+#pragma unroll
+            for (int d = 1; d <= kPeakHalfWin; ++d) {
+                if (i - d >= 0) c &= fi > sf[i - d];
+                if (i + d < kBins) c &= fi >= sf[i + d];
+            }
         }
+        const unsigned m = __ballot_sync(0xffffffffu, c);
+        if (lane == 0) smask[i0 >> 5] = m;
     }
+    __syncthreads();
+    // thread tid owns bins [16 tid, 16 tid + 16): half a mask word
+    const int i0 = tid * kPerThread;
+    unsigned mask = (smask[tid >> 1] >> ((tid & 1) * 16)) & 0xFFFFu;
     const int cnt = __popc(mask);
     // ---- block exclusive scan of cnt
-    const int lane = tid & 31, warp = tid >> 5;
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {

@@ -35,10 +35,10 @@ namespace {
 using namespace tc;
 
 constexpr int kTileM = 128;
-constexpr int kStages = 2;
 constexpr int kThreadsTc = 192;
+constexpr int kFinalStride = kTileM - 4;   // dec1 + final conv: tiles overlap by 4 rows
 
-enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2 };
+enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2, EPI_FINAL = 3 };
 
 __host__ __device__ constexpr int pow2ceil(int x) {
     int p = 32;
@@ -47,13 +47,14 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 }
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_>
+template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = PREC == PVF_BF16 ? 2 : 1;      // bytes per element
     static constexpr int PW = 16 / ES;                       // channels per 16-byte plane row
     static constexpr int CA = CA_, CB = CB_, CIN = CA_ + CB_, COUT = COUT_, L = L_, EPI = EPI_;
     static constexpr int CUP = CUP_;
+    static constexpr int STAGES = STAGES_;
     static constexpr int PA = CA / PW, PB = CB / PW, PIN = PA + PB, POUT = COUT / PW;
     // A single input plane is half an MMA's K (32 bytes): pair taps (2j, 2j+1) in one MMA
     // by pointing the K-adjacent core matrix at the next row; a 6th zero tap pads.
@@ -61,7 +62,8 @@ struct Cfg {
     static constexpr int TAPS = PAIR ? 6 : 5;
     static constexpr int ROWS = kTileM + TAPS - 1;           // halo'd tile rows
     static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
-    static constexpr int TPE = (L + kTileM - 1) / kTileM;    // tiles per event
+    static constexpr int STRIDE = EPI == EPI_FINAL ? kFinalStride : kTileM;
+    static constexpr int TPE = (L + STRIDE - 1) / STRIDE;    // tiles per event
     static constexpr int A_STAGE = align_up(PIN * ROWS * 16, 128);
     static constexpr int W_BYTES = TAPS * PIN * COUT * 16;
     static constexpr int N2 = EPI == EPI_UP ? 2 * CUP : 0;   // fused ConvT: n = r * CUP + co
@@ -70,11 +72,16 @@ struct Cfg {
     static constexpr int A2_BYTES = EPI == EPI_UP ? P2 * kTileM * 16 : 0;
     static constexpr int COLS_BUF = COUT + N2;
     static constexpr int TMEM_COLS = pow2ceil(2 * COLS_BUF);
+    // float parameters kept in shared memory: bias, bias2, column scales, final conv
+    static constexpr int NPAR = 2 * (COUT + N2) + (EPI == EPI_FINAL ? kFinalFloats : 0);
     static constexpr int OFF_W = 0;
     static constexpr int OFF_W2 = align_up(OFF_W + W_BYTES, 128);
-    static constexpr int OFF_A = align_up(OFF_W2 + W2_BYTES, 128);
-    static constexpr int OFF_A2 = OFF_A + kStages * A_STAGE;
-    static constexpr int OFF_BAR = align_up(OFF_A2 + 2 * A2_BYTES, 128);
+    static constexpr int OFF_PAR = align_up(OFF_W2 + W2_BYTES, 128);
+    static constexpr int OFF_A = align_up(OFF_PAR + 4 * NPAR, 128);
+    static constexpr int OFF_A2 = OFF_A + STAGES * A_STAGE;
+    static constexpr int OFF_G = align_up(OFF_A2 + 2 * A2_BYTES, 128);
+    static constexpr int G_BYTES = EPI == EPI_FINAL ? 2 * 5 * kTileM * 4 : 0;
+    static constexpr int OFF_BAR = align_up(OFF_G + G_BYTES, 128);
     static constexpr int SMEM = OFF_BAR + 256;
     static constexpr uint32_t FMT = PREC == PVF_BF16 ? 1u : 0u;
     static constexpr uint32_t IDESC1 = idesc_f32acc(kTileM, COUT, FMT);
@@ -83,21 +90,55 @@ struct Cfg {
     static_assert(N2 % 16 == 0 && N2 <= 256, "MMA N of the fused GEMM");
     static_assert(PIN % 2 == 0 || PAIR, "K planes come in pairs");
     static_assert(EPI != EPI_UP || P2 % 2 == 0, "fused GEMM K planes come in pairs");
+    static_assert(EPI != EPI_FINAL || COUT == kC0, "final conv reads c0 channels");
     static_assert(TMEM_COLS <= 512, "TMEM columns");
+    static_assert(STAGES >= 2 && STAGES <= 8, "stages");
     static_assert(SMEM <= 227 * 1024, "shared memory");
-    static_assert(COUT % 16 == 0 && CUP % 16 == 0 || EPI != EPI_UP, "16-column epilogue chunks");
+    static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
 };
 
 struct TcArgs {
     const unsigned char *inA, *inB;     // plane-major inputs (inB: skip half of the concat)
     unsigned char *out, *outp;          // conv or ConvT output; pooled output
+    float *logits;                      // EPI_FINAL: [n_events][L] float32
     const unsigned char *w, *w2;        // packed weights (shared-memory image)
     const float *bias, *bias2;          // float32 biases
     const float *cs, *cs2;              // fp8: per-column dequantisation scales; bf16: null
+    const float *final_w;               // EPI_FINAL: W[t][ci] then b (float32)
     float out_inv, mid_inv;             // fp8: 1 / scale of the stored output and of A2
+    float *amax;                        // calibration: running max |x| per scale slot, or null
+    int amax_out, amax_mid;             // slots of the stored output and of A2 (kScale*)
     int n_events;
     int32_t *status;
 };
+
+// Calibration: folds max |v| of 16 values (rows with valid = false count as 0) into the
+// warp maximum and lane 0 raises amax[slot] with an integer atomicMax on the float bits,
+// which orders non-negative floats correctly and does not depend on arrival order.
+__device__ __forceinline__ void amax_fold(float *amax, int slot, const float (&v)[16], bool valid) {
+    float m = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m = fmaxf(m, fabsf(v[j]));
+    if (!valid) m = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(amax + slot), __float_as_int(m));
+}
+
+// Barrier slots in shared memory (uint64 each).
+template <class C> struct Bars {
+    static constexpr int W = 0, FULL = 1, EMPTY = 1 + C::STAGES, TFULL = 1 + 2 * C::STAGES,
+                         TEMPTY = TFULL + 2, A2FULL = TFULL + 4, T2FULL = TFULL + 6,
+                         DRAIN = TFULL + 8, GREADY = DRAIN + 1, N = GREADY + 2;
+    static_assert(N * 8 + 8 <= 256, "barrier area");
+};
+
+template <class C>
+__device__ __forceinline__ void tile_pos(int t, int &e, int &p0) {
+    e = t / C::TPE;
+    const int k = t % C::TPE;
+    p0 = C::EPI == EPI_FINAL ? k * kFinalStride - kPad : k * kTileM;
+}
 
 // Quantises 16 values to the form's element type and stores them as 16 / PW plane rows.
 template <int ES>
@@ -127,7 +168,8 @@ __device__ __forceinline__ void zero_planes(unsigned char *base, int64_t e, int 
 
 template <class C>
 __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, volatile int *abort) {
-    uint64_t *wbar = bar, *full = bar + 1, *empty = bar + 3;
+    using B = Bars<C>;
+    uint64_t *wbar = bar + B::W, *full = bar + B::FULL, *empty = bar + B::EMPTY;
     const int ntiles = a.n_events * C::TPE;
     mbar_arrive_expect_tx(wbar, C::W_BYTES + C::W2_BYTES);
     bulk_g2s(smem + C::OFF_W, a.w, C::W_BYTES, wbar);
@@ -135,23 +177,27 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
     int i = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int s = i % kStages;
-        const uint32_t ph = (i / kStages) & 1;
+        const int s = i % C::STAGES;
+        const uint32_t ph = (i / C::STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
-        const int e = t / C::TPE, p0 = (t % C::TPE) * kTileM;
-        const int rows = min(C::ROWS, C::ROWS_E - p0);
+        int e, p0;
+        tile_pos<C>(t, e, p0);
+        // tile row r <-> storage row p0 + r; rows before the event start are not copied
+        const int src0 = p0 > 0 ? p0 : 0, dst0 = src0 - p0;
+        const int rows = min(C::ROWS - dst0, C::ROWS_E - src0);
         mbar_arrive_expect_tx(&full[s], (uint32_t)(C::PIN * rows * 16));
-        unsigned char *dst = smem + C::OFF_A + s * C::A_STAGE;
+        unsigned char *dst = smem + C::OFF_A + s * C::A_STAGE + dst0 * 16;
         for (int k = 0; k < C::PA; ++k)
-            bulk_g2s(dst + k * C::ROWS * 16, a.inA + planar_off(e, k, C::PA, C::ROWS_E, p0), rows * 16, &full[s]);
+            bulk_g2s(dst + k * C::ROWS * 16, a.inA + planar_off(e, k, C::PA, C::ROWS_E, src0), rows * 16,
+                     &full[s]);
         for (int k = 0; k < C::PB; ++k)
-            bulk_g2s(dst + (C::PA + k) * C::ROWS * 16, a.inB + planar_off(e, k, C::PB, C::ROWS_E, p0),
+            bulk_g2s(dst + (C::PA + k) * C::ROWS * 16, a.inB + planar_off(e, k, C::PB, C::ROWS_E, src0),
                      rows * 16, &full[s]);
     }
     // copies still in flight land before the CTA can exit: wait (bounded) for the last ones
-    for (int j = max(0, i - kStages); j < i; ++j) {
+    for (int j = max(0, i - C::STAGES); j < i; ++j) {
         const uint64_t t0 = globaltimer();
-        while (!mbar_try_wait(&full[j % kStages], (j / kStages) & 1))
+        while (!mbar_try_wait(&full[j % C::STAGES], (j / C::STAGES) & 1))
             if (globaltimer() - t0 > kWaitLimitNs) break;
     }
     if (!mbar_try_wait(wbar, 0)) {
@@ -162,10 +208,50 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
 }
 
 template <class C>
+__device__ __forceinline__ void issue_conv(uint32_t d, uint32_t as, uint32_t w_base) {
+    if constexpr (C::PAIR) {
+#pragma unroll
+        for (int j = 0; j < C::TAPS / 2; ++j) {
+            const uint64_t ad = smem_desc(as + 2 * j * 16, 16, 128);
+            const uint64_t bd = smem_desc(w_base + 2 * j * C::COUT * 16, C::COUT * 16, 128);
+            if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, j != 0);
+            else mma_fp8(d, ad, bd, C::IDESC1, j != 0);
+        }
+    } else {
+#pragma unroll
+        for (int tap = 0; tap < 5; ++tap)
+#pragma unroll
+            for (int kb = 0; kb < C::PIN / 2; ++kb) {
+                const uint64_t ad = smem_desc(as + 2 * kb * C::ROWS * 16 + tap * 16, C::ROWS * 16, 128);
+                const uint64_t bd = smem_desc(w_base + (tap * C::PIN + 2 * kb) * C::COUT * 16,
+                                              C::COUT * 16, 128);
+                if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, (tap | kb) != 0);
+                else mma_fp8(d, ad, bd, C::IDESC1, (tap | kb) != 0);
+            }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void issue_up(uint32_t d2, uint32_t a2, uint32_t w2_base) {
+#pragma unroll
+    for (int kb = 0; kb < C::P2 / 2; ++kb) {
+        const uint64_t ad = smem_desc(a2 + 2 * kb * kTileM * 16, kTileM * 16, 128);
+        const uint64_t bd = smem_desc(w2_base + 2 * kb * C::N2 * 16, C::N2 * 16, 128);
+        if constexpr (C::PREC == PVF_BF16) mma_bf16(d2, ad, bd, C::IDESC2, kb != 0);
+        else mma_fp8(d2, ad, bd, C::IDESC2, kb != 0);
+    }
+}
+
+// One thread issues all MMAs. With a fused ConvT, the conv of tile i is issued before the
+// ConvT of tile i - 1, so the tensor core works while the epilogue turns tile i - 1's
+// conv accumulator into the shared-memory operand of its ConvT.
+template <class C>
 __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
                            volatile int *abort) {
-    uint64_t *wbar = bar, *full = bar + 1, *empty = bar + 3, *tfull = bar + 5, *tempty = bar + 7,
-             *a2full = bar + 9, *t2full = bar + 11, *drain = bar + 13;
+    using B = Bars<C>;
+    uint64_t *wbar = bar + B::W, *full = bar + B::FULL, *empty = bar + B::EMPTY,
+             *tfull = bar + B::TFULL, *tempty = bar + B::TEMPTY, *a2full = bar + B::A2FULL,
+             *t2full = bar + B::T2FULL, *drain = bar + B::DRAIN;
     const int ntiles = a.n_events * C::TPE;
     bool ok = mbar_wait(wbar, 0, abort);
     tc_fence_after();
@@ -175,46 +261,33 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
     const uint32_t a2_base = smem_u32(smem + C::OFF_A2);
     int i = 0;
     for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
-        const int s = i % kStages, b = i & 1;
-        const uint32_t ph_s = (i / kStages) & 1, ph_b = (i >> 1) & 1;
+        const int s = i % C::STAGES, b = i & 1;
+        const uint32_t ph_s = (i / C::STAGES) & 1, ph_b = (i >> 1) & 1;
         if (!mbar_wait(&tempty[b], ph_b ^ 1, abort) || !mbar_wait(&full[s], ph_s, abort)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d = tmem + b * C::COLS_BUF;
-        const uint32_t as = a_base + s * C::A_STAGE;
-        if constexpr (C::PAIR) {
-#pragma unroll
-            for (int j = 0; j < C::TAPS / 2; ++j) {
-                const uint64_t ad = smem_desc(as + 2 * j * 16, 16, 128);
-                const uint64_t bd = smem_desc(w_base + 2 * j * C::COUT * 16, C::COUT * 16, 128);
-                if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, j != 0);
-                else mma_fp8(d, ad, bd, C::IDESC1, j != 0);
-            }
-        } else {
-#pragma unroll
-            for (int tap = 0; tap < 5; ++tap)
-#pragma unroll
-                for (int kb = 0; kb < C::PIN / 2; ++kb) {
-                    const uint64_t ad = smem_desc(as + 2 * kb * C::ROWS * 16 + tap * 16, C::ROWS * 16, 128);
-                    const uint64_t bd = smem_desc(w_base + (tap * C::PIN + 2 * kb) * C::COUT * 16,
-                                                  C::COUT * 16, 128);
-                    if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, (tap | kb) != 0);
-                    else mma_fp8(d, ad, bd, C::IDESC1, (tap | kb) != 0);
-                }
-        }
+        issue_conv<C>(tmem + b * C::COLS_BUF, a_base + s * C::A_STAGE, w_base);
         mma_commit(&empty[s]);
         mma_commit(&tfull[b]);
         if constexpr (C::EPI == EPI_UP) {
-            if (!mbar_wait(&a2full[b], ph_b, abort)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t a2 = a2_base + b * C::A2_BYTES;
-#pragma unroll
-            for (int kb = 0; kb < C::P2 / 2; ++kb) {
-                const uint64_t ad = smem_desc(a2 + 2 * kb * kTileM * 16, kTileM * 16, 128);
-                const uint64_t bd = smem_desc(w2_base + 2 * kb * C::N2 * 16, C::N2 * 16, 128);
-                if constexpr (C::PREC == PVF_BF16) mma_bf16(d + C::COUT, ad, bd, C::IDESC2, kb != 0);
-                else mma_fp8(d + C::COUT, ad, bd, C::IDESC2, kb != 0);
+            if (i > 0) {
+                const int bp = (i - 1) & 1;
+                if (!mbar_wait(&a2full[bp], ((i - 1) >> 1) & 1, abort)) { ok = false; break; }
+                tc_fence_after();
+                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + bp * C::A2_BYTES, w2_base);
+                mma_commit(&t2full[bp]);
             }
-            mma_commit(&t2full[b]);
+        }
+    }
+    if constexpr (C::EPI == EPI_UP) {
+        if (ok && i > 0) {
+            const int bp = (i - 1) & 1;
+            if (mbar_wait(&a2full[bp], ((i - 1) >> 1) & 1, abort)) {
+                tc_fence_after();
+                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + bp * C::A2_BYTES, w2_base);
+                mma_commit(&t2full[bp]);
+            } else {
+                ok = false;
+            }
         }
     }
     // every MMA issued above completes before TMEM is released
@@ -227,39 +300,81 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
 template <class C>
 __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
                          volatile int *abort, int warp, int lane) {
-    uint64_t *tfull = bar + 5, *tempty = bar + 7, *a2full = bar + 9, *t2full = bar + 11;
+    using B = Bars<C>;
+    uint64_t *tfull = bar + B::TFULL, *tempty = bar + B::TEMPTY, *a2full = bar + B::A2FULL,
+             *t2full = bar + B::T2FULL, *gready = bar + B::GREADY;
     constexpr int ES = C::ES;
+    const float *par = reinterpret_cast<const float *>(smem + C::OFF_PAR);
+    const float *sbias = par, *sbias2 = par + C::COUT, *scs = par + C::COUT + C::N2,
+                *scs2 = scs + C::COUT, *sfin = par + 2 * (C::COUT + C::N2);
     const int q = warp & 3;                         // TMEM lane quarter of this warp
-    const int m = q * 32 + lane;                    // tile row = output position - p0
+    const int m = q * 32 + lane;                    // tile row
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
     const int ntiles = a.n_events * C::TPE;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
     constexpr int LO = 2 * C::L;                    // ConvT output length
     constexpr int64_t ROWS_O = LO + 2 * kPad;
-    constexpr int PUP = C::CUP / C::PW;
+    constexpr int PUP = C::EPI == EPI_UP ? C::CUP / C::PW : 1;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int b = i & 1;
         const uint32_t ph_b = (i >> 1) & 1;
-        const int e = t / C::TPE, p0 = (t % C::TPE) * kTileM;
+        int e, p0;
+        tile_pos<C>(t, e, p0);
         const int p = p0 + m;
-        const bool valid = p < C::L;
+        const bool valid = p >= 0 && p < C::L;
         if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
         tc_fence_after();
         const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
+        if constexpr (C::EPI == EPI_FINAL) {
+            float v[16];
+            tmem_ld16(dcol, v);
+            tc_fence_before();
+            mbar_arrive(&tempty[b]);
+            float g[5];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[j];
+                v[j] = valid ? leaky(fmaf(v[j], sc, sbias[j])) : 0.0f;   // zero padding outside
+            }
+            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
+#pragma unroll
+            for (int tp = 0; tp < 5; ++tp) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc = fmaf(sfin[tp * kC0 + j], v[j], acc);
+                g[tp] = acc;
+            }
+            float *sg = reinterpret_cast<float *>(smem + C::OFF_G) + b * 5 * kTileM;
+#pragma unroll
+            for (int tp = 0; tp < 5; ++tp) sg[tp * kTileM + m] = g[tp];
+            // neighbours' partial sums: a bounded mbarrier among the 128 epilogue threads
+            mbar_arrive(&gready[b]);
+            if (!mbar_wait(&gready[b], ph_b, abort)) return false;
+            if (m >= kPad && m < kTileM - kPad && valid) {
+                // f(p) = b + sum_t g_t(p + t - 2), in tap order
+                float f = sfin[5 * kC0];
+#pragma unroll
+                for (int tp = 0; tp < 5; ++tp) f += sg[tp * kTileM + m + tp - 2];
+                a.logits[(size_t)e * C::L + p] = f;
+            }
+            continue;
+        }
 #pragma unroll 1
         for (int c0 = 0; c0 < C::COUT; c0 += 16) {
             float v[16];
             tmem_ld16(dcol + c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float sc = C::PREC == PVF_BF16 ? 1.0f : __ldg(a.cs + c0 + j);
-                v[j] = leaky(fmaf(v[j], sc, __ldg(a.bias + c0 + j)));
+                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[c0 + j];
+                v[j] = leaky(fmaf(v[j], sc, sbias[c0 + j]));
             }
             if constexpr (C::EPI == EPI_UP) {
+                if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
                 unsigned char *a2 = smem + C::OFF_A2 + b * C::A2_BYTES;
                 put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
             } else {
+                if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
                 if (valid)
                     put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
                               (size_t)C::ROWS_E * 16, v, a.out_inv);
@@ -302,9 +417,10 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                 const int r = c0 / C::CUP, co0 = c0 % C::CUP;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float sc = C::PREC == PVF_BF16 ? 1.0f : __ldg(a.cs2 + c0 + j);
-                    v[j] = leaky(fmaf(v[j], sc, __ldg(a.bias2 + co0 + j)));
+                    const float sc = C::PREC == PVF_BF16 ? 1.0f : scs2[c0 + j];
+                    v[j] = leaky(fmaf(v[j], sc, sbias2[co0 + j]));
                 }
+                if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
                 if (valid)
                     put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
                               (size_t)ROWS_O * 16, v, a.out_inv);
@@ -326,27 +442,39 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
 
 template <class C>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_conv_tc(TcArgs a) {
+    using B = Bars<C>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
-    // bar: 0 weights | 1,2 full | 3,4 empty | 5,6 tmem full | 7,8 tmem empty |
-    //      9,10 A2 full | 11,12 second accumulator full | 13 drain
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 16);
-    volatile int *abort = reinterpret_cast<volatile int *>(bar + 17);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + B::N);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // biases, column scales and the final conv in shared memory
+    float *par = reinterpret_cast<float *>(smem + C::OFF_PAR);
+    for (int k = threadIdx.x; k < C::NPAR; k += kThreadsTc) {
+        float v;
+        if (k < C::COUT) v = a.bias[k];
+        else if (k < C::COUT + C::N2) v = a.bias2[(k - C::COUT) % (C::CUP > 0 ? C::CUP : 1)];
+        else if (k < 2 * C::COUT + C::N2) v = a.cs ? a.cs[k - C::COUT - C::N2] : 1.0f;
+        else if (k < 2 * (C::COUT + C::N2)) v = a.cs2 ? a.cs2[k - 2 * C::COUT - C::N2] : 1.0f;
+        else v = a.final_w[k - 2 * (C::COUT + C::N2)];
+        par[k] = v;
+    }
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&bar[1 + s], 1);
-            mbar_init(&bar[3 + s], 1);
+        mbar_init(&bar[B::W], 1);
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&bar[B::FULL + s], 1);
+            mbar_init(&bar[B::EMPTY + s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&bar[5 + b], 1);
-            mbar_init(&bar[7 + b], 128);
-            mbar_init(&bar[9 + b], 128);
-            mbar_init(&bar[11 + b], 1);
+            mbar_init(&bar[B::TFULL + b], 1);
+            mbar_init(&bar[B::TEMPTY + b], 128);
+            mbar_init(&bar[B::A2FULL + b], 128);
+            mbar_init(&bar[B::T2FULL + b], 1);
         }
-        mbar_init(&bar[13], 1);
+        mbar_init(&bar[B::DRAIN], 1);
+        mbar_init(&bar[B::GREADY], 128);
+        mbar_init(&bar[B::GREADY + 1], 128);
         *abort = 0;
         fence_mbar_init();
     }
@@ -399,17 +527,24 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
     const int by_tmem_smem = kSmemPerSm / kMaxByTmem - 1024;
     if (smem < by_tmem_smem) smem = by_tmem_smem;
     if (smem > 227 * 1024) smem = 227 * 1024;
-    static bool configured = false;
-    if (!configured) {
+    static int per_sm = 0;
+    if (!per_sm) {
         cudaError_t err = cudaFuncSetAttribute(k_conv_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err != cudaSuccess) return err;
-        configured = true;
+        cudaFuncAttributes fa;
+        err = cudaFuncGetAttributes(&fa, k_conv_tc<C>);
+        if (err != cudaSuccess) return err;
+        // resident CTAs per SM from registers (allocated per warp in units of 256),
+        // shared memory (+1 KB reserved per CTA), threads and TMEM columns
+        const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+        const int by_regs = 65536 / (warp_regs * (kThreadsTc / 32));
+        const int by_smem = kSmemPerSm / (smem + 1024);
+        const int by_threads = 2048 / kThreadsTc;
+        int n = by_regs < by_smem ? by_regs : by_smem;
+        if (by_threads < n) n = by_threads;
+        if (kMaxByTmem < n) n = kMaxByTmem;
+        per_sm = n < 1 ? 1 : n;
     }
-    int per_sm = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<C>, kThreadsTc, smem);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > kMaxByTmem) per_sm = kMaxByTmem;
     const int ntiles = a.n_events * C::TPE;
     int grid = sm_count() * per_sm;
     if (grid > ntiles) grid = ntiles;
@@ -421,12 +556,12 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 // ---------------------------------------------------------------- weight packing (host)
 
 template <int PREC> struct Net {
-    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0>;
-    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0>;
-    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64>;
-    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32>;
-    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16>;
-    using Dec1 = Cfg<PREC, 16, 16, 16, 4000, EPI_STORE, 0>;
+    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4>;
+    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4>;
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4>;
+    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3>;
+    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3>;
+    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4>;
 };
 
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
@@ -560,33 +695,35 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStre
     TcArgs a{};
     a.n_events = ne;
     a.status = n.status;
+    a.amax = n.amax;
     // enc2: p1 (s0) -> e2, p2 (s1)
     a.inA = U(b.s0); a.inB = nullptr; a.out = U(b.e2); a.outp = U(b.s1);
-    a.w = W(0); a.bias = n.b[0]; a.cs = cs(0); a.out_inv = inv(kScaleL2);
+    a.w = W(0); a.bias = n.b[0]; a.cs = cs(0); a.out_inv = inv(kScaleL2); a.amax_out = kScaleL2;
     if ((err = launch_conv<typename N::Enc2>(a, s, prof, "enc2")) != cudaSuccess) return err;
     // enc3: p2 (s1) -> e3, p3 (s0)
     a.inA = U(b.s1); a.out = U(b.e3); a.outp = U(b.s0);
-    a.w = W(1); a.bias = n.b[1]; a.cs = cs(1); a.out_inv = inv(kScaleL3);
+    a.w = W(1); a.bias = n.b[1]; a.cs = cs(1); a.out_inv = inv(kScaleL3); a.amax_out = kScaleL3;
     if ((err = launch_conv<typename N::Enc3>(a, s, prof, "enc3")) != cudaSuccess) return err;
     // enc4 + up3: p3 (s0) -> u3 (up)
     a.inA = U(b.s0); a.out = U(b.up); a.outp = nullptr;
     a.w = W(2); a.bias = n.b[2]; a.cs = cs(2); a.w2 = W(6); a.bias2 = n.b[6]; a.cs2 = cs(6);
-    a.mid_inv = inv(kScaleE4); a.out_inv = inv(kScaleL3);
+    a.mid_inv = inv(kScaleE4); a.out_inv = inv(kScaleL3); a.amax_mid = kScaleE4; a.amax_out = kScaleL3;
     if ((err = launch_conv<typename N::Enc4Up3>(a, s, prof, "enc4_up3")) != cudaSuccess) return err;
     // dec3 + up2: [u3 (up), e3] -> u2 (deep)
     a.inA = U(b.up); a.inB = U(b.e3); a.out = U(b.deep);
     a.w = W(3); a.bias = n.b[3]; a.cs = cs(3); a.w2 = W(7); a.bias2 = n.b[7]; a.cs2 = cs(7);
-    a.mid_inv = inv(kScaleD3); a.out_inv = inv(kScaleL2);
+    a.mid_inv = inv(kScaleD3); a.out_inv = inv(kScaleL2); a.amax_mid = kScaleD3; a.amax_out = kScaleL2;
     if ((err = launch_conv<typename N::Dec3Up2>(a, s, prof, "dec3_up2")) != cudaSuccess) return err;
     // dec2 + up1: [u2 (deep), e2] -> u1 (up)
     a.inA = U(b.deep); a.inB = U(b.e2); a.out = U(b.up);
     a.w = W(4); a.bias = n.b[4]; a.cs = cs(4); a.w2 = W(8); a.bias2 = n.b[8]; a.cs2 = cs(8);
-    a.mid_inv = inv(kScaleD2); a.out_inv = inv(kScaleL1);
+    a.mid_inv = inv(kScaleD2); a.out_inv = inv(kScaleL1); a.amax_mid = kScaleD2; a.amax_out = kScaleL1;
     if ((err = launch_conv<typename N::Dec2Up1>(a, s, prof, "dec2_up1")) != cudaSuccess) return err;
-    // dec1: [u1 (up), e1] -> d1 (deep)
-    a.inA = U(b.up); a.inB = U(b.e1); a.out = U(b.deep); a.w2 = nullptr;
-    a.w = W(5); a.bias = n.b[5]; a.cs = cs(5); a.out_inv = inv(kScaleD1);
-    return launch_conv<typename N::Dec1>(a, s, prof, "dec1");
+    // dec1 + final conv: [u1 (up), e1] -> logits (float32)
+    a.inA = U(b.up); a.inB = U(b.e1); a.out = nullptr; a.w2 = nullptr; a.bias2 = nullptr;
+    a.cs2 = nullptr; a.logits = b.logits; a.final_w = n.final_w; a.amax_out = kScaleD1;
+    a.w = W(5); a.bias = n.b[5]; a.cs = cs(5);
+    return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final");
 }
 
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, cudaStream_t s,

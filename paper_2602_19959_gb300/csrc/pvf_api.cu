@@ -134,7 +134,11 @@ void fill_f32(const std::vector<HostLayer> &Ls, const F32Layout &L, std::vector<
         const int nout = H.shape[0], nin = H.shape[1];
         const int pitch = l == 0 ? kFcInPad : kFcHidden;
         for (int o = 0; o < nout; ++o)
-            for (int i = 0; i < nin; ++i) fc[fc_w_off(l) + o * pitch + i] = H.w[(size_t)o * nin + i];
+            for (int i = 0; i < nin; ++i) {
+                const float w = H.w[(size_t)o * nin + i];
+                if (l < 5) fc[fc_w_off(l) + o * pitch + i] = w;
+                else fc[fc_w_off(l) + i * kFcOut + o] = w;      // layer 6 transposed
+            }
         for (int o = 0; o < nout; ++o) fc[fc_b_off(l) + o] = H.b[o];
     }
     {   // enc1 W[co][0][t] -> [t][co]
@@ -174,7 +178,7 @@ void fill_f32(const std::vector<HostLayer> &Ls, const F32Layout &L, std::vector<
 }
 
 struct Plan {
-    size_t status, ev_flag, f32w, tcw, act, total;
+    size_t status, ev_flag, f32w, tcw, logits, act, total;
     size_t act_slot_big, act_slot_small;   // bytes per slot for the chunk
     int chunk;
 };
@@ -198,6 +202,7 @@ Plan make_plan(const pvf_config *c) {
     p.ev_flag = o; o = align256(o + sizeof(int32_t) * (size_t)c->max_events);
     p.f32w = o; o = align256(o + sizeof(float) * f32_layout().total);
     p.tcw = o; o = align256(o + tc_weight_bytes(c->precision));
+    p.logits = o; o = align256(o + (c->precision != PVF_FP32 ? sizeof(float) * kBins * (size_t)p.chunk : 0));
     const size_t eb = elem_bytes(c->precision);
     p.act_slot_big = align256((size_t)p.chunk * kBigElems * eb);
     p.act_slot_small = align256((size_t)p.chunk * kSmallElems * eb);
@@ -318,6 +323,8 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
     h->buf.up = act + 4 * plan.act_slot_big;
     h->buf.s0 = act + 5 * plan.act_slot_big;
     h->buf.s1 = act + 5 * plan.act_slot_big + plan.act_slot_small;
+    h->buf.logits = reinterpret_cast<float *>(h->pool + plan.logits);
+    h->tc.final_w = h->fin;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     std::vector<float> f32;
@@ -443,6 +450,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.e1_inv_scale = 1.0f / h->act_scale[kScaleL1];
         a.ev_flag = flags;
         a.status = status;
+        a.amax = h->tc.amax;
         err = launch_front(a, prec, h->front_smem, s);
         if (err != cudaSuccess) return err;
     }
@@ -456,11 +464,17 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         TailArgs t{};
         t.d1 = h->buf.deep;
         t.logit_in = logit_in;
+        t.logit_in_base = 0;
+        t.ev_flag = logit_in ? nullptr : flags;
+        if (!logit_in && prec != PVF_FP32) {
+            // tensor-core forms: the final conv ran in dec1's epilogue; peaks only
+            t.logit_in = h->buf.logits;
+            t.logit_in_base = ev_base;
+        }
         t.d1_scale = h->act_scale[kScaleD1];
         t.final_w = h->fin;
         t.n_events = n;
         t.ev_base = ev_base;
-        t.ev_flag = logit_in ? nullptr : flags;
         t.logit_out = logit_out;
         t.pv_z = pv_z;
         t.pv_count = pv_count;
@@ -539,6 +553,32 @@ pvf_status pvf_stage_peaks(pvf_handle *h, const float *logit, int32_t n, float *
                       nullptr, false, false, true, s) != cudaSuccess)
             return PVF_ERR_CUDA;
     }
+    return PVF_OK;
+}
+
+pvf_status pvf_calibrate(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
+                         int32_t n, float *out_scales, pvf_stream_t stream_) {
+    if (!h || n < 1 || n > h->cfg.max_events || !out_scales) return PVF_ERR_INVALID_ARG;
+    if (h->cfg.precision != PVF_BF16) return PVF_ERR_UNSUPPORTED;
+    if (!tracks_ok(tracks) || !offsets || !aligned4(offsets)) return PVF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    float *amax = reinterpret_cast<float *>(h->pool + h->plan.status + 64);
+    if (cudaMemsetAsync(amax, 0, sizeof(float) * PVF_N_ACT_SCALES, s) != cudaSuccess) return PVF_ERR_CUDA;
+    h->tc.amax = amax;
+    cudaError_t err = cudaSuccess;
+    for (int c0 = 0; c0 < n && err == cudaSuccess; c0 += h->plan.chunk) {
+        const int nc = n - c0 < h->plan.chunk ? n - c0 : h->plan.chunk;
+        err = run_chunk(h, tracks, offsets, nullptr, nullptr, c0, nc, nullptr, nullptr, nullptr,
+                        nullptr, true, true, false, s);
+    }
+    h->tc.amax = nullptr;
+    float host[PVF_N_ACT_SCALES];
+    if (err != cudaSuccess ||
+        cudaMemcpyAsync(host, amax, sizeof host, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PVF_ERR_CUDA;
+    for (int i = 0; i < PVF_N_ACT_SCALES; ++i)
+        out_scales[i] = (i < kNumScales && host[i] > 0.0f) ? host[i] / 448.0f : 1.0f;
     return PVF_OK;
 }
 

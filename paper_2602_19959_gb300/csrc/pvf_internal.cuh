@@ -34,8 +34,8 @@ constexpr float kThreshold = 0.01f;
 constexpr int kPeakHalfWin = 5;
 constexpr int kCentroidHalf = 3;
 
-// FC weights in float32 (the FP32 form and the CUDA-core reference layouts).
-// Layer l: W[out][in] row-major, layer 1 padded to 12 inputs; then all biases.
+// FC weights in float32. Layers 1-5: W[out][in] row-major, layer 1 padded to 12 inputs;
+// layer 6 transposed, W6T[in][out] (bin-parallel output layer); then all biases.
 constexpr int kFcW1 = kFcHidden * kFcInPad;          // 384
 constexpr int kFcWH = kFcHidden * kFcHidden;         // 1024
 constexpr int kFcW6 = kFcOut * kFcHidden;            // 3200
@@ -116,13 +116,15 @@ struct FrontArgs {
     void *e1;                    // chunk-local padded [n][4004][16]
     void *p1;                    // chunk-local padded [n][2004][16]
     float e1_inv_scale;          // fp8 only: 1 / scale of e1/p1
+    float *amax;                 // calibration: max |e1| into amax[0], or null
     int32_t *ev_flag;            // global [max_events]: 1 = bypassed
     int32_t *status;
 };
 
 struct TailArgs {
     const void *d1;              // chunk-local padded [n][4004][16], or null for logit_in
-    const float *logit_in;       // non-null: peaks only, read logits (global rows)
+    const float *logit_in;       // non-null: peaks only, read logits
+    int32_t logit_in_base;       // event index of logit_in's first row (0: global rows)
     float d1_scale;              // fp8 only
     const float *final_w;        // kFinalFloats
     int32_t n_events;
@@ -169,6 +171,7 @@ constexpr int64_t kBigElems = 504 * 128;    // largest of (L + 4) * C over the b
 constexpr int64_t kSmallElems = 504 * 64;   // largest over p1, p2, p3
 struct UnetBuffers {
     void *e1, *e2, *e3, *deep, *up, *s0, *s1;
+    float *logits;   // tensor-core forms: final-conv output of the chunk, [n][4000]
 };
 cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n_events,
                             cudaStream_t s, const ProfHook *prof);

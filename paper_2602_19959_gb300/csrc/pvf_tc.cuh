@@ -34,6 +34,8 @@ struct TcNet {
     const float *b[9];       // biases, float32
     const float *wscale[9];  // per-accumulator-column dequantisation scales (fp8)
     float act_scale[PVF_N_ACT_SCALES];
+    const float *final_w;    // final conv (float32, W[t][ci] then b)
+    float *amax;             // calibration capture (kNumScales floats) or null
     int32_t *status;         // device status word
 };
 

@@ -35,8 +35,8 @@ N_ACT_SCALES = 16
 
 EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex",
             "pvf_stage_histogram", "pvf_stage_unet", "pvf_stage_peaks",
-            "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_destroy",
-            "pvf_status_str", "pvf_version")
+            "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_calibrate",
+            "pvf_destroy", "pvf_status_str", "pvf_version")
 
 
 class PvfConfig(ctypes.Structure):
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
             "pvf_last_device_status": (S, [P, ctypes.POINTER(I32), P]),
             "pvf_profile_enable": (S, [P, I32]),
             "pvf_profile_read": (S, [P, ctypes.POINTER(PvfKernelTime), I32, ctypes.POINTER(I32), P]),
+            "pvf_calibrate": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P]),
             "pvf_destroy": (S, [P]),
             "pvf_status_str": (ctypes.c_char_p, [S]),
             "pvf_version": (I32, []),
@@ -241,6 +242,15 @@ class PVFinder:
         _check(self.lib.pvf_profile_read(self.handle, buf, 64, ctypes.byref(n), _stream_ptr(stream)),
                "pvf_profile_read")
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+    def calibrate(self, features, offsets, stream=None) -> np.ndarray:
+        """FP8 activation scales from a calibration pass of this (bf16) handle."""
+        tr = tracks_struct(features)
+        n = int(offsets.numel() - 1)
+        out = np.zeros(N_ACT_SCALES, dtype=np.float32)
+        _check(self.lib.pvf_calibrate(self.handle, ctypes.byref(tr), offsets.data_ptr(), n,
+                                      out.ctypes.data, _stream_ptr(stream)), "pvf_calibrate")
+        return out
 
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int32(0)

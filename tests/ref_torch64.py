@@ -99,9 +99,10 @@ def peaks(f: np.ndarray, p: np.ndarray, thr: float = 0.01):
 
 def unet_quantized(w: dict, hist: np.ndarray, q):
     """The UNet in float64 with q() applied wherever the tensor-core forms store a
-    reduced-precision tensor: every GEMM operand (activations and weights), the fused
-    ConvT operands (e4, d3, d2) and d1. enc1 and the final conv keep float32 weights.
-    Used to check the kernels' wiring tightly, not as the oracle."""
+    reduced-precision tensor: every GEMM operand (activations and weights) including the
+    fused ConvT operands (e4, d3, d2). enc1 and the final conv keep float32 weights, and
+    the final conv reads d1 unrounded (it runs in dec1's epilogue). Used to check the
+    kernels' wiring tightly, not as the oracle."""
     def conv(x, name, quant_w=True):
         W, b = w[name]
         Wt = _t(W)
@@ -122,10 +123,60 @@ def unet_quantized(w: dict, hist: np.ndarray, q):
     u2 = q(up(d3, "up2"))
     d2 = q(lr(conv(torch.cat([u2, e2], dim=1), "dec2")))
     u1 = q(up(d2, "up1"))
-    d1 = q(lr(conv(torch.cat([u1, e1], dim=1), "dec1")))
+    d1 = lr(conv(torch.cat([u1, e1], dim=1), "dec1"))
     f = conv(d1, "final", quant_w=False).reshape(-1)
     return f.numpy()
 
 
 def q_bf16(t):
     return t.to(torch.bfloat16).to(torch.float64)
+
+
+def _e4m3(t):
+    """Saturating round-to-nearest-even to float8 e4m3 and back to float64."""
+    return t.clamp(-448.0, 448.0).to(torch.float8_e4m3fn).to(torch.float64)
+
+
+def unet_quantized_fp8(w: dict, hist: np.ndarray, act_scale):
+    """The UNet in float64 with the FP8 form's quantisation points: every stored
+    activation x becomes e4m3(x / s) * s with the per-tensor scale s of its slot (skip
+    concat halves share one), every GEMM weight becomes e4m3(W / s_w[co]) * s_w[co] with
+    s_w[co] = max |W[co]| / 448 per output channel. enc1 and the final conv stay float32
+    and read unrounded inputs. Used to check the FP8 kernels' wiring, not as the oracle."""
+    s = [float(v) for v in act_scale]
+    qa = lambda t, k: _e4m3(t / s[k]) * s[k]
+
+    def qw_conv(W):
+        W = _t(W)
+        sw = W.abs().amax(dim=(1, 2), keepdim=True) / 448.0
+        sw = torch.where(sw > 0, sw, torch.ones_like(sw))
+        return _e4m3(W / sw) * sw
+
+    def qw_up(W):
+        W = _t(W)                                     # [Cin][Cout][2]
+        sw = W.abs().amax(dim=(0, 2), keepdim=True) / 448.0
+        sw = torch.where(sw > 0, sw, torch.ones_like(sw))
+        return _e4m3(W / sw) * sw
+
+    def conv(x, name, q=True):
+        W, b = w[name]
+        return F.conv1d(x, qw_conv(W) if q else _t(W), _t(b), padding=2)
+
+    def up(x, name):
+        W, b = w[name]
+        return F.leaky_relu(F.conv_transpose1d(x, qw_up(W), _t(b), stride=2), 0.01)
+
+    lr = lambda v: F.leaky_relu(v, 0.01)
+    x = _t(hist).reshape(1, 1, -1)
+    e1 = qa(lr(conv(x, "enc1", q=False)), 0)
+    e2 = qa(lr(conv(F.max_pool1d(e1, 2), "enc2")), 1)
+    e3 = qa(lr(conv(F.max_pool1d(e2, 2), "enc3")), 2)
+    e4 = qa(lr(conv(F.max_pool1d(e3, 2), "enc4")), 3)
+    u3 = qa(up(e4, "up3"), 2)
+    d3 = qa(lr(conv(torch.cat([u3, e3], dim=1), "dec3")), 4)
+    u2 = qa(up(d3, "up2"), 1)
+    d2 = qa(lr(conv(torch.cat([u2, e2], dim=1), "dec2")), 5)
+    u1 = qa(up(d2, "up1"), 0)
+    d1 = lr(conv(torch.cat([u1, e1], dim=1), "dec1"))
+    f = conv(d1, "final", q=False).reshape(-1)
+    return f.numpy()

@@ -125,3 +125,66 @@ def test_bf16_full_size_sampled(PVFinder, weights):
     for i, e in enumerate(sample):
         assert np.max(np.abs(r["logit"][e] - rr["logit"][i])) <= 0.05 * np.max(np.abs(rr["logit"][i]))
     assert np.all(r["count"] >= 0)
+
+
+# ---------------------------------------------------------------- FP8 (E4M3)
+
+@pytest.fixture(scope="module")
+def fp8_scales(PVFinder, weights):
+    """Per-tensor activation scales from the calibration pass: 512 seeded events, disjoint
+    from the test events, through a BF16 handle."""
+    cal = synth.generate_standard(512, 1)
+    pv = PVFinder(weights, precision="bf16", max_events=512, max_pv_per_event=8)
+    feats, offs = to_cuda(cal)
+    scales = pv.calibrate(feats, offs)
+    pv.close()
+    return scales
+
+
+@pytest.fixture(scope="module")
+def fp8(PVFinder, weights, fp8_scales):
+    return PVFinder(weights, precision="fp8", max_events=64, max_pv_per_event=MAX_PV,
+                    fp8_act_scales=fp8_scales)
+
+
+def test_fp8_calibration_scales(fp8_scales):
+    assert np.all(np.isfinite(fp8_scales)) and np.all(fp8_scales > 0)
+    assert np.all(fp8_scales[7:] == 1.0)
+    assert np.all(fp8_scales[:7] != 1.0)
+    print("fp8 act scales:", fp8_scales[:7])
+
+
+def test_fp8_unet_wiring_matches_quantised_emulation(fp8, weights, ref16, fp8_scales):
+    h32 = ref16["hist"].astype(np.float32)
+    logit = torch.zeros((16, 4000), dtype=torch.float32, device="cuda")
+    fp8.stage_unet(torch.from_numpy(h32).cuda(), logit)
+    torch.cuda.synchronize()
+    f = logit.cpu().numpy().astype(np.float64)
+    for e in range(4):
+        want = ref.unet_quantized_fp8(weights, h32[e].astype(np.float64), fp8_scales)
+        scale = np.max(np.abs(want))
+        d = np.abs(f[e] - want) / scale
+        print(f"fp8 event {e}: median {np.median(d):.2e} p99 {np.quantile(d, 0.99):.2e} max {d.max():.2e}")
+        assert np.median(d) <= 1e-3
+        assert np.quantile(d, 0.99) <= 3e-2
+
+
+def test_fp8_against_oracle(fp8, ev16, ref16):
+    r = run_full(fp8, ev16)
+    rel = [np.max(np.abs(r["logit"][e] - ref16["logit"][e])) / np.max(np.abs(ref16["logit"][e]))
+           for e in range(16)]
+    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    print("fp8 per-bin logit err / max:", max(rel), "agreement:", a)
+    assert max(rel) <= 0.2
+    assert a["max_dz"] <= 0.1
+    assert a["exempt"] >= 0.999
+
+
+def test_fp8_deterministic_and_batch_invariant(fp8, ev16):
+    r1 = run_full(fp8, ev16)
+    r2 = run_full(fp8, ev16)
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(r1[k], r2[k])
+    rs = run_full(fp8, ev16.subset(9, 12))
+    np.testing.assert_array_equal(rs["logit"], r1["logit"][9:12])
