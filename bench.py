@@ -115,6 +115,28 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def rank_workload_seed(rank: int) -> int:
+    """Each rank draws its own events (weak scaling): no event is shared between ranks."""
+    return 1000 + rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's time: all_reduce(MAX) of one float (the only collective, outside
+    the timed region)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(events_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: all ranks' events over the slowest rank's device time."""
+    return events_per_rank * world * steps / (max_ms / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -254,7 +276,7 @@ def main():
     import synth
     rank, world, local = dist_env()
     weights = synth.he_weights(0)
-    batch = synth.generate_standard(args.events, 1000 + rank)
+    batch = synth.generate_standard(args.events, rank_workload_seed(rank))
 
     if args.impl == "reference":
         run_reference(args, weights, batch, rank, world)
@@ -344,18 +366,10 @@ def main():
     clocks = sampler.stop()
     e2e_ms, _, _ = timed(step_e2e, False)
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    dev_ms = max_over_ranks(dev_ms)
-    e2e_ms = max_over_ranks(e2e_ms)
-    total_events = args.events * world * args.steps
-    value = total_events / (dev_ms / 1000.0)
-    e2e_value = total_events / (e2e_ms / 1000.0)
+    dev_ms = max_over_ranks(dev_ms, world, "cuda")
+    e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
+    value = aggregate_value(args.events, world, args.steps, dev_ms)
+    e2e_value = aggregate_value(args.events, world, args.steps, e2e_ms)
 
     # dominant kernel and its roofline (algorithmic work / live launch duration)
     peaks, peak_src = load_peaks()
