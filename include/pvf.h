@@ -188,6 +188,31 @@ PVF_API pvf_status pvf_profile_enable(pvf_handle *h, int32_t on);
 PVF_API pvf_status pvf_profile_read(pvf_handle *h, pvf_kernel_time *out, int32_t max_entries,
                                     int32_t *n_entries, pvf_stream_t stream);
 
+/* Steps 1-2 (validation, slice sort, FC net, histogram) in float32 without allocating any
+ * device memory and without a handle or pool. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate, such as code running inside a host
+ * framework that owns every device allocation and forbids new ones while events flow
+ * (the fixed-pool model of a trigger), or a process whose device allocator is not
+ * available to this library. The caller passes inputs and outputs only:
+ *   weights_blob   host "PVFW" blob (parsed on every call; its FC layers are used)
+ *   tracks         device SoA features, as for pvf_infer
+ *   event_offsets  device int32[n_events + 1]
+ *   n_events       0..4096 (larger: PVF_ERR_INVALID_ARG)
+ *   out_hist       device float[n_events * 4000], 16-byte aligned
+ *   out_bypass     device int32[n_events] or NULL: 1 where the event was bypassed (bad
+ *                  offsets or more than 2048 tracks; its histogram row is all zero)
+ * The kernel's scratch (packed FC weights, per-event flags) is a fixed 64 KiB array
+ * inside libpvf.so that every GPU loading the library holds until the process exits.
+ * The first call on each device looks up that array's device address (make it before
+ * any stream capture). Every call overwrites the array, which keeps the last call's
+ * contents; calls that overlap on the GPU race on it. Asynchronous on stream (the blob
+ * is copied out of host memory before the call returns). */
+PVF_API pvf_status pvf_histogram_static(const void *weights_blob, size_t blob_bytes,
+                                        const pvf_tracks_soa *tracks,
+                                        const int32_t *event_offsets, int32_t n_events,
+                                        float *out_hist, int32_t *out_bypass,
+                                        pvf_stream_t stream);
+
 /* Frees the handle's host state. The pool stays owned by the caller. NULL is a no-op. */
 PVF_API pvf_status pvf_destroy(pvf_handle *h);
 

@@ -131,7 +131,8 @@ __device__ __forceinline__ void zero_row16(void *base, int64_t e, int64_t rows_e
     store_row16<T>(base, e, rows_e, row, z, 1.0f);
 }
 
-template <int PREC>
+// ENC1 = false: steps a-e only (the histogram), nothing written to e1/p1.
+template <int PREC, bool ENC1 = true>
 __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     const int e = blockIdx.x;
     const int ge = a.ev_base + e;
 
-    for (int i = tid; i < kEnc1Floats; i += kThreads) senc[i] = a.enc1[i];
+    if constexpr (ENC1)
+        for (int i = tid; i < kEnc1Floats; i += kThreads) senc[i] = a.enc1[i];
 
     if (a.hist_in) {
         const float *src = a.hist_in + (size_t)ge * kBins;
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
         for (int i = tid; i < kBins / 4; i += kThreads) dst[i] = src[i];
     }
 
+    if constexpr (!ENC1) return;
     // ---- f. e1 = LeakyReLU(conv_k5(hist) + b), p1 = maxpool2(e1)
     const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
@@ -302,6 +305,15 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
 }  // namespace
 
 size_t front_smem_bytes(int max_tracks) { return FrontSmem::total(max_tracks); }
+
+cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem, cudaStream_t s) {
+    if (a.n_events <= 0) return cudaSuccess;
+    cudaError_t err = cudaFuncSetAttribute(k_front<PVF_FP32, false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_front<PVF_FP32, false><<<a.n_events, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;

@@ -212,6 +212,18 @@ Plan make_plan(const pvf_config *c) {
 }
 
 }  // namespace
+
+pvf_status pack_fc_from_blob(const void *blob, size_t bytes, float *out) {
+    std::vector<HostLayer> layers;
+    const pvf_status st = parse_blob(blob, bytes, layers);
+    if (st != PVF_OK) return st;
+    std::vector<float> f32;
+    const F32Layout L = f32_layout();
+    fill_f32(layers, L, f32);
+    std::memcpy(out, f32.data() + L.fc, sizeof(float) * kFcFloats);
+    return PVF_OK;
+}
+
 }  // namespace pvf
 
 using namespace pvf;

@@ -155,6 +155,10 @@ struct ProfScope {
 // Host-side launchers (defined in the kernel translation units).
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem_bytes, cudaStream_t s);
 size_t front_smem_bytes(int max_tracks);
+// Steps 1-2 only (validate, sort, FC, histogram into a.hist_out), float32; e1/p1 unused.
+cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem_bytes, cudaStream_t s);
+// Reads a "PVFW" blob and writes the packed float32 FC block (kFcFloats floats) to out.
+pvf_status pack_fc_from_blob(const void *blob, size_t bytes, float *out);
 cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s);
 
 struct ConvF32Weights {

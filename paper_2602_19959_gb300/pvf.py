@@ -36,7 +36,7 @@ N_ACT_SCALES = 16
 EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex",
             "pvf_stage_histogram", "pvf_stage_unet", "pvf_stage_peaks",
             "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_calibrate",
-            "pvf_destroy", "pvf_status_str", "pvf_version")
+            "pvf_histogram_static", "pvf_destroy", "pvf_status_str", "pvf_version")
 
 
 class PvfConfig(ctypes.Structure):
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
             "pvf_profile_enable": (S, [P, I32]),
             "pvf_profile_read": (S, [P, ctypes.POINTER(PvfKernelTime), I32, ctypes.POINTER(I32), P]),
             "pvf_calibrate": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P]),
+            "pvf_histogram_static": (S, [P, SZ, ctypes.POINTER(PvfTracks), P, I32, P, P, P]),
             "pvf_destroy": (S, [P]),
             "pvf_status_str": (ctypes.c_char_p, [S]),
             "pvf_version": (I32, []),
@@ -152,6 +153,20 @@ def tracks_struct(features) -> PvfTracks:
             raise ValueError("all feature rows must have the same length")
         t.f[k] = r.data_ptr()
     return t
+
+
+def histogram_static(weights: dict, features, offsets, out_hist, out_bypass=None, stream=None):
+    """Steps 1-2 through pvf_histogram_static (no device allocation by the library)."""
+    lib = load()
+    blob = pack_blob(weights)
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    tr = tracks_struct(features)
+    n = int(offsets.numel() - 1)
+    _check(lib.pvf_histogram_static(buf, len(blob), ctypes.byref(tr), offsets.data_ptr(), n,
+                                    out_hist.data_ptr(),
+                                    out_bypass.data_ptr() if out_bypass is not None else None,
+                                    _stream_ptr(stream)), "pvf_histogram_static")
+    return out_hist
 
 
 class PVFinder:
