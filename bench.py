@@ -11,7 +11,12 @@ including the host->device copy of the track features and offsets and the
 device->host copy of the PV lists.
 
   python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16|fp8]
+  python bench.py --mode batch --events 50000     # one autotuned graph launch, uneven events
+  python bench.py --mode serve                    # Poisson arrivals at 20k..200k events/s
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+The default line is the BF16 form; it also carries the plain FP32 form measured on the
+same events ("comparison") and a 2 s serving sample at 120k events/s ("serving").
 
 With N > 1 (torchrun) every rank runs its own 1000 events (weak scaling, no
 collective on the data path; events are independent).
@@ -258,55 +263,88 @@ def workload_config(args, dtype):
                   else "not flushed (profiling run)", "form": args.precision}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
-    ap.add_argument("--events", type=int, default=N_EVENTS)
-    ap.add_argument("--max-pv", type=int, default=672)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--flush-mb", type=int, default=512,
-                    help="L2 flush buffer written between steps (0: none, for small profiling runs)")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-
-    import synth
-    rank, world, local = dist_env()
-    weights = synth.he_weights(0)
-    batch = synth.generate_standard(args.events, rank_workload_seed(rank))
-
-    if args.impl == "reference":
-        run_reference(args, weights, batch, rank, world)
-        return
-
+def make_finder(args, weights, precision, events, **kw):
+    """PVFinder for `precision`; FP8 scales come from a calibration pass (512 seeded
+    events, seed 1, through a BF16 handle) outside any timed region."""
     import torch
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2602_19959_gb300 import build, PVFinder
-    if rank == 0:
-        build()
-    if world > 1:
-        dist.barrier()
-
-    dtype = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision]
-    stream = torch.cuda.current_stream()
+    import synth
+    from paper_2602_19959_gb300 import PVFinder
     scales = None
-    if args.precision == "fp8":
-        # per-tensor activation scales from the calibration pass (512 seeded events through
-        # a BF16 handle), outside any timed region
+    if precision == "fp8":
         cal = synth.generate_standard(512, 1)
         pcal = PVFinder(weights, precision="bf16", max_events=512, max_pv_per_event=8)
         scales = pcal.calibrate(torch.from_numpy(cal.features).cuda(),
                                 torch.from_numpy(cal.offsets).cuda())
         pcal.close()
-        del pcal
-    pv = PVFinder(weights, precision=args.precision, max_events=args.events,
-                  max_pv_per_event=args.max_pv, fp8_act_scales=scales)
+    return PVFinder(weights, precision=precision, max_events=events, fp8_act_scales=scales, **kw)
+
+
+def time_steps(pv, step, flush, steps, world, profile):
+    """K steps, each bracketed by CUDA events on the launch stream; L2 flushed between
+    steps outside the events; barrier + synchronize on both sides."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    prof = {}
+    pv.profile_enable(profile)
+    barrier(world)
+    w0 = time.perf_counter()
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        if profile:
+            for k, (n, ms) in pv.profile_read().items():
+                a = prof.setdefault(k, [0, 0.0])
+                a[0] += n
+                a[1] += ms
+    barrier(world)
+    wall = time.perf_counter() - w0
+    pv.profile_enable(False)
+    return sum(a.elapsed_time(b) for a, b in ev), wall, prof
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight):
+    """Poisson arrivals at `rate` events/s for `seconds` through pvf_serve_replay."""
+    rng = np.random.default_rng(seed)
+    n = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1e9 / rate, n)).astype(np.int64)
+    req = (np.arange(n) % store.n_events).astype(np.int32)
+    t0 = time.perf_counter()
+    done, cnt, batches, _ = pv.serve_replay(store, arrivals, req, max_batch=max_batch,
+                                            max_inflight=max_inflight)
+    wall = time.perf_counter() - t0
+    lat = (done - arrivals) / 1000.0
+    return {"rate_offered": rate, "events": n, "seconds": seconds,
+            "events_per_s": n / ((done.max() - arrivals.min()) / 1e9),
+            "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+            "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()),
+            "batches": batches, "mean_batch": n / max(batches, 1), "wall_s": wall,
+            "under_400us_p99": bool(np.percentile(lat, 99) < 400.0)}
+
+
+def run_step(args, weights, batch, rank, world, local):
+    import torch
+    from paper_2602_19959_gb300 import build
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build()
+    barrier(world)
+
+    dtype = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision]
+    pv = make_finder(args, weights, args.precision, args.events, max_pv_per_event=args.max_pv)
     feats_h = torch.from_numpy(batch.features).pin_memory()
     offs_h = torch.from_numpy(batch.offsets).pin_memory()
     feats = feats_h.cuda()
@@ -332,39 +370,11 @@ def main():
     torch.cuda.synchronize()
     status = pv.device_status()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def timed(fn, profile):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        prof = {}
-        pv.profile_enable(profile)
-        barrier()
-        w0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            ev[i][0].record(stream)
-            fn()
-            ev[i][1].record(stream)
-            if profile:
-                for k, (n, ms) in pv.profile_read().items():
-                    a = prof.setdefault(k, [0, 0.0])
-                    a[0] += n
-                    a[1] += ms
-        barrier()
-        wall = time.perf_counter() - w0
-        pv.profile_enable(False)
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        return ms, wall, prof
-
     sampler = ClockSampler(local)
     sampler.start()
-    dev_ms, wall, prof = timed(step_device, True)
+    dev_ms, wall, prof = time_steps(pv, step_device, flush, args.steps, world, True)
     clocks = sampler.stop()
-    e2e_ms, _, _ = timed(step_e2e, False)
+    e2e_ms, _, _ = time_steps(pv, step_e2e, flush, args.steps, world, False)
 
     dev_ms = max_over_ranks(dev_ms, world, "cuda")
     e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
@@ -400,12 +410,117 @@ def main():
         "clocks": clocks, "wall_s_timed": wall, "device_status": status,
         "peaks_source": peak_src,
     }
+    pv.close()
+    del pv
+    if args.compare and args.precision != "fp32":
+        # the plain FP32 GPU form on the same events, same timing
+        p32 = make_finder(args, weights, "fp32", args.events, max_pv_per_event=args.max_pv)
+
+        def step32():
+            p32.infer(feats, offs, out=(z, c))
+
+        for _ in range(args.warmup):
+            step32()
+        ms32, _, _ = time_steps(p32, step32, flush, max(args.steps // 4, 3), world, False)
+        ms32 = max_over_ranks(ms32, world, "cuda")
+        v32 = aggregate_value(args.events, world, max(args.steps // 4, 3), ms32)
+        line["comparison"] = {"fp32_plain_events_per_s": v32, "speedup_vs_fp32": value / v32}
+        p32.close()
+        del p32
+    if args.serve_seconds > 0 and world == 1:
+        import synth
+        store = synth.generate_uneven(4096, 55)
+        ps = make_finder(args, weights, args.precision, args.serve_batch,
+                         max_pv_per_event=args.max_pv)
+        line["serving"] = serve_sample(ps, store, args.serve_rate, args.serve_seconds, 7,
+                                       args.serve_batch, args.serve_inflight)
+        line["serving"]["workload"] = "uneven events (N_PV ~ U{1..12}, heavy-tailed background)"
+        ps.close()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_cpu_baseline(weights, batch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batch(args, weights):
+    """One persistent, graph-captured launch over the uneven workload; the autotuner picks
+    the chunk schedule."""
+    import torch
+    import synth
+    from paper_2602_19959_gb300 import build
+    from paper_2602_19959_gb300.autotune import tune_chunk
+    build()
+    b = synth.generate_uneven(args.events, 4)
+    best, table = tune_chunk(weights, b, args.precision, max_pv=args.max_pv, repeats=args.steps)
+    ms = table[best]
+    print(json.dumps({"metric": "events/s (one graph launch)", "value": args.events / (ms / 1000.0),
+                      "unit": "events/s", "workload": f"{args.events} uneven events, one graph launch",
+                      "dtype": args.precision, "best_chunk": best or args.events,
+                      "ms_per_launch": {str(k or args.events): v for k, v in table.items()},
+                      "l2": "flushed between launches (512 MB write)"}), flush=True)
+
+
+def run_serve(args, weights):
+    import synth
+    from paper_2602_19959_gb300 import build
+    build()
+    store = synth.generate_uneven(20000, 55)
+    for rate in args.rates:
+        pv = make_finder(args, weights, args.precision, args.serve_batch, max_pv_per_event=args.max_pv)
+        r = serve_sample(pv, store, rate, args.serve_seconds_full, 100 + int(rate // 1000),
+                         args.serve_batch, args.serve_inflight)
+        r.update({"metric": "serving latency", "dtype": args.precision,
+                  "workload": "Poisson arrivals over 20000 stored uneven events (cycled)",
+                  "max_batch": args.serve_batch, "max_inflight": args.serve_inflight})
+        print(json.dumps(r), flush=True)
+        pv.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step")
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--events", type=int, default=N_EVENTS)
+    ap.add_argument("--max-pv", type=int, default=672)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the plain FP32 comparison run")
+    ap.add_argument("--flush-mb", type=int, default=512,
+                    help="L2 flush buffer written between steps (0: none, for small profiling runs)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="serving sample folded into the step line (0: none)")
+    ap.add_argument("--serve-rate", type=float, default=120000.0)
+    ap.add_argument("--serve-batch", type=int, default=128)
+    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-seconds-full", type=float, default=10.0)
+    ap.add_argument("--rates", type=float, nargs="+", default=[20000, 60000, 120000, 200000])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    import synth
+    rank, world, local = dist_env()
+    weights = synth.he_weights(0)
+    if args.impl == "reference":
+        batch = synth.generate_standard(args.events, rank_workload_seed(rank))
+        run_reference(args, weights, batch, rank, world)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if args.mode == "batch":
+        run_batch(args, weights)
+        return
+    if args.mode == "serve":
+        run_serve(args, weights)
+        return
+    batch = synth.generate_standard(args.events, rank_workload_seed(rank))
+    run_step(args, weights, batch, rank, world, local)
 
 
 if __name__ == "__main__":

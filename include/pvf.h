@@ -213,6 +213,60 @@ PVF_API pvf_status pvf_histogram_static(const void *weights_blob, size_t blob_by
                                         float *out_hist, int32_t *out_bypass,
                                         pvf_stream_t stream);
 
+/* CUDA graph of one pvf_infer launch sequence (every chunk, every kernel) for fixed
+ * argument pointers: the batching form, where thousands of events run as one graph
+ * launch. The graph reads the current contents of tracks, event_offsets and n_events'
+ * outputs at each launch, so the caller refills those buffers between launches.
+ * pvf_graph_create captures on a private stream (no work is executed) and instantiates
+ * the graph; it must not be called while another capture is active on this thread.
+ * Profiling (pvf_profile_enable) is suspended while capturing. */
+typedef struct pvf_graph pvf_graph;
+PVF_API pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks,
+                                    const int32_t *event_offsets, int32_t n_events,
+                                    float *out_pv_z, int32_t *out_pv_count, pvf_graph **out);
+PVF_API pvf_status pvf_graph_launch(pvf_graph *g, pvf_stream_t stream);
+PVF_API pvf_status pvf_graph_destroy(pvf_graph *g);
+
+/* Serving: a continuous-batching request loop on the host (the library's runtime).
+ * Requests are events of a host-side event store, arriving at given times. Whenever
+ * fewer than max_inflight batches are enqueued on the stream, the loop admits the queued
+ * events that fit one in-flight slot (at most max_batch events and max_tracks_per_batch
+ * tracks: the slot's memory), packs their tracks into pinned staging, and enqueues one
+ * host->device copy, pvf_infer and the copies of PV counts and z lists back, all on
+ * `stream`. A batch is launched as soon as a slot is free and min_batch events are
+ * queued, or the oldest queued event has waited max_wait_us, or no more arrivals remain. */
+typedef struct {
+    int32_t max_batch;            /* events per launch, 1..max_events of the handle      */
+    int32_t max_tracks_per_batch; /* tracks per launch; every stored event must fit       */
+    int32_t max_inflight;         /* batches enqueued at once, 1..16                      */
+    int32_t min_batch;            /* >= 1                                                 */
+    float max_wait_us;            /* batching window for the oldest queued event          */
+    int32_t reserved[3];
+} pvf_serve_config;
+
+/* Device bytes the in-flight slots need (inputs and outputs of max_inflight batches). */
+PVF_API pvf_status pvf_serve_bytes_required(const pvf_serve_config *cfg, int32_t max_pv_per_event,
+                                            size_t *out_bytes);
+
+/* Replays n_requests arrivals and blocks until every request has completed.
+ *   store_f[9], store_offsets  host SoA event store (n_store events), as in pvf_infer
+ *   arrival_ns[i]              host time of request i, ns after the call starts, ascending
+ *   request_event[i]           store index of request i
+ *   device_slots               caller-owned device memory, >= pvf_serve_bytes_required
+ *   out_done_ns[i]             host time at which request i's batch was seen complete
+ *   out_pv_count[i]            its PV count (-1 = bypassed), or NULL
+ *   out_pv_z                   host float[n_requests * max_pv_per_event]: its z list, or NULL
+ *   out_batches                number of launches, or NULL
+ * Pinned host staging (one slot's size per in-flight batch) is allocated for the call
+ * and freed before it returns; no device memory is allocated. */
+PVF_API pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg,
+                                    const float *const *store_f, const int32_t *store_offsets,
+                                    int32_t n_store, const int64_t *arrival_ns,
+                                    const int32_t *request_event, int32_t n_requests,
+                                    void *device_slots, size_t device_bytes, int64_t *out_done_ns,
+                                    int32_t *out_pv_count, float *out_pv_z, int32_t *out_batches,
+                                    pvf_stream_t stream);
+
 /* Frees the handle's host state. The pool stays owned by the caller. NULL is a no-op. */
 PVF_API pvf_status pvf_destroy(pvf_handle *h);
 

@@ -1,0 +1,168 @@
+// Device code shared by the front kernels (k_front.cu: CUDA-core FC for the FP32 form and
+// the static-scratch histogram; k_front_tc.cu: tcgen05 FC for the BF16 and FP8 forms):
+// event validation, the stable slice sort, and enc1 + pool with its stores.
+#pragma once
+
+#include "pvf_internal.cuh"
+
+namespace pvf {
+namespace front {
+
+__device__ __forceinline__ float softplus_f(float x) { return x > 20.0f ? x : log1pf(expf(x)); }
+
+// Slice of a float32 z (round-to-nearest add and divide); -1 when outside [0, 40).
+__device__ __forceinline__ int slice_of(float z) {
+    float q = __fdiv_rn(__fadd_rn(z, 100.0f), 10.0f);
+    if (!(q >= 0.0f && q < 40.0f)) return -1;
+    return (int)floorf(q);
+}
+
+// Stores the 16 channels of storage row `row` of event e: channel-last float32 rows for
+// the FP32 form, plane-major rows (two bf16 planes / one e4m3 plane) otherwise.
+template <class T>
+__device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_e, int64_t row,
+                                            const float v[kC0], float inv_scale) {
+    if constexpr (sizeof(T) == 4) {
+        float4 *d = reinterpret_cast<float4 *>(reinterpret_cast<float *>(base) + (e * rows_e + row) * kC0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else if constexpr (sizeof(T) == 2) {
+        uint4 pk[2];
+        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(pk);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        unsigned char *cb = reinterpret_cast<unsigned char *>(base);
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)) = pk[0];
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 1, 2, rows_e, row)) = pk[1];
+    } else {
+        uint4 pk;
+        __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv_scale);
+        unsigned char *cb = reinterpret_cast<unsigned char *>(base);
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 1, rows_e, row)) = pk;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void zero_row16(void *base, int64_t e, int64_t rows_e, int64_t row) {
+    float z[kC0];
+#pragma unroll
+    for (int i = 0; i < kC0; ++i) z[i] = 0.0f;
+    store_row16<T>(base, e, rows_e, row, z, 1.0f);
+}
+
+// Steps a-c for event ge: validation (bypass flag), slice per track, stable counting
+// sort by slice. On return (after a block barrier) ssorted[0..nvalid) holds the event's
+// valid track indices grouped by slice in input order, sseg[s]..sseg[s+1] bounds slice s.
+// scnt/srun must hold 48 ints each. Every thread of the block must call this.
+template <int NT>
+__device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int tid, int *scnt, int *sseg,
+                                              int *srun, uint16_t *ssorted, uint8_t *sslice,
+                                              int64_t &t0_out, int &nvalid_out) {
+    const int64_t t0 = a.offsets[ge], t1 = a.offsets[ge + 1];
+    const bool bypass = t0 < 0 || t1 < t0 || t1 > a.n_tracks || (t1 - t0) > a.max_tracks;
+    const int n = bypass ? 0 : (int)(t1 - t0);
+    if (tid == 0) {
+        a.ev_flag[ge] = bypass ? 1 : 0;
+        if (bypass) raise_status(a.status, PVF_WARN_EVENTS_SKIPPED);
+    }
+    if (tid < 48) { scnt[tid] = 0; srun[tid] = 0; }
+    __syncthreads();
+    // slice per track (integer counts through shared atomics: exact)
+    for (int t = tid; t < n; t += NT) {
+        const int64_t gt = t0 + t;
+        bool finite = true;
+#pragma unroll
+        for (int k = 0; k < kFeatures; ++k) finite &= isfinite(a.feat[k][gt]);
+        const int s = finite ? slice_of(a.feat[2][gt]) : -1;
+        sslice[t] = s < 0 ? 255 : (uint8_t)s;
+        if (s >= 0) atomicAdd(&scnt[s], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int s = 0; s < kSlices; ++s) { sseg[s] = acc; acc += scnt[s]; }
+        sseg[kSlices] = acc;
+    }
+    __syncthreads();
+    // stable ranks by slice: warp 0 walks the tracks in input order
+    if (tid < 32) {
+        const unsigned lane = tid;
+        for (int base = 0; base < n; base += 32) {
+            const int t = base + lane;
+            const int s = t < n ? sslice[t] : 255;
+            const unsigned peers = __match_any_sync(0xffffffffu, s);
+            const unsigned lower = peers & ((1u << lane) - 1u);
+            int before = 0;
+            if (s != 255) before = srun[s];
+            __syncwarp();
+            if (s != 255) {
+                ssorted[sseg[s] + before + __popc(lower)] = (uint16_t)t;
+                if (lower == 0) srun[s] = before + __popc(peers);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    t0_out = t0;
+    nvalid_out = sseg[kSlices];
+}
+
+// The nine features of track gt with feature 2 made slice-relative (exact offset).
+__device__ __forceinline__ void track_features(const FrontArgs &a, int64_t gt, int s, float x[kFcInPad]) {
+#pragma unroll
+    for (int k = 0; k < kFeatures; ++k) x[k] = a.feat[k][gt];
+    x[2] = __fsub_rn(x[2], -100.0f + 10.0f * (float)s);
+#pragma unroll
+    for (int k = kFeatures; k < kFcInPad; ++k) x[k] = 0.0f;
+}
+
+// Step f: e1 = LeakyReLU(conv_k5(hist) + b), p1 = maxpool2(e1), stored in the form's
+// precision with the pad rows zeroed; calibration folds max |e1| into a.amax[0].
+template <class T, int NT>
+__device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, const float *shist,
+                                          const float *senc) {
+    const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
+    const float inv = a.e1_inv_scale;
+    float vmax = 0.0f;
+    for (int q = tid; q < kBins / 2; q += NT) {
+        float hv[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int p = 2 * q + k - 2;
+            hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
+        }
+        float v0[kC0], v1[kC0], vp[kC0];
+#pragma unroll
+        for (int co = 0; co < kC0; ++co) {
+            float a0 = senc[5 * kC0 + co], a1 = a0;
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                a0 = fmaf(senc[t * kC0 + co], hv[t], a0);
+                a1 = fmaf(senc[t * kC0 + co], hv[t + 1], a1);
+            }
+            v0[co] = leaky(a0);
+            v1[co] = leaky(a1);
+            vp[co] = fmaxf(v0[co], v1[co]);
+            vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
+        }
+        store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
+        store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
+        store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
+    }
+    if (a.amax) {   // calibration: integer max on the float bits (order-independent)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
+    }
+    if (tid < 4) {
+        const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3
+        zero_row16<T>(a.e1, e, rows1, r);
+        const int rp = tid < 2 ? tid : kBins / 2 + tid;
+        zero_row16<T>(a.p1, e, rows2, rp);
+    }
+}
+
+}  // namespace front
+}  // namespace pvf

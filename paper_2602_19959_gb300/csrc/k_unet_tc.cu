@@ -185,8 +185,17 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
         // tile row r <-> storage row p0 + r; rows before the event start are not copied
         const int src0 = p0 > 0 ? p0 : 0, dst0 = src0 - p0;
         const int rows = min(C::ROWS - dst0, C::ROWS_E - src0);
-        mbar_arrive_expect_tx(&full[s], (uint32_t)(C::PIN * rows * 16));
         unsigned char *dst = smem + C::OFF_A + s * C::A_STAGE + dst0 * 16;
+        if constexpr (C::PAIR) {
+            // the zero-weight 6th tap reads one row past the copied ones on an event's last
+            // tile; 0 x (stale bits of a NaN) would be NaN, so that row is zeroed first
+            if (dst0 + rows < C::ROWS) {
+                for (int k = 0; k < C::PIN; ++k)
+                    *reinterpret_cast<uint4 *>(dst + k * C::ROWS * 16 + rows * 16) = make_uint4(0, 0, 0, 0);
+                fence_proxy_async_smem();
+            }
+        }
+        mbar_arrive_expect_tx(&full[s], (uint32_t)(C::PIN * rows * 16));
         for (int k = 0; k < C::PA; ++k)
             bulk_g2s(dst + k * C::ROWS * 16, a.inA + planar_off(e, k, C::PA, C::ROWS_E, src0), rows * 16,
                      &full[s]);
@@ -671,7 +680,22 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
         }
         off_s[li] = pk.put_raw(cs.data(), cs.size() * sizeof(float));
     }
+    // FC images (bf16 in both forms): element (out o, in i) of layer l at
+    // ((i / 8) * N + o) * 16 + (i % 8) * 2 of the layer's image
+    std::vector<unsigned char> fcimg(kFcImgBytes, 0);
+    for (int l = 0; l < 6; ++l) {
+        const LayerF32 &Lw = layers[l];
+        const int nout = (int)Lw.shape[0], nin = (int)Lw.shape[1];
+        const int n = l < 5 ? kFcHidden : kFcN6;
+        for (int o = 0; o < nout; ++o)
+            for (int i = 0; i < nin; ++i) {
+                __nv_bfloat16 hv = __float2bfloat16_rn(Lw.w[(size_t)o * nin + i]);
+                std::memcpy(&fcimg[fc_img_off(l) + ((i / 8) * n + o) * 16 + (i % 8) * 2], &hv, 2);
+            }
+    }
+    const size_t off_fc = pk.put_raw(fcimg.data(), fcimg.size());
     if (pk.bytes.size() > tc_weight_bytes(precision)) return false;
+    net->fc_img = dev_base + off_fc;
     for (int li = 0; li < 9; ++li) {
         net->w[li] = dev_base + off_w[li];
         net->b[li] = reinterpret_cast<const float *>(dev_base + off_b[li]);

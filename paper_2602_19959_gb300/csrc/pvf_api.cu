@@ -268,6 +268,9 @@ struct pvf_handle {
     float act_scale[PVF_N_ACT_SCALES];
 };
 
+int pvf_handle_max_pv(const pvf_handle *h) { return h->cfg.max_pv_per_event; }
+int pvf_handle_max_events(const pvf_handle *h) { return h->cfg.max_events; }
+
 extern "C" {
 
 int32_t pvf_version(void) { return (1 << 16) | 0; }
@@ -463,7 +466,12 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.ev_flag = flags;
         a.status = status;
         a.amax = h->tc.amax;
-        err = launch_front(a, prec, h->front_smem, s);
+        if (prec == PVF_FP32) {
+            err = launch_front(a, prec, h->front_smem, s);
+        } else {
+            a.fc_img = h->tc.fc_img;
+            err = launch_front_tc(a, prec, s);
+        }
         if (err != cudaSuccess) return err;
     }
     if (run_unet) {
@@ -591,6 +599,76 @@ pvf_status pvf_calibrate(pvf_handle *h, const pvf_tracks_soa *tracks, const int3
         return PVF_ERR_CUDA;
     for (int i = 0; i < PVF_N_ACT_SCALES; ++i)
         out_scales[i] = (i < kNumScales && host[i] > 0.0f) ? host[i] / 448.0f : 1.0f;
+    return PVF_OK;
+}
+
+}  // extern "C"
+
+struct pvf_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
+                            int32_t n, float *pv_z, int32_t *pv_count, pvf_graph **out) {
+    if (!out) return PVF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h || n < 1 || n > h->cfg.max_events) return PVF_ERR_INVALID_ARG;
+    if (!tracks_ok(tracks) || !offsets || !aligned4(offsets) || !pv_z || !aligned4(pv_z) ||
+        !pv_count || !aligned4(pv_count))
+        return PVF_ERR_INVALID_ARG;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PVF_ERR_CUDA;
+    const bool prof = h->prof.on;
+    h->prof.on = false;
+    pvf_graph *g = new (std::nothrow) pvf_graph();
+    pvf_status st = g ? PVF_OK : PVF_ERR_INVALID_ARG;
+    if (st == PVF_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        st = PVF_ERR_CUDA;
+    if (st == PVF_OK) {
+        cudaError_t err = cudaSuccess;
+        for (int c0 = 0; c0 < n && err == cudaSuccess; c0 += h->plan.chunk) {
+            const int nc = n - c0 < h->plan.chunk ? n - c0 : h->plan.chunk;
+            err = run_chunk(h, tracks, offsets, nullptr, nullptr, c0, nc, pv_z, pv_count, nullptr,
+                            nullptr, true, true, true, cs);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t end = cudaStreamEndCapture(cs, &graph);
+        if (err != cudaSuccess || end != cudaSuccess || !graph) {
+            st = PVF_ERR_CUDA;
+            if (graph) cudaGraphDestroy(graph);
+        } else {
+            g->graph = graph;
+            if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) st = PVF_ERR_CUDA;
+        }
+    }
+    h->prof.on = prof;
+    cudaStreamDestroy(cs);
+    if (st != PVF_OK) {
+        if (g) {
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            if (g->graph) cudaGraphDestroy(g->graph);
+            delete g;
+        }
+        return st;
+    }
+    *out = g;
+    return PVF_OK;
+}
+
+pvf_status pvf_graph_launch(pvf_graph *g, pvf_stream_t stream) {
+    if (!g || !g->exec) return PVF_ERR_INVALID_ARG;
+    return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? PVF_OK
+                                                                                        : PVF_ERR_CUDA;
+}
+
+pvf_status pvf_graph_destroy(pvf_graph *g) {
+    if (!g) return PVF_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
     return PVF_OK;
 }
 

@@ -51,6 +51,18 @@ __host__ __device__ constexpr int fc_b_off(int l) {
     return kFcWTotal + (l < 5 ? l * kFcHidden : 5 * kFcHidden);
 }
 
+// FC weights of the tensor-core forms: bf16 images of the tcgen05 B operands (K-major
+// planes of 8 inputs x N rows x 16 bytes). Layer 1: K = 16 (nine features, zeros), N = 32;
+// layers 2-5: K = 32, N = 32; layer 6: K = 32, N = 112 (outputs 100..111 are zero rows).
+constexpr int kFcN6 = 112;
+constexpr int kFcImgW1 = 2 * kFcHidden * 16;
+constexpr int kFcImgWH = 4 * kFcHidden * 16;
+constexpr int kFcImgW6 = 4 * kFcN6 * 16;
+constexpr int kFcImgBytes = kFcImgW1 + 4 * kFcImgWH + kFcImgW6;   // 16384
+__host__ __device__ constexpr int fc_img_off(int l) {
+    return l == 0 ? 0 : (l < 5 ? kFcImgW1 + (l - 1) * kFcImgWH : kFcImgW1 + 4 * kFcImgWH);
+}
+
 // enc1 (1 -> 16, k5) in float32: W[t][co] then b[co].
 constexpr int kEnc1Floats = 5 * kC0 + kC0;
 // final (16 -> 1, k5) in float32: W[t][ci] then b.
@@ -109,7 +121,8 @@ struct FrontArgs {
     int32_t n_events;            // events in this launch
     int32_t ev_base;             // global index of the launch's first event
     int32_t max_tracks;          // per-event cap
-    const float *fc;             // packed FC block (kFcFloats)
+    const float *fc;             // packed FC block (kFcFloats); its biases serve both forms
+    const unsigned char *fc_img; // tensor-core forms: bf16 FC operand images (kFcImgBytes)
     const float *enc1;           // kEnc1Floats
     const float *hist_in;        // non-null: skip steps 1-2, read histograms (global rows)
     float *hist_out;             // nullable, global rows [ev_base + e]
@@ -155,6 +168,8 @@ struct ProfScope {
 // Host-side launchers (defined in the kernel translation units).
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem_bytes, cudaStream_t s);
 size_t front_smem_bytes(int max_tracks);
+// Steps 1-2 + enc1 with the FC on tcgen05 (BF16 and FP8 forms).
+cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s);
 // Steps 1-2 only (validate, sort, FC, histogram into a.hist_out), float32; e1/p1 unused.
 cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem_bytes, cudaStream_t s);
 // Reads a "PVFW" blob and writes the packed float32 FC block (kFcFloats floats) to out.
@@ -181,3 +196,7 @@ cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n
                             cudaStream_t s, const ProfHook *prof);
 
 }  // namespace pvf
+
+// Plan values of a handle, for the host runtime in other translation units.
+int pvf_handle_max_pv(const pvf_handle *h);
+int pvf_handle_max_events(const pvf_handle *h);

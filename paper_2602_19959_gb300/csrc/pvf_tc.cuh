@@ -35,6 +35,7 @@ struct TcNet {
     const float *wscale[9];  // per-accumulator-column dequantisation scales (fp8)
     float act_scale[PVF_N_ACT_SCALES];
     const float *final_w;    // final conv (float32, W[t][ci] then b)
+    const unsigned char *fc_img;   // bf16 FC operand images (kFcImgBytes)
     float *amax;             // calibration capture (kNumScales floats) or null
     int32_t *status;         // device status word
 };

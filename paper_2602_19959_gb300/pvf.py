@@ -36,7 +36,9 @@ N_ACT_SCALES = 16
 EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex",
             "pvf_stage_histogram", "pvf_stage_unet", "pvf_stage_peaks",
             "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_calibrate",
-            "pvf_histogram_static", "pvf_destroy", "pvf_status_str", "pvf_version")
+            "pvf_histogram_static", "pvf_graph_create", "pvf_graph_launch", "pvf_graph_destroy",
+            "pvf_serve_bytes_required", "pvf_serve_replay", "pvf_destroy", "pvf_status_str",
+            "pvf_version")
 
 
 class PvfConfig(ctypes.Structure):
@@ -52,6 +54,12 @@ class PvfTracks(ctypes.Structure):
 
 class PvfKernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_float)]
+
+
+class PvfServeConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_tracks_per_batch", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("min_batch", ctypes.c_int32),
+                ("max_wait_us", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
 
 
 class PvfError(RuntimeError):
@@ -88,6 +96,12 @@ def load(path: str = LIB_PATH):
             "pvf_profile_read": (S, [P, ctypes.POINTER(PvfKernelTime), I32, ctypes.POINTER(I32), P]),
             "pvf_calibrate": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P]),
             "pvf_histogram_static": (S, [P, SZ, ctypes.POINTER(PvfTracks), P, I32, P, P, P]),
+            "pvf_graph_create": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P, ctypes.POINTER(P)]),
+            "pvf_graph_launch": (S, [P, P]),
+            "pvf_graph_destroy": (S, [P]),
+            "pvf_serve_bytes_required": (S, [ctypes.POINTER(PvfServeConfig), I32, ctypes.POINTER(SZ)]),
+            "pvf_serve_replay": (S, [P, ctypes.POINTER(PvfServeConfig), ctypes.POINTER(P), P, I32, P, P,
+                                     I32, P, SZ, P, P, P, P, P]),
             "pvf_destroy": (S, [P]),
             "pvf_status_str": (ctypes.c_char_p, [S]),
             "pvf_version": (I32, []),
@@ -167,6 +181,27 @@ def histogram_static(weights: dict, features, offsets, out_hist, out_bypass=None
                                     out_bypass.data_ptr() if out_bypass is not None else None,
                                     _stream_ptr(stream)), "pvf_histogram_static")
     return out_hist
+
+
+class Graph:
+    """A captured launch sequence; keeps the captured buffers alive."""
+
+    def __init__(self, lib, handle, keep):
+        self.lib, self.handle, self._keep = lib, handle, keep
+
+    def launch(self, stream=None):
+        _check(self.lib.pvf_graph_launch(self.handle, _stream_ptr(stream)), "pvf_graph_launch")
+
+    def close(self):
+        if self.handle:
+            self.lib.pvf_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class PVFinder:
@@ -266,6 +301,48 @@ class PVFinder:
         _check(self.lib.pvf_calibrate(self.handle, ctypes.byref(tr), offsets.data_ptr(), n,
                                       out.ctypes.data, _stream_ptr(stream)), "pvf_calibrate")
         return out
+
+    def capture_graph(self, features, offsets, out):
+        """A CUDA graph of the whole launch sequence for these fixed buffers."""
+        tr = tracks_struct(features)
+        n = int(offsets.numel() - 1)
+        z, c = out
+        g = ctypes.c_void_p()
+        _check(self.lib.pvf_graph_create(self.handle, ctypes.byref(tr), offsets.data_ptr(), n,
+                                         z.data_ptr(), c.data_ptr(), ctypes.byref(g)), "pvf_graph_create")
+        return Graph(self.lib, g, (features, offsets, out))
+
+    def serve_replay(self, store, arrival_ns, request_event, max_batch=128,
+                     max_tracks_per_batch=None, max_inflight=4, min_batch=1, max_wait_us=0.0,
+                     want_z=False, stream=None):
+        """Continuous-batching replay (pvf_serve_replay). store: an EventBatch (host SoA).
+        Returns (done_ns int64 [n], pv_count int32 [n], batches, z [n, max_pv] or None)."""
+        import torch
+        feats = np.ascontiguousarray(store.features, dtype=np.float32)
+        offs = np.ascontiguousarray(store.offsets, dtype=np.int32)
+        arrival_ns = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        request_event = np.ascontiguousarray(request_event, dtype=np.int32)
+        n = int(arrival_ns.shape[0])
+        if max_tracks_per_batch is None:
+            max_tracks_per_batch = int(max(np.diff(offs).max(), 1) * max_batch)
+        cfg = PvfServeConfig(max_batch, max_tracks_per_batch, max_inflight, min_batch,
+                             float(max_wait_us))
+        need = ctypes.c_size_t(0)
+        _check(self.lib.pvf_serve_bytes_required(ctypes.byref(cfg), self.max_pv, ctypes.byref(need)),
+               "pvf_serve_bytes_required")
+        slots = torch.empty(int(need.value), dtype=torch.uint8, device=self.device)
+        fptr = (ctypes.c_void_p * 9)(*[feats[k].ctypes.data for k in range(9)])
+        done = np.zeros(n, dtype=np.int64)
+        cnt = np.zeros(n, dtype=np.int32)
+        z = np.zeros((n, self.max_pv), dtype=np.float32) if want_z else None
+        nb = ctypes.c_int32(0)
+        _check(self.lib.pvf_serve_replay(self.handle, ctypes.byref(cfg), fptr, offs.ctypes.data,
+                                         int(offs.shape[0] - 1), arrival_ns.ctypes.data,
+                                         request_event.ctypes.data, n, slots.data_ptr(),
+                                         int(need.value), done.ctypes.data, cnt.ctypes.data,
+                                         z.ctypes.data if want_z else None,
+                                         ctypes.byref(nb), _stream_ptr(stream)), "pvf_serve_replay")
+        return done, cnt, int(nb.value), z
 
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int32(0)

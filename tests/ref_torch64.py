@@ -180,3 +180,25 @@ def unet_quantized_fp8(w: dict, hist: np.ndarray, act_scale):
     d1 = lr(conv(torch.cat([u1, e1], dim=1), "dec1"))
     f = conv(d1, "final", q=False).reshape(-1)
     return f.numpy()
+
+
+def histogram_quantized(w: dict, feats: np.ndarray, q):
+    """One event's histogram with the tensor-core FC's rounding points: features (with
+    the slice-relative z formed in float32) and every FC weight through q(), hidden
+    activations through q() after each LeakyReLU, the output layer and softplus in
+    float64, summed per bin. Checks the tcgen05 FC wiring, not the oracle."""
+    feats = np.asarray(feats, dtype=np.float32)
+    s = slice_of(feats[2])
+    ok = (s >= 0) & np.all(np.isfinite(feats), axis=0)
+    x32 = feats[:, ok].T.copy()
+    s = s[ok]
+    x32[:, 2] = x32[:, 2] - (np.float32(-100.0) + np.float32(10.0) * s.astype(np.float32))
+    h = q(_t(x32.astype(np.float64)))
+    for i in range(1, 6):
+        W, b = w[f"fc{i}"]
+        h = q(F.leaky_relu(F.linear(h, q(_t(W)), _t(b)), 0.01))
+    W, b = w["fc6"]
+    out = F.softplus(F.linear(h, q(_t(W)), _t(b)), beta=1.0, threshold=20.0).numpy()
+    hist = np.zeros((40, 100), dtype=np.float64)
+    np.add.at(hist, s, out)
+    return hist.reshape(-1)

@@ -1,0 +1,86 @@
+"""Batching and serving through the C ABI: the graph-captured launch and the
+continuous-batching request loop. Each result must be the same alone and in the mix:
+the path is batch-invariant bit for bit, so the comparison is exact."""
+
+import numpy as np
+import pytest
+
+import synth
+from tests.helpers import to_cuda
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def PVFinder():
+    from paper_2602_19959_gb300 import build, PVFinder
+    build()
+    return PVFinder
+
+
+@pytest.fixture(scope="module")
+def weights():
+    return synth.he_weights(0)
+
+
+def alone(pv, batch, max_pv):
+    """Each event run by itself: (counts [n], z [n, max_pv])."""
+    n = batch.n_events
+    cnt = np.zeros(n, np.int32)
+    z = np.zeros((n, max_pv), np.float32)
+    for e in range(n):
+        sub = batch.subset(e, e + 1)
+        zz, cc = pv.infer(*to_cuda(sub))
+        torch.cuda.synchronize()
+        cnt[e] = cc.cpu().numpy()[0]
+        z[e] = zz.cpu().numpy()[0]
+    return cnt, z
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, precision):
+    b1 = synth.generate_uneven(48, 11)
+    b2 = synth.generate_uneven(48, 12)
+    cap = int(max(b1.n_tracks, b2.n_tracks))
+    pv = PVFinder(weights, precision=precision, max_events=48, chunk_events=16, max_pv_per_event=96)
+    feats = torch.zeros((9, cap), dtype=torch.float32, device="cuda")
+    offs = torch.zeros(49, dtype=torch.int32, device="cuda")
+    out = pv.alloc_outputs(48)
+    g = pv.capture_graph(feats, offs, out)
+    for b in (b1, b2):
+        feats.zero_()
+        feats[:, :b.n_tracks] = torch.from_numpy(b.features).cuda()
+        offs.copy_(torch.from_numpy(b.offsets).cuda())
+        g.launch()
+        torch.cuda.synchronize()
+        gz, gc = out[0].cpu().numpy().copy(), out[1].cpu().numpy().copy()
+        zz, cc = pv.infer(feats, offs)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(gc, cc.cpu().numpy())
+        zz = zz.cpu().numpy()
+        for e in range(48):            # slots past an event's count are left untouched
+            k = min(int(gc[e]), 96)
+            np.testing.assert_array_equal(gz[e, :k], zz[e, :k])
+    g.close()
+
+
+def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights):
+    store = synth.generate_uneven(40, 21)
+    max_pv = 96
+    pv = PVFinder(weights, precision="bf16", max_events=32, max_pv_per_event=max_pv)
+    rng = np.random.default_rng(5)
+    n = 300
+    arrivals = np.cumsum(rng.exponential(1e9 / 60000.0, n)).astype(np.int64)   # 60k events/s
+    req = rng.integers(0, store.n_events, n).astype(np.int32)
+    done, cnt, batches, z = pv.serve_replay(store, arrivals, req, max_batch=32, max_inflight=3,
+                                            want_z=True)
+    assert batches >= n // 32 and np.all(done >= arrivals)
+    ref_cnt, ref_z = alone(pv, store, max_pv)
+    np.testing.assert_array_equal(cnt, ref_cnt[req])
+    for i in range(n):
+        k = min(cnt[i], max_pv)
+        np.testing.assert_array_equal(z[i, :k], ref_z[req[i], :k])
+    lat_us = (done - arrivals) / 1000.0
+    print("serving latency p50/p99 us:", np.percentile(lat_us, 50), np.percentile(lat_us, 99),
+          "batches", batches)

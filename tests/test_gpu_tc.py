@@ -59,8 +59,10 @@ def run_full(pv, batch):
     logit = torch.zeros((n, 4000), dtype=torch.float32, device="cuda")
     z, c = pv.infer(feats, offs, hist=hist, logit=logit)
     torch.cuda.synchronize()
-    return dict(z=z.cpu().numpy(), count=c.cpu().numpy(), hist=hist.cpu().numpy(),
-                logit=logit.cpu().numpy())
+    r = dict(z=z.cpu().numpy(), count=c.cpu().numpy(), hist=hist.cpu().numpy(),
+             logit=logit.cpu().numpy())
+    assert np.all(np.isfinite(r["hist"])) and np.all(np.isfinite(r["logit"]))
+    return r
 
 
 def test_bf16_unet_wiring_matches_quantised_emulation(bf16, weights, ref16):
@@ -79,11 +81,29 @@ def test_bf16_unet_wiring_matches_quantised_emulation(bf16, weights, ref16):
         assert d.max() <= 2e-2
 
 
-def test_bf16_histogram_is_the_fp32_histogram(bf16, ev16, ref16):
+def test_bf16_fc_wiring_matches_quantised_emulation(bf16, weights, ev16):
     r = run_full(bf16, ev16)
+    for e in range(6):
+        feats = ev16.features[:, ev16.offsets[e]:ev16.offsets[e + 1]]
+        want = ref.histogram_quantized(weights, feats, ref.q_bf16)
+        scale = np.max(np.abs(want))
+        d = np.abs(r["hist"][e] - want) / scale
+        print(f"fc event {e}: median {np.median(d):.2e} max {d.max():.2e}")
+        assert np.median(d) <= 1e-5
+        assert d.max() <= 2e-3
+        np.testing.assert_array_equal(r["hist"][e] == 0, want == 0)
+
+
+def test_bf16_histogram_against_oracle(bf16, ev16, ref16):
+    """bf16 FC (8-bit mantissas, six layers): per-bin error within 3% of the event max."""
+    r = run_full(bf16, ev16)
+    worst = 0.0
     for e in range(16):
         scale = np.max(np.abs(ref16["hist"][e]))
-        assert np.max(np.abs(r["hist"][e] - ref16["hist"][e])) <= 1e-4 * scale
+        err = np.max(np.abs(r["hist"][e] - ref16["hist"][e])) / scale
+        worst = max(worst, err)
+        assert err <= 3e-2
+    print("bf16 histogram per-bin err / max:", worst)
 
 
 def test_bf16_against_oracle(bf16, ev16, ref16):
@@ -154,11 +174,22 @@ def test_fp8_calibration_scales(fp8_scales):
     print("fp8 act scales:", fp8_scales[:7])
 
 
+def _poison_shared_memory():
+    """Leaves NaN bit patterns in shared memory of every SM (a float32 fill of NaNs sized
+    to run on all SMs), so that a kernel reading a shared-memory row it never wrote
+    produces NaN instead of a plausible number."""
+    x = torch.full((152 * 64 * 1024,), float("nan"), device="cuda")
+    torch.cumsum(x.view(152 * 64, 1024), dim=1)
+    torch.cuda.synchronize()
+
+
 def test_fp8_unet_wiring_matches_quantised_emulation(fp8, weights, ref16, fp8_scales):
     h32 = ref16["hist"].astype(np.float32)
     logit = torch.zeros((16, 4000), dtype=torch.float32, device="cuda")
+    _poison_shared_memory()
     fp8.stage_unet(torch.from_numpy(h32).cuda(), logit)
     torch.cuda.synchronize()
+    assert np.all(np.isfinite(logit.cpu().numpy()))
     f = logit.cpu().numpy().astype(np.float64)
     for e in range(4):
         want = ref.unet_quantized_fp8(weights, h32[e].astype(np.float64), fp8_scales)
