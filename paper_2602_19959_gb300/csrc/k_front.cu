@@ -2,7 +2,8 @@
 // plus the first UNet convolution (1 -> 16 channels, k5) and its 2:1 max-pool, fused so
 // that the histogram never leaves shared memory on its way into the UNet.
 //
-// One CTA per event (§3: each event maps to one thread block):
+// A persistent grid walks the events, one event at a time per CTA (§3: each event is
+// processed by one thread block); per event:
 //   a. validate the event's offsets; bypass it (flag = 1, histogram of zeros) when they
 //      are negative, decreasing or past the feature arrays, or the event holds more
 //      than max_tracks tracks;
@@ -105,69 +106,97 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     uint8_t *sslice = smem + FrontSmem::slices(a.max_tracks);
 
     const int tid = threadIdx.x;
-    const int e = blockIdx.x;
-    const int ge = a.ev_base + e;
-
     if constexpr (ENC1)
         for (int i = tid; i < kEnc1Floats; i += kThreads) senc[i] = a.enc1[i];
-
-    if (a.hist_in) {
-        const float *src = a.hist_in + (size_t)ge * kBins;
-        for (int i = tid; i < kBins; i += kThreads) shist[i] = src[i];
-    } else {
-        // ---- a-c. validate, slice per track, stable sort by slice
+    if (!a.hist_in)
         for (int i = tid; i < kFcFloats; i += kThreads) sfc[i] = a.fc[i];
-        for (int i = tid; i < kBins; i += kThreads) shist[i] = 0.0f;
-        int64_t t0;
-        int nvalid;
-        validate_sort<kThreads>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
-
-        // ---- d/e. hidden layers per track, then output layer + per-bin sequential sums
-        const float *w6t = sfc + fc_w_off(5);
-        const float *b6 = sfc + fc_b_off(5);
-        const int grp = tid / kFcOut, j = tid % kFcOut;   // two groups of 100 bin threads
-        for (int c0 = 0; c0 < nvalid; c0 += kChunk) {
-            const int r = c0 + tid;
-            if (r < nvalid) {
-                const int t = ssorted[r];
-                const int64_t gt = t0 + t;
-                float x[kFcInPad];
-                track_features(a, gt, sslice[t], x);
-                fc_hidden(sfc, x, sh5 + tid * kHPitch);
-            }
-            __syncthreads();
-            if (grp < 2) {
-                float w[kFcHidden];
-#pragma unroll
-                for (int i = 0; i < kFcHidden; ++i) w[i] = w6t[i * kFcOut + j];
-                const float bj = b6[j];
-                const int c1 = min(c0 + kChunk, nvalid);
-                for (int s = grp; s < kSlices; s += 2) {
-                    const int lo = max(sseg[s], c0), hi = min(sseg[s + 1], c1);
-                    if (lo >= hi) continue;
-                    float acc = shist[s * kSliceBins + j];
-                    for (int rr = lo; rr < hi; ++rr) {
-                        const float *hr = sh5 + (rr - c0) * kHPitch;
-                        float o = bj;
-#pragma unroll
-                        for (int i = 0; i < kFcHidden; ++i) o = fmaf(w[i], hr[i], o);
-                        acc = __fadd_rn(acc, softplus_f(o));
-                    }
-                    shist[s * kSliceBins + j] = acc;
-                }
-            }
-            __syncthreads();
-        }
-    }
     __syncthreads();
 
-    if (a.hist_out) {
-        float4 *dst = reinterpret_cast<float4 *>(a.hist_out + (size_t)ge * kBins);
-        const float4 *src = reinterpret_cast<const float4 *>(shist);
-        for (int i = tid; i < kBins / 4; i += kThreads) dst[i] = src[i];
-    }
+    // persistent: the CTA walks the launch's events (weights loaded once above)
+    for (int e = blockIdx.x; e < a.n_events; e += gridDim.x) {
+        const int ge = a.ev_base + e;
+        if (a.hist_in) {
+            const float *src = a.hist_in + (size_t)ge * kBins;
+            for (int i = tid; i < kBins; i += kThreads) shist[i] = src[i];
+        } else {
+            // ---- a-c. validate, slice per track, stable sort by slice
+            for (int i = tid; i < kBins; i += kThreads) shist[i] = 0.0f;
+            int64_t t0;
+            int nvalid;
+            validate_sort<kThreads>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
 
-    if constexpr (ENC1) enc1_pool<T, kThreads>(a, e, tid, shist, senc);
+            // ---- d/e. hidden layers per track, then output layer + per-bin sequential sums
+            const float *w6t = sfc + fc_w_off(5);
+            const float *b6 = sfc + fc_b_off(5);
+            const int grp = tid / kFcOut, j = tid % kFcOut;   // two groups of 100 bin threads
+            for (int c0 = 0; c0 < nvalid; c0 += kChunk) {
+                const int r = c0 + tid;
+                if (r < nvalid) {
+                    const int t = ssorted[r];
+                    const int64_t gt = t0 + t;
+                    float x[kFcInPad];
+                    track_features(a, gt, sslice[t], x);
+                    fc_hidden(sfc, x, sh5 + tid * kHPitch);
+                }
+                __syncthreads();
+                if (grp < 2) {
+                    float w[kFcHidden];
+#pragma unroll
+                    for (int i = 0; i < kFcHidden; ++i) w[i] = w6t[i * kFcOut + j];
+                    const float bj = b6[j];
+                    const int c1 = min(c0 + kChunk, nvalid);
+                    for (int s = grp; s < kSlices; s += 2) {
+                        const int lo = max(sseg[s], c0), hi = min(sseg[s + 1], c1);
+                        if (lo >= hi) continue;
+                        float acc = shist[s * kSliceBins + j];
+                        for (int rr = lo; rr < hi; ++rr) {
+                            const float *hr = sh5 + (rr - c0) * kHPitch;
+                            float o = bj;
+#pragma unroll
+                            for (int i = 0; i < kFcHidden; ++i) o = fmaf(w[i], hr[i], o);
+                            acc = __fadd_rn(acc, softplus_f(o));
+                        }
+                        shist[s * kSliceBins + j] = acc;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+
+        if (a.hist_out) {
+            float4 *dst = reinterpret_cast<float4 *>(a.hist_out + (size_t)ge * kBins);
+            const float4 *src = reinterpret_cast<const float4 *>(shist);
+            for (int i = tid; i < kBins / 4; i += kThreads) dst[i] = src[i];
+        }
+
+        if constexpr (ENC1) enc1_pool<T, kThreads>(a, e, tid, shist, senc);
+        __syncthreads();                   // shist and the sort arrays are reused next event
+    }
+}
+
+// Persistent grid: as many CTAs as the shared memory lets reside (at most two per SM,
+// the register limit at 256 threads), capped by the number of events.
+template <int PREC, bool ENC1>
+cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
+    static size_t configured = 0;
+    static int sms = 0;
+    if (smem > configured) {
+        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        configured = smem;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    int per_sm = (int)((228 * 1024) / (smem + 1024));
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
+    if (grid > a.n_events) grid = a.n_events;
+    k_front<PREC, ENC1><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -176,33 +205,16 @@ size_t front_smem_bytes(int max_tracks) { return FrontSmem::total(max_tracks); }
 
 cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    cudaError_t err = cudaFuncSetAttribute(k_front<PVF_FP32, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    k_front<PVF_FP32, false><<<a.n_events, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_front_t<PVF_FP32, false>(a, smem, s);
 }
 
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    dim3 grid(a.n_events), block(kThreads);
-    cudaError_t err = cudaSuccess;
     switch (precision) {
-    case PVF_FP32:
-        err = cudaFuncSetAttribute(k_front<PVF_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err == cudaSuccess) k_front<PVF_FP32><<<grid, block, smem, s>>>(a);
-        break;
-    case PVF_BF16:
-        err = cudaFuncSetAttribute(k_front<PVF_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err == cudaSuccess) k_front<PVF_BF16><<<grid, block, smem, s>>>(a);
-        break;
-    default:
-        err = cudaFuncSetAttribute(k_front<PVF_FP8_E4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err == cudaSuccess) k_front<PVF_FP8_E4M3><<<grid, block, smem, s>>>(a);
-        break;
+    case PVF_FP32: return launch_front_t<PVF_FP32, true>(a, smem, s);
+    case PVF_BF16: return launch_front_t<PVF_BF16, true>(a, smem, s);
+    default: return launch_front_t<PVF_FP8_E4M3, true>(a, smem, s);
     }
-    if (err != cudaSuccess) return err;
-    return cudaGetLastError();
 }
 
 }  // namespace pvf

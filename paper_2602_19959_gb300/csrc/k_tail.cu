@@ -1,7 +1,7 @@
 // End of step 3 and step 4 of the path (§2): the final 16 -> 1 channel k5 convolution
 // (float32 in every form) and heuristic peak finding on its output.
 //
-// One CTA per event, 256 threads:
+// A persistent grid of 256-thread CTAs walks the events, one event at a time per CTA:
 //   1. f[p] = b + sum_t sum_ci W[t][ci] d1[p + t - 2][ci]  (the logit; prob = sigmoid(f)),
 //      kept in shared memory, optionally copied out;
 //   2. local-maximum rule with a fixed threshold in place of the paper's learned ones:
@@ -67,100 +67,104 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
     __shared__ int swarp[kThreads / 32];
 
     const int tid = threadIdx.x;
-    const int e = blockIdx.x;
-    const int ge = a.ev_base + e;
-
-    if (a.logit_in) {
-        const float *src = a.logit_in + (size_t)(ge - a.logit_in_base) * kBins;
-        for (int p = tid; p < kBins; p += kThreads) sf[p] = src[p];
-    } else {
+    const int lane = tid & 31, warp = tid >> 5;
+    if (!a.logit_in) {
         for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
         __syncthreads();
-        const int64_t rows1 = padded_rows(kBins);
-        for (int p = tid; p < kBins; p += kThreads) {
-            float acc = sw[5 * kC0];
-#pragma unroll
-            for (int t = 0; t < 5; ++t) {
-                float v[kC0];
-                load_row16<T>(a.d1, e, rows1, p + t, v, a.d1_scale);   // storage row p + t = position p + t - 2
-#pragma unroll
-                for (int ci = 0; ci < kC0; ++ci) acc = fmaf(sw[t * kC0 + ci], v[ci], acc);
-            }
-            sf[p] = acc;
-        }
     }
-    __syncthreads();
-    if (a.logit_out) {
-        float *dst = a.logit_out + (size_t)ge * kBins;
-        for (int p = tid; p < kBins; p += kThreads) dst[p] = sf[p];
-    }
-    if (!a.pv_count) return;
-
-    const bool bypass = a.ev_flag && a.ev_flag[ge] != 0;
-    const int lane = tid & 31, warp = tid >> 5;
-    // ---- candidate flags: consecutive lanes test consecutive bins (conflict-free shared
-    //      reads); a warp ballot packs 32 bins into one mask word
-    __shared__ uint32_t smask[kThreads * kPerThread / 32];
-    for (int i0 = warp * 32; i0 < kThreads * kPerThread; i0 += kThreads) {
-        const int i = i0 + lane;
-        bool c = false;
-        if (!bypass && i < kBins) {
-            const float fi = sf[i];
-            c = fi > kThrLogit;
+    // persistent: the CTA walks the launch's events
+    for (int e = blockIdx.x; e < a.n_events; e += gridDim.x) {
+        const int ge = a.ev_base + e;
+        if (a.logit_in) {
+            const float *src = a.logit_in + (size_t)(ge - a.logit_in_base) * kBins;
+            for (int p = tid; p < kBins; p += kThreads) sf[p] = src[p];
+        } else {
+            const int64_t rows1 = padded_rows(kBins);
+            for (int p = tid; p < kBins; p += kThreads) {
+                float acc = sw[5 * kC0];
 #pragma unroll
-            for (int d = 1; d <= kPeakHalfWin; ++d) {
-                if (i - d >= 0) c &= fi > sf[i - d];
-                if (i + d < kBins) c &= fi >= sf[i + d];
+                for (int t = 0; t < 5; ++t) {
+                    float v[kC0];
+                    load_row16<T>(a.d1, e, rows1, p + t, v, a.d1_scale);   // storage row p + t = position p + t - 2
+#pragma unroll
+                    for (int ci = 0; ci < kC0; ++ci) acc = fmaf(sw[t * kC0 + ci], v[ci], acc);
+                }
+                sf[p] = acc;
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, c);
-        if (lane == 0) smask[i0 >> 5] = m;
-    }
-    __syncthreads();
-    // thread tid owns bins [16 tid, 16 tid + 16): half a mask word
-    const int i0 = tid * kPerThread;
-    unsigned mask = (smask[tid >> 1] >> ((tid & 1) * 16)) & 0xFFFFu;
-    const int cnt = __popc(mask);
-    // ---- block exclusive scan of cnt
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) swarp[warp] = incl;
-    __syncthreads();
-    int wbase = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-        const int v = swarp[w];
-        if (w < warp) wbase += v;
-        total += v;
-    }
-    int idx = wbase + incl - cnt;
-    float *zout = a.pv_z + (size_t)ge * a.max_pv;
-    while (mask) {
-        const int k = __ffs(mask) - 1;
-        mask &= mask - 1;
-        if (idx < a.max_pv) {
-            const int i = i0 + k;
-            float num = 0.0f, den = 0.0f;
-#pragma unroll
-            for (int d = -kCentroidHalf; d <= kCentroidHalf; ++d) {
-                const int j = i + d;
-                if (j < 0 || j >= kBins) continue;
-                const float pj = sigmoid_f(sf[j]);
-                num = fmaf(pj, (float)d, num);
-                den += pj;
-            }
-            // z = zc(i) + 0.1 * (sum p_j (j - i) / sum p_j), zc(i) = -100 + (i + 0.5) * 0.1
-            zout[idx] = fmaf((float)i + 0.5f + num / den, kBinW, kZLo);
+        __syncthreads();
+        if (a.logit_out) {
+            float *dst = a.logit_out + (size_t)ge * kBins;
+            for (int p = tid; p < kBins; p += kThreads) dst[p] = sf[p];
         }
-        ++idx;
-    }
-    if (tid == 0) {
-        a.pv_count[ge] = bypass ? -1 : total;
-        if (!bypass && total > a.max_pv) raise_status(a.status, PVF_WARN_TRUNCATED);
+        if (a.pv_count) {
+            const bool bypass = a.ev_flag && a.ev_flag[ge] != 0;
+            // ---- candidate flags: consecutive lanes test consecutive bins (conflict-free shared
+            //      reads); a warp ballot packs 32 bins into one mask word
+            __shared__ uint32_t smask[kThreads * kPerThread / 32];
+            for (int i0 = warp * 32; i0 < kThreads * kPerThread; i0 += kThreads) {
+                const int i = i0 + lane;
+                bool c = false;
+                if (!bypass && i < kBins) {
+                    const float fi = sf[i];
+                    c = fi > kThrLogit;
+#pragma unroll
+                    for (int d = 1; d <= kPeakHalfWin; ++d) {
+                        if (i - d >= 0) c &= fi > sf[i - d];
+                        if (i + d < kBins) c &= fi >= sf[i + d];
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, c);
+                if (lane == 0) smask[i0 >> 5] = m;
+            }
+            __syncthreads();
+            // thread tid owns bins [16 tid, 16 tid + 16): half a mask word
+            const int i0 = tid * kPerThread;
+            unsigned mask = (smask[tid >> 1] >> ((tid & 1) * 16)) & 0xFFFFu;
+            const int cnt = __popc(mask);
+            // ---- block exclusive scan of cnt
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) swarp[warp] = incl;
+            __syncthreads();
+            int wbase = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const int v = swarp[w];
+                if (w < warp) wbase += v;
+                total += v;
+            }
+            int idx = wbase + incl - cnt;
+            float *zout = a.pv_z + (size_t)ge * a.max_pv;
+            while (mask) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (idx < a.max_pv) {
+                    const int i = i0 + k;
+                    float num = 0.0f, den = 0.0f;
+#pragma unroll
+                    for (int d = -kCentroidHalf; d <= kCentroidHalf; ++d) {
+                        const int j = i + d;
+                        if (j < 0 || j >= kBins) continue;
+                        const float pj = sigmoid_f(sf[j]);
+                        num = fmaf(pj, (float)d, num);
+                        den += pj;
+                    }
+                    // z = zc(i) + 0.1 * (sum p_j (j - i) / sum p_j), zc(i) = -100 + (i + 0.5) * 0.1
+                    zout[idx] = fmaf((float)i + 0.5f + num / den, kBinW, kZLo);
+                }
+                ++idx;
+            }
+            if (tid == 0) {
+                a.pv_count[ge] = bypass ? -1 : total;
+                if (!bypass && total > a.max_pv) raise_status(a.status, PVF_WARN_TRUNCATED);
+            }
+        }
+        __syncthreads();                       // sf, smask and swarp are reused next event
     }
 }
 
@@ -168,7 +172,15 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
 
 cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    dim3 grid(a.n_events), block(kThreads);
+    // persistent grid: four CTAs per SM, each walking events
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    dim3 grid(a.n_events < 4 * sms ? a.n_events : 4 * sms), block(kThreads);
     switch (precision) {
     case PVF_FP32: k_tail<PVF_FP32><<<grid, block, 0, s>>>(a); break;
     case PVF_BF16: k_tail<PVF_BF16><<<grid, block, 0, s>>>(a); break;

@@ -72,12 +72,14 @@ _lock = threading.Lock()
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Loads libpvf.so and declares the C signatures. Raises if it is missing."""
+def load(path: str = None):
+    """Loads libpvf.so (LIB_PATH unless given) and declares the C signatures. Raises if it
+    is missing."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
+        path = path or LIB_PATH
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is missing: build it with paper_2602_19959_gb300.build()")
         lib = ctypes.CDLL(path)
