@@ -4,19 +4,20 @@
 // per CTA (§3: each event is processed by one thread block), so weights and TMEM are set
 // up once per CTA rather than once per event.
 //
-// Per tile of 128 slice-sorted tracks (one track per TMEM lane / thread; two tiles per
-// pass, one per warpgroup, sharing each layer's MMA round trip):
-//   X [128 x 16] (nine features, feature 2 slice-relative, zero padded) ->
-//   5 x { MMA (N = 32) -> TMEM -> bias + LeakyReLU -> bf16 -> H [128 x 32] } ->
-//   MMA (N = 112, 100 used) -> TMEM -> bias + softplus (fp32) -> staging tile (25
-//   columns at a time) ->
-//   per-bin sums in a fixed two-level order: within each 32-row chunk of the sorted
-//   tracks a slice segment's outputs are added in order, then the chunk partials are
-//   added in row order to hist[100 s + j].
-// The layers are dependent, so the tile runs MMA and epilogue in lockstep; one thread
-// issues the MMAs, every wait on their completion is bounded. The histogram order
-// depends only on the event's own track list (chunks are counted from the event's first
-// sorted track), so results are identical alone and in any batch.
+// Per pass of up to 256 slice-sorted tracks (two 128-row tiles, one per warpgroup, one
+// track per TMEM lane / thread in the hidden layers):
+//   X [256 x 16] (nine features, feature 2 slice-relative, zero padded) ->
+//   5 x { MMA per tile (M = 128 tracks, N = 32) -> TMEM -> bias + LeakyReLU -> bf16 ->
+//         H [256 x 32] } ->
+//   output layer as the transposed product Out^T = W6^T H^T (one MMA, M = 128 output
+//   lanes, N = tracks of the pass), so TMEM lane = output bin and column = sorted track ->
+//   each thread adds bias + softplus of its bin over the tracks in sorted order, flushing
+//   a slice's running sum into hist[100 s + j] when the slice's segment ends.
+// Warpgroup 0 takes the first half of the pass's tracks and warpgroup 1 the second;
+// warpgroup 1 adds its first segment's partial after warpgroup 0 has added its own, so
+// every bin is summed in one fixed order that depends only on the event's own sorted
+// track list: results are identical alone and in any batch. One thread issues the MMAs;
+// every wait on their completion is bounded.
 #include "front_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -28,19 +29,18 @@ using namespace tc;
 
 constexpr int kT = 256;                 // threads: two warpgroups, one 128-row tile each
 constexpr int kRows = 128;              // tile rows = TMEM lanes
-constexpr int kN6 = kFcN6;              // 100 outputs padded to a multiple of 16
-constexpr int kQ = 25;                  // output columns per staging pass (4 passes)
-constexpr int kTmemCols = 256;          // tile g uses columns [128 g, 128 g + 112)
+constexpr int kPass = 2 * kRows;        // tracks per pass
+constexpr int kPlane = kPass * 16;      // bytes of one K-major plane of X or H
+constexpr int kTmemCols = 256;          // hidden layers: tile g at column 128 g; output: [0, N)
 
 struct TcSmem {
     static constexpr size_t img = 0;                                   // kFcImgBytes
     static constexpr size_t bias = img + kFcImgBytes;                  // kFcBTotal floats
     static constexpr size_t enc1 = bias + sizeof(float) * kFcBTotal;   // kEnc1Floats
-    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1Floats + 127) / 128 * 128;  // 2 tiles x 2 planes
-    static constexpr size_t h = x + 2 * 2 * kRows * 16;                // 2 tiles x 4 planes
-    static constexpr size_t hist = h + 2 * 4 * kRows * 16;
-    static constexpr size_t stage = hist + sizeof(float) * kBins;      // 2 tiles x 128 x 25 floats
-    static constexpr size_t cnt = stage + sizeof(float) * 2 * kRows * kQ;
+    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1Floats + 127) / 128 * 128;  // 2 planes x 256 rows
+    static constexpr size_t h = x + 2 * kPlane;                        // 4 planes x 256 rows
+    static constexpr size_t hist = h + 4 * kPlane;
+    static constexpr size_t cnt = hist + sizeof(float) * kBins;
     static constexpr size_t seg = cnt + sizeof(int) * 48;
     static constexpr size_t run = seg + sizeof(int) * 48;
     static constexpr size_t bar = (run + sizeof(int) * 48 + 15) / 16 * 16;   // mbarrier + slot + flag
@@ -57,9 +57,25 @@ __device__ __forceinline__ uint4 pack8_bf16(const float *v) {
     return r;
 }
 
-// Per pass of up to two 128-track tiles (warpgroup g owns tile g, one row per thread):
-// six dependent layers, each one MMA round trip for both tiles, then the output layer
-// in four 25-column passes through a staging tile and the ordered per-bin sums.
+// softplus(x) = max(x, 0) + log1p(u), u = exp(-|x|) in (0, 1], for the tensor-core forms.
+// log1p(u) = 2 atanh(t) with t = u / (2 + u) in (0, 1/3], summed as the odd power series
+// of atanh, 2 t (1 + t^2/3 + ... + t^12/13): the first omitted term is below 2e-8
+// relative, under the error of the fast exponential (about 1e-6 relative at |x| = 20).
+// Large |x| needs no special case: u underflows smoothly and t ~ u / 2.
+__device__ __forceinline__ float softplus_tc(float x) {
+    const float u = __expf(-fabsf(x));
+    const float t = __fdividef(u, 2.0f + u);
+    const float q = t * t;
+    float p = 1.0f / 13.0f;
+    p = fmaf(p, q, 1.0f / 11.0f);
+    p = fmaf(p, q, 1.0f / 9.0f);
+    p = fmaf(p, q, 1.0f / 7.0f);
+    p = fmaf(p, q, 1.0f / 5.0f);
+    p = fmaf(p, q, 1.0f / 3.0f);
+    p = fmaf(p, q, 1.0f);
+    return fmaf(2.0f * t, p, fmaxf(x, 0.0f));
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     using T = typename Elem<PREC>::T;
@@ -67,7 +83,6 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     float *sbias = reinterpret_cast<float *>(smem + TcSmem::bias);
     float *senc = reinterpret_cast<float *>(smem + TcSmem::enc1);
     float *shist = reinterpret_cast<float *>(smem + TcSmem::hist);
-    float *sstage = reinterpret_cast<float *>(smem + TcSmem::stage);
     int *scnt = reinterpret_cast<int *>(smem + TcSmem::cnt);
     int *sseg = reinterpret_cast<int *>(smem + TcSmem::seg);
     int *srun = reinterpret_cast<int *>(smem + TcSmem::run);
@@ -77,10 +92,12 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     uint16_t *ssorted = reinterpret_cast<uint16_t *>(smem + TcSmem::sorted);
     uint8_t *sslice = smem + TcSmem::slices(a.max_tracks);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp >> 2;                       // tile of this warpgroup
     const int m = tid & (kRows - 1);               // row within the tile = TMEM lane
     const uint32_t lane_field = (uint32_t)((warp & 3) * 32) << 16;
+    // output layer: this thread's TMEM lane holds output o (-1: a zero row)
+    const int o_bin = lane < kFcOutPerWarp ? (warp & 3) * kFcOutPerWarp + lane : -1;
 
     // once per CTA: enc1 weights, FC operand images and biases, barrier, TMEM
     for (int i = tid; i < kEnc1Floats; i += kT) senc[i] = a.enc1[i];
@@ -105,9 +122,10 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     const uint32_t tmem = *tmem_slot;
     const uint32_t img = smem_u32(smem + TcSmem::img);
     const uint32_t sx = smem_u32(smem + TcSmem::x), sh = smem_u32(smem + TcSmem::h);
-    unsigned char *xbuf = smem + TcSmem::x + (size_t)g * 2 * kRows * 16;
-    unsigned char *hbuf = smem + TcSmem::h + (size_t)g * 4 * kRows * 16;
+    unsigned char *xrow = smem + TcSmem::x + (size_t)(g * kRows + m) * 16;   // + plane * kPlane
+    unsigned char *hrow = smem + TcSmem::h + (size_t)(g * kRows + m) * 16;
     const uint32_t dcol = tmem + lane_field + (uint32_t)(g * 128);
+    const float b6 = o_bin >= 0 ? sbias[5 * kFcHidden + o_bin] : 0.0f;
     bool failed = false;
     uint32_t phase = 0;
 
@@ -137,30 +155,38 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                         const int t = ssorted[r];
                         track_features(a, t0 + t, sslice[t], x);
                     }
-                    *reinterpret_cast<uint4 *>(xbuf + (0 * kRows + m) * 16) = pack8_bf16(x);
-                    *reinterpret_cast<uint4 *>(xbuf + (1 * kRows + m) * 16) = pack8_bf16(x + 8);
+                    *reinterpret_cast<uint4 *>(xrow) = pack8_bf16(x);
+                    *reinterpret_cast<uint4 *>(xrow + kPlane) = pack8_bf16(x + 8);
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
                 __syncthreads();
+                const int nrow = min(nvalid - c0, kPass);
+                const int n6 = (nrow + 15) / 16 * 16;          // output MMA: N = tracks, rounded
                 for (int l = 0; l < 6 && !failed; ++l) {
                     tc_fence_after();
                     if (tid == 0) {
-                        for (int tg = 0; tg < ntile; ++tg) {
-                            const uint32_t d = tmem + (uint32_t)(tg * 128);
-                            if (l == 0) {
-                                mma_bf16(d, smem_desc(sx + tg * 2 * kRows * 16, kRows * 16, 128),
+                        if (l == 0) {
+                            for (int tg = 0; tg < ntile; ++tg)
+                                mma_bf16(tmem + (uint32_t)(tg * 128), smem_desc(sx + tg * kRows * 16, kPlane, 128),
                                          smem_desc(img, kFcHidden * 16, 128), idesc_f32acc(kRows, kFcHidden, 1), 0);
-                            } else {
-                                const int n = l < 5 ? kFcHidden : kN6;
-                                const uint32_t w = img + fc_img_off(l);
-                                const uint32_t ha = sh + tg * 4 * kRows * 16;
+                        } else if (l < 5) {
+                            const uint32_t w = img + fc_img_off(l);
+                            for (int tg = 0; tg < ntile; ++tg) {
 #pragma unroll
                                 for (int kb = 0; kb < 2; ++kb)
-                                    mma_bf16(d, smem_desc(ha + 2 * kb * kRows * 16, kRows * 16, 128),
-                                             smem_desc(w + 2 * kb * n * 16, n * 16, 128),
-                                             idesc_f32acc(kRows, n, 1), kb);
+                                    mma_bf16(tmem + (uint32_t)(tg * 128),
+                                             smem_desc(sh + tg * kRows * 16 + 2 * kb * kPlane, kPlane, 128),
+                                             smem_desc(w + 2 * kb * kFcHidden * 16, kFcHidden * 16, 128),
+                                             idesc_f32acc(kRows, kFcHidden, 1), kb);
                             }
+                        } else {   // Out^T [128 lanes x n6] = W6^T (A) x H^T (B = H, K-major)
+                            const uint32_t w = img + fc_img_off(5);
+#pragma unroll
+                            for (int kb = 0; kb < 2; ++kb)
+                                mma_bf16(tmem, smem_desc(w + 2 * kb * kFcM6 * 16, kFcM6 * 16, 128),
+                                         smem_desc(sh + 2 * kb * kPlane, kPlane, 128),
+                                         idesc_f32acc(kFcM6, n6, 1), kb);
                         }
                         mma_commit(bar);
                     }
@@ -178,61 +204,64 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                             for (int o = 0; o < kFcHidden; ++o) v[o] = leaky(v[o] + b[o]);
 #pragma unroll
                             for (int k = 0; k < 4; ++k)
-                                *reinterpret_cast<uint4 *>(hbuf + (k * kRows + m) * 16) = pack8_bf16(v + 8 * k);
+                                *reinterpret_cast<uint4 *>(hrow + k * kPlane) = pack8_bf16(v + 8 * k);
                         }
                         fence_proxy_async_smem();
                         tc_fence_before();
                         __syncthreads();
                         continue;
                     }
-                    // output layer: four passes of 25 columns through the staging tile
-                    const float *b6 = sbias + 5 * kFcHidden;
-                    const int c1 = min(c0 + 2 * kRows, nvalid);
+                    // output layer: warpgroup g adds its bin over pass rows [cb, ce) in order
+                    const int half = (nrow + 31) / 32 * 16;
+                    const int cb = g == 0 ? 0 : half, ce = g == 0 ? min(half, nrow) : nrow;
+                    float acc = 0.0f, held = 0.0f;
+                    int held_s = -1;
+                    if (cb < ce) {
+                        int s = sslice[ssorted[c0 + cb]];
+                        int send = sseg[s + 1] - c0;           // first pass row past slice s
+                        bool hold = g == 1;                    // warpgroup 1 holds its first segment
 #pragma unroll 1
-                    for (int q = 0; q < kFcOut / kQ; ++q) {
-                        if (active) {
+                        for (int col = cb; col < ce; col += 32) {
                             float v[32];
-                            tmem_ld16(dcol + q * kQ, *reinterpret_cast<float(*)[16]>(v));
-                            tmem_ld16(dcol + q * kQ + 16, *reinterpret_cast<float(*)[16]>(v + 16));
-                            if (live) {
-                                float *row = sstage + ((size_t)g * kRows + m) * kQ;
+                            tmem_ld32(tmem + lane_field + (uint32_t)col, v);
 #pragma unroll
-                                for (int j = 0; j < kQ; ++j) row[j] = softplus_f(v[j] + b6[q * kQ + j]);
+                            for (int t = 0; t < 32; ++t) v[t] = softplus_tc(v[t] + b6);
+                            if (col + 32 <= min(ce, send)) {   // one slice throughout
+#pragma unroll
+                                for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, v[t]);
+                                continue;
+                            }
+#pragma unroll
+                            for (int t = 0; t < 32; ++t) {
+                                const int r = col + t;
+                                if (r < ce) {
+                                    if (r == send) {           // slice s ends: flush, move on
+                                        if (hold) { held = acc; held_s = s; hold = false; }
+                                        else if (o_bin >= 0) {
+                                            float *hp = shist + s * kSliceBins + o_bin;
+                                            *hp = __fadd_rn(*hp, acc);
+                                        }
+                                        acc = 0.0f;
+                                        s = sslice[ssorted[c0 + r]];
+                                        send = sseg[s + 1] - c0;
+                                    }
+                                    acc = __fadd_rn(acc, v[t]);
+                                }
                             }
                         }
-                        tc_fence_before();
-                        __syncthreads();
-                        // per-bin sums in a fixed two-level order: thread (column j, chunk k)
-                        // adds the rows of each slice segment inside its 32-row chunk in
-                        // order and leaves the chunk's partial in the segment's last row of
-                        // the chunk; then each (slice, column) adds its chunks' partials in
-                        // row order to the histogram
-                        const int nrow = c1 - c0;
-                        if (tid < 8 * kQ) {
-                            const int j = tid % kQ, k = tid / kQ;
-                            const int r0 = 32 * k, r1 = min(r0 + 32, nrow);
-                            // from the slice of the chunk's first row to the last one it holds
-                            for (int s = r0 < r1 ? sslice[ssorted[c0 + r0]] : kSlices;
-                                 s < kSlices && sseg[s] - c0 < r1; ++s) {
-                                const int lo = max(sseg[s] - c0, r0), hi = min(sseg[s + 1] - c0, r1);
-                                if (lo >= hi) continue;
-                                float acc = sstage[(size_t)lo * kQ + j];
-                                for (int rr = lo + 1; rr < hi; ++rr) acc = __fadd_rn(acc, sstage[(size_t)rr * kQ + j]);
-                                sstage[(size_t)(hi - 1) * kQ + j] = acc;
-                            }
+                        if (hold) { held = acc; held_s = s; }
+                        else if (o_bin >= 0) {
+                            float *hp = shist + s * kSliceBins + o_bin;
+                            *hp = __fadd_rn(*hp, acc);
                         }
-                        __syncthreads();
-                        for (int it = tid; it < kSlices * kQ; it += kT) {
-                            const int s = it / kQ, j = it % kQ;
-                            const int lo = max(sseg[s] - c0, 0), hi = min(sseg[s + 1] - c0, nrow);
-                            if (lo >= hi) continue;
-                            float acc = shist[s * kSliceBins + q * kQ + j];
-                            for (int k = lo / 32; k <= (hi - 1) / 32; ++k)
-                                acc = __fadd_rn(acc, sstage[(size_t)(min(hi, 32 * (k + 1)) - 1) * kQ + j]);
-                            shist[s * kSliceBins + q * kQ + j] = acc;
-                        }
-                        __syncthreads();
                     }
+                    tc_fence_before();
+                    __syncthreads();
+                    if (held_s >= 0 && o_bin >= 0) {
+                        float *hp = shist + held_s * kSliceBins + o_bin;
+                        *hp = __fadd_rn(*hp, held);
+                    }
+                    __syncthreads();
                 }
             }
             if (failed) {

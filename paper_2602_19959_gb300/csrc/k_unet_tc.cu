@@ -16,11 +16,13 @@
 // LeakyReLU(0.01) in the epilogue; the fused ConvT reads the conv tile from shared
 // memory, so the deepest level's activations (e4, d3, d2) never reach global memory.
 //
-// Warp roles (192 threads): warp 0 issues the bulk copies (weights once, then one halo'd
-// activation tile per 128 positions into a 2-stage ring); warp 1 allocates TMEM and one
-// thread issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the
-// MMAs of tile i + 1); warps 2-5 are the epilogue, one TMEM lane (= output position) per
-// thread. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
+// Warp roles: warp 0 issues the bulk copies (weights once, then one halo'd activation
+// tile per 128 positions into a ring of stages); warp 1 allocates TMEM and one thread
+// issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the MMAs
+// of tile i + 1); the remaining one or two warpgroups are the epilogue, one TMEM lane
+// (= output position) per thread. With two, they split the accumulator columns (for a
+// fused ConvT: warpgroup r writes output rows 2p + r), which doubles the epilogue
+// throughput of the kernels that fit one CTA per SM. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include "pvf_tc.cuh"
 #include "tc_ptx.cuh"
@@ -35,7 +37,6 @@ namespace {
 using namespace tc;
 
 constexpr int kTileM = 128;
-constexpr int kThreadsTc = 192;
 constexpr int kFinalStride = kTileM - 4;   // dec1 + final conv: tiles overlap by 4 rows
 
 enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2, EPI_FINAL = 3 };
@@ -47,7 +48,8 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 }
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_>
+template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_, int EWG_ = 1,
+          int MAXREG_ = 128, int NB_ = 2>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = PREC == PVF_BF16 ? 2 : 1;      // bytes per element
@@ -55,6 +57,17 @@ struct Cfg {
     static constexpr int CA = CA_, CB = CB_, CIN = CA_ + CB_, COUT = COUT_, L = L_, EPI = EPI_;
     static constexpr int CUP = CUP_;
     static constexpr int STAGES = STAGES_;
+    static constexpr int EWG = EWG_;                         // epilogue warpgroups
+    static constexpr int THREADS = 64 + 128 * EWG;
+    // register cap: a warp's registers come from one SM sub-partition's 16K, so k CTAs of
+    // 6 warps fit when 6k/4 (rounded up) warps x regs x 32 <= 16384
+    static constexpr int MAXREG = MAXREG_;
+    // TMEM accumulator buffers: the MMAs of tile i wait only for the epilogue of tile i - NB
+    static constexpr int NB = NB_;
+    static constexpr int EPI_COLS = COUT / EWG;              // conv columns per epilogue thread
+    // TMEM load width of the epilogue: 32 columns per wait where the split kernels have the
+    // registers; 16 keeps the many-CTA kernels' register count (and residency) low
+    static constexpr int LDW = (EWG == 2 && EPI_COLS % 32 == 0) ? 32 : 16;
     static constexpr int PA = CA / PW, PB = CB / PW, PIN = PA + PB, POUT = COUT / PW;
     // A single input plane is half an MMA's K (32 bytes): pair taps (2j, 2j+1) in one MMA
     // by pointing the K-adjacent core matrix at the next row; a 6th zero tap pads.
@@ -71,7 +84,7 @@ struct Cfg {
     static constexpr int W2_BYTES = EPI == EPI_UP ? P2 * N2 * 16 : 0;
     static constexpr int A2_BYTES = EPI == EPI_UP ? P2 * kTileM * 16 : 0;
     static constexpr int COLS_BUF = COUT + N2;
-    static constexpr int TMEM_COLS = pow2ceil(2 * COLS_BUF);
+    static constexpr int TMEM_COLS = pow2ceil(NB * COLS_BUF);
     // float parameters kept in shared memory: bias, bias2, column scales, final conv
     static constexpr int NPAR = 2 * (COUT + N2) + (EPI == EPI_FINAL ? kFinalFloats : 0);
     static constexpr int OFF_W = 0;
@@ -92,9 +105,11 @@ struct Cfg {
     static_assert(EPI != EPI_UP || P2 % 2 == 0, "fused GEMM K planes come in pairs");
     static_assert(EPI != EPI_FINAL || COUT == kC0, "final conv reads c0 channels");
     static_assert(TMEM_COLS <= 512, "TMEM columns");
-    static_assert(STAGES >= 2 && STAGES <= 8, "stages");
+    static_assert(STAGES >= 2 && STAGES <= 6, "stages");
+    static_assert(NB == 2 || NB == 4, "accumulator buffers");
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
+    static_assert(EWG == 1 || (EWG == 2 && EPI != EPI_FINAL && EPI_COLS % 16 == 0), "column split");
 };
 
 struct TcArgs {
@@ -125,11 +140,13 @@ __device__ __forceinline__ void amax_fold(float *amax, int slot, const float (&v
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(amax + slot), __float_as_int(m));
 }
 
-// Barrier slots in shared memory (uint64 each).
+// Barrier slots in shared memory (uint64 each). TFULL/TEMPTY follow the NB accumulator
+// buffers (tile i: buffer i % NB); A2FULL/T2FULL/GREADY follow the two shared-memory
+// buffers of the fused ConvT operand and of the final conv's exchange (tile i: i % 2).
 template <class C> struct Bars {
     static constexpr int W = 0, FULL = 1, EMPTY = 1 + C::STAGES, TFULL = 1 + 2 * C::STAGES,
-                         TEMPTY = TFULL + 2, A2FULL = TFULL + 4, T2FULL = TFULL + 6,
-                         DRAIN = TFULL + 8, GREADY = DRAIN + 1, N = GREADY + 2;
+                         TEMPTY = TFULL + C::NB, A2FULL = TEMPTY + C::NB, T2FULL = A2FULL + 2,
+                         DRAIN = T2FULL + 2, GREADY = DRAIN + 1, N = GREADY + 2;
     static_assert(N * 8 + 8 <= 256, "barrier area");
 };
 
@@ -270,8 +287,8 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
     const uint32_t a2_base = smem_u32(smem + C::OFF_A2);
     int i = 0;
     for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
-        const int s = i % C::STAGES, b = i & 1;
-        const uint32_t ph_s = (i / C::STAGES) & 1, ph_b = (i >> 1) & 1;
+        const int s = i % C::STAGES, b = i % C::NB;
+        const uint32_t ph_s = (i / C::STAGES) & 1, ph_b = (i / C::NB) & 1;
         if (!mbar_wait(&tempty[b], ph_b ^ 1, abort) || !mbar_wait(&full[s], ph_s, abort)) { ok = false; break; }
         tc_fence_after();
         issue_conv<C>(tmem + b * C::COLS_BUF, a_base + s * C::A_STAGE, w_base);
@@ -279,21 +296,21 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
         mma_commit(&tfull[b]);
         if constexpr (C::EPI == EPI_UP) {
             if (i > 0) {
-                const int bp = (i - 1) & 1;
-                if (!mbar_wait(&a2full[bp], ((i - 1) >> 1) & 1, abort)) { ok = false; break; }
+                const int bp = (i - 1) % C::NB, ap = (i - 1) & 1;
+                if (!mbar_wait(&a2full[ap], ((i - 1) >> 1) & 1, abort)) { ok = false; break; }
                 tc_fence_after();
-                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + bp * C::A2_BYTES, w2_base);
-                mma_commit(&t2full[bp]);
+                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + ap * C::A2_BYTES, w2_base);
+                mma_commit(&t2full[ap]);
             }
         }
     }
     if constexpr (C::EPI == EPI_UP) {
         if (ok && i > 0) {
-            const int bp = (i - 1) & 1;
-            if (mbar_wait(&a2full[bp], ((i - 1) >> 1) & 1, abort)) {
+            const int bp = (i - 1) % C::NB, ap = (i - 1) & 1;
+            if (mbar_wait(&a2full[ap], ((i - 1) >> 1) & 1, abort)) {
                 tc_fence_after();
-                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + bp * C::A2_BYTES, w2_base);
-                mma_commit(&t2full[bp]);
+                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + ap * C::A2_BYTES, w2_base);
+                mma_commit(&t2full[ap]);
             } else {
                 ok = false;
             }
@@ -318,6 +335,8 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                 *scs2 = scs + C::COUT, *sfin = par + 2 * (C::COUT + C::N2);
     const int q = warp & 3;                         // TMEM lane quarter of this warp
     const int m = q * 32 + lane;                    // tile row
+    const int wg = (warp - 2) >> 2;                 // epilogue warpgroup: column half
+    const int cbeg = wg * C::EPI_COLS;
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
     const int ntiles = a.n_events * C::TPE;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
@@ -326,8 +345,8 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
     constexpr int PUP = C::EPI == EPI_UP ? C::CUP / C::PW : 1;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int b = i & 1;
-        const uint32_t ph_b = (i >> 1) & 1;
+        const int b = i % C::NB, ab = i & 1;
+        const uint32_t ph_b = (i / C::NB) & 1, ph_a = (i >> 1) & 1;
         int e, p0;
         tile_pos<C>(t, e, p0);
         const int p = p0 + m;
@@ -354,12 +373,12 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                 for (int j = 0; j < 16; ++j) acc = fmaf(sfin[tp * kC0 + j], v[j], acc);
                 g[tp] = acc;
             }
-            float *sg = reinterpret_cast<float *>(smem + C::OFF_G) + b * 5 * kTileM;
+            float *sg = reinterpret_cast<float *>(smem + C::OFF_G) + ab * 5 * kTileM;
 #pragma unroll
             for (int tp = 0; tp < 5; ++tp) sg[tp * kTileM + m] = g[tp];
             // neighbours' partial sums: a bounded mbarrier among the 128 epilogue threads
-            mbar_arrive(&gready[b]);
-            if (!mbar_wait(&gready[b], ph_b, abort)) return false;
+            mbar_arrive(&gready[ab]);
+            if (!mbar_wait(&gready[ab], ph_a, abort)) return false;
             if (m >= kPad && m < kTileM - kPad && valid) {
                 // f(p) = b + sum_t g_t(p + t - 2), in tap order
                 float f = sfin[5 * kC0];
@@ -369,36 +388,46 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             }
             continue;
         }
+        // this warpgroup's conv columns, LDW at a time with one wait each
 #pragma unroll 1
-        for (int c0 = 0; c0 < C::COUT; c0 += 16) {
-            float v[16];
-            tmem_ld16(dcol + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[c0 + j];
-                v[j] = leaky(fmaf(v[j], sc, sbias[c0 + j]));
-            }
-            if constexpr (C::EPI == EPI_UP) {
-                if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
-                unsigned char *a2 = smem + C::OFF_A2 + b * C::A2_BYTES;
-                put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
+        for (int cc = 0; cc < C::EPI_COLS; cc += C::LDW) {
+            float vv[C::LDW];
+            if constexpr (C::LDW == 32) {
+                tmem_ld32(dcol + cbeg + cc, vv);
             } else {
-                if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
-                if (valid)
-                    put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
-                              (size_t)C::ROWS_E * 16, v, a.out_inv);
-                if constexpr (C::EPI == EPI_POOL) {
-                    float w[16];
+                tmem_ld16(dcol + cbeg + cc, vv);
+            }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
-                    if (valid && (m & 1) == 0)
-                        put16<ES>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
-                                  (size_t)ROWS_P * 16, w, a.out_inv);
+            for (int h = 0; h < C::LDW / 16; ++h) {
+                const int c0 = cbeg + cc + 16 * h;
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[c0 + j];
+                    v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias[c0 + j]));
+                }
+                if constexpr (C::EPI == EPI_UP) {
+                    if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
+                    unsigned char *a2 = smem + C::OFF_A2 + ab * C::A2_BYTES;
+                    put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
+                } else {
+                    if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
+                    if (valid)
+                        put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
+                                  (size_t)C::ROWS_E * 16, v, a.out_inv);
+                    if constexpr (C::EPI == EPI_POOL) {
+                        float w[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                        if (valid && (m & 1) == 0)
+                            put16<ES>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
+                                      (size_t)ROWS_P * 16, w, a.out_inv);
+                    }
                 }
             }
         }
         if constexpr (C::EPI != EPI_UP) {
-            if (p == 0) {
+            if (p == 0 && wg == 0) {
                 zero_planes(a.out, e, C::POUT, C::ROWS_E, 0);
                 zero_planes(a.out, e, C::POUT, C::ROWS_E, 1);
                 if constexpr (C::EPI == EPI_POOL) {
@@ -406,7 +435,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                     zero_planes(a.outp, e, C::POUT, ROWS_P, 1);
                 }
             }
-            if (p == C::L - 1) {
+            if (p == C::L - 1 && wg == 0) {
                 zero_planes(a.out, e, C::POUT, C::ROWS_E, C::L + kPad);
                 zero_planes(a.out, e, C::POUT, C::ROWS_E, C::L + kPad + 1);
                 if constexpr (C::EPI == EPI_POOL) {
@@ -416,29 +445,42 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             }
         } else {
             fence_proxy_async_smem();               // A2 writes -> visible to the tensor core
-            mbar_arrive(&a2full[b]);
-            if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
+            mbar_arrive(&a2full[ab]);
+            if (!mbar_wait(&t2full[ab], ph_a, abort)) return false;
             tc_fence_after();
+            // ConvT columns n = r * CUP + co; warpgroup r (or the only one, both r) writes
+            // output row 2p + r
+            constexpr int N2W = C::N2 / C::EWG;
+            constexpr int LDW2 = (C::EWG == 2 && N2W % 32 == 0) ? 32 : 16;
 #pragma unroll 1
-            for (int c0 = 0; c0 < C::N2; c0 += 16) {
-                float v[16];
-                tmem_ld16(dcol + C::COUT + c0, v);
-                const int r = c0 / C::CUP, co0 = c0 % C::CUP;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float sc = C::PREC == PVF_BF16 ? 1.0f : scs2[c0 + j];
-                    v[j] = leaky(fmaf(v[j], sc, sbias2[co0 + j]));
+            for (int cc = 0; cc < N2W; cc += LDW2) {
+                float vv[LDW2];
+                if constexpr (LDW2 == 32) {
+                    tmem_ld32(dcol + C::COUT + wg * N2W + cc, vv);
+                } else {
+                    tmem_ld16(dcol + C::COUT + wg * N2W + cc, vv);
                 }
-                if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
-                if (valid)
-                    put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
-                              (size_t)ROWS_O * 16, v, a.out_inv);
+#pragma unroll
+                for (int h = 0; h < LDW2 / 16; ++h) {
+                    const int c0 = wg * N2W + cc + 16 * h;
+                    const int r = c0 / C::CUP, co0 = c0 % C::CUP;
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float sc = C::PREC == PVF_BF16 ? 1.0f : scs2[c0 + j];
+                        v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias2[co0 + j]));
+                    }
+                    if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
+                    if (valid)
+                        put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
+                                  (size_t)ROWS_O * 16, v, a.out_inv);
+                }
             }
-            if (p == 0) {
+            if (p == 0 && wg == 0) {
                 zero_planes(a.out, e, PUP, ROWS_O, 0);
                 zero_planes(a.out, e, PUP, ROWS_O, 1);
             }
-            if (p == C::L - 1) {
+            if (p == C::L - 1 && wg == 0) {
                 zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
                 zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
             }
@@ -450,7 +492,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
 }
 
 template <class C>
-__global__ void __launch_bounds__(kThreadsTc, 1) k_conv_tc(TcArgs a) {
+__global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(TcArgs a) {
     using B = Bars<C>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
@@ -460,7 +502,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_conv_tc(TcArgs a) {
 
     // biases, column scales and the final conv in shared memory
     float *par = reinterpret_cast<float *>(smem + C::OFF_PAR);
-    for (int k = threadIdx.x; k < C::NPAR; k += kThreadsTc) {
+    for (int k = threadIdx.x; k < C::NPAR; k += C::THREADS) {
         float v;
         if (k < C::COUT) v = a.bias[k];
         else if (k < C::COUT + C::N2) v = a.bias2[(k - C::COUT) % (C::CUP > 0 ? C::CUP : 1)];
@@ -475,10 +517,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_conv_tc(TcArgs a) {
             mbar_init(&bar[B::FULL + s], 1);
             mbar_init(&bar[B::EMPTY + s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::NB; ++b) {
             mbar_init(&bar[B::TFULL + b], 1);
-            mbar_init(&bar[B::TEMPTY + b], 128);
-            mbar_init(&bar[B::A2FULL + b], 128);
+            mbar_init(&bar[B::TEMPTY + b], 128 * C::EWG);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar[B::A2FULL + b], 128 * C::EWG);
             mbar_init(&bar[B::T2FULL + b], 1);
         }
         mbar_init(&bar[B::DRAIN], 1);
@@ -543,12 +587,12 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
         cudaFuncAttributes fa;
         err = cudaFuncGetAttributes(&fa, k_conv_tc<C>);
         if (err != cudaSuccess) return err;
-        // resident CTAs per SM from registers (allocated per warp in units of 256),
-        // shared memory (+1 KB reserved per CTA), threads and TMEM columns
+        // resident CTAs per SM: registers (each of the 4 sub-partitions holds 16K, allocated
+        // per warp in units of 256), shared memory (+1 KB reserved per CTA), threads, TMEM
         const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
-        const int by_regs = 65536 / (warp_regs * (kThreadsTc / 32));
+        const int by_regs = 4 * (16384 / warp_regs) / (C::THREADS / 32);
         const int by_smem = kSmemPerSm / (smem + 1024);
-        const int by_threads = 2048 / kThreadsTc;
+        const int by_threads = 2048 / C::THREADS;
         int n = by_regs < by_smem ? by_regs : by_smem;
         if (by_threads < n) n = by_threads;
         if (kMaxByTmem < n) n = kMaxByTmem;
@@ -558,19 +602,19 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
     int grid = sm_count() * per_sm;
     if (grid > ntiles) grid = ntiles;
     ProfScope ps(prof, name, s);
-    k_conv_tc<C><<<grid, kThreadsTc, smem, s>>>(a);
+    k_conv_tc<C><<<grid, C::THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- weight packing (host)
 
 template <int PREC> struct Net {
-    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4>;
-    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4>;
-    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4>;
-    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3>;
-    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3>;
-    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4>;
+    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56>;    // 6 CTAs per SM
+    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80>;    // 4
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4, 2>;
+    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4>;   // 1 CTA per SM
+    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4>;   // 2
+    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4>;   // 4
 };
 
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
@@ -681,16 +725,18 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
         off_s[li] = pk.put_raw(cs.data(), cs.size() * sizeof(float));
     }
     // FC images (bf16 in both forms): element (out o, in i) of layer l at
-    // ((i / 8) * N + o) * 16 + (i % 8) * 2 of the layer's image
+    // ((i / 8) * R + row) * 16 + (i % 8) * 2 of the layer's image, R rows per plane;
+    // row = o for layers 1-5 (R = 32), fc6_row(o) for layer 6 (R = 128)
     std::vector<unsigned char> fcimg(kFcImgBytes, 0);
     for (int l = 0; l < 6; ++l) {
         const LayerF32 &Lw = layers[l];
         const int nout = (int)Lw.shape[0], nin = (int)Lw.shape[1];
-        const int n = l < 5 ? kFcHidden : kFcN6;
+        const int rows = l < 5 ? kFcHidden : kFcM6;
         for (int o = 0; o < nout; ++o)
             for (int i = 0; i < nin; ++i) {
                 __nv_bfloat16 hv = __float2bfloat16_rn(Lw.w[(size_t)o * nin + i]);
-                std::memcpy(&fcimg[fc_img_off(l) + ((i / 8) * n + o) * 16 + (i % 8) * 2], &hv, 2);
+                const int row = l < 5 ? o : fc6_row(o);
+                std::memcpy(&fcimg[fc_img_off(l) + ((i / 8) * rows + row) * 16 + (i % 8) * 2], &hv, 2);
             }
     }
     const size_t off_fc = pk.put_raw(fcimg.data(), fcimg.size());

@@ -51,14 +51,18 @@ __host__ __device__ constexpr int fc_b_off(int l) {
     return kFcWTotal + (l < 5 ? l * kFcHidden : 5 * kFcHidden);
 }
 
-// FC weights of the tensor-core forms: bf16 images of the tcgen05 B operands (K-major
-// planes of 8 inputs x N rows x 16 bytes). Layer 1: K = 16 (nine features, zeros), N = 32;
-// layers 2-5: K = 32, N = 32; layer 6: K = 32, N = 112 (outputs 100..111 are zero rows).
-constexpr int kFcN6 = 112;
+// FC weights of the tensor-core forms: bf16 images of K-major tcgen05 operands (planes of
+// 8 inputs x rows x 16 bytes). Layers 1-5 are B operands with N = 32 rows (layer 1:
+// K = 16, nine features then zeros; layers 2-5: K = 32). Layer 6 is the A operand of the
+// transposed product (outputs on TMEM lanes): M = 128 rows, K = 32, output o on row
+// 32 (o / 25) + o % 25 so that each warp's lane quarter holds 25 outputs; other rows zero.
+constexpr int kFcM6 = 128;
+constexpr int kFcOutPerWarp = 25;
+__host__ __device__ constexpr int fc6_row(int o) { return 32 * (o / kFcOutPerWarp) + o % kFcOutPerWarp; }
 constexpr int kFcImgW1 = 2 * kFcHidden * 16;
 constexpr int kFcImgWH = 4 * kFcHidden * 16;
-constexpr int kFcImgW6 = 4 * kFcN6 * 16;
-constexpr int kFcImgBytes = kFcImgW1 + 4 * kFcImgWH + kFcImgW6;   // 16384
+constexpr int kFcImgW6 = 4 * kFcM6 * 16;
+constexpr int kFcImgBytes = kFcImgW1 + 4 * kFcImgWH + kFcImgW6;   // 17408
 __host__ __device__ constexpr int fc_img_off(int l) {
     return l == 0 ? 0 : (l < 5 ? kFcImgW1 + (l - 1) * kFcImgWH : kFcImgW1 + 4 * kFcImgWH);
 }
