@@ -119,10 +119,10 @@ __device__ __forceinline__ void track_features(const FrontArgs &a, int64_t gt, i
 }
 
 // Step f: e1 = LeakyReLU(conv_k5(hist) + b), p1 = maxpool2(e1), stored in the form's
-// precision with the pad rows zeroed; calibration folds max |e1| into a.amax[0].
-template <class T, int NT>
-__device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, const float *shist,
-                                          const float *senc) {
+// precision with the pad rows zeroed; calibration (AMAX) folds max |e1| into a.amax[0].
+template <class T, int NT, bool AMAX>
+__device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, const float *shist,
+                                            const float *senc) {
     const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
     float vmax = 0.0f;
@@ -134,24 +134,36 @@ __device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, co
             hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
         }
         float v0[kC0], v1[kC0], vp[kC0];
+        // weights read four channels at a time (senc is 16-byte aligned)
+        const float4 *w4 = reinterpret_cast<const float4 *>(senc);
 #pragma unroll
-        for (int co = 0; co < kC0; ++co) {
-            float a0 = senc[5 * kC0 + co], a1 = a0;
+        for (int c4 = 0; c4 < kC0 / 4; ++c4) {
+            const float4 bb = w4[5 * (kC0 / 4) + c4];
+            float a0[4] = {bb.x, bb.y, bb.z, bb.w}, a1[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
             for (int t = 0; t < 5; ++t) {
-                a0 = fmaf(senc[t * kC0 + co], hv[t], a0);
-                a1 = fmaf(senc[t * kC0 + co], hv[t + 1], a1);
+                const float4 w = w4[t * (kC0 / 4) + c4];
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a0[j] = fmaf(wv[j], hv[t], a0[j]);
+                    a1[j] = fmaf(wv[j], hv[t + 1], a1[j]);
+                }
             }
-            v0[co] = leaky(a0);
-            v1[co] = leaky(a1);
-            vp[co] = fmaxf(v0[co], v1[co]);
-            vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int co = 4 * c4 + j;
+                v0[co] = leaky(a0[j]);
+                v1[co] = leaky(a1[j]);
+                vp[co] = fmaxf(v0[co], v1[co]);
+                if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
+            }
         }
         store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
         store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
         store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
     }
-    if (a.amax) {   // calibration: integer max on the float bits (order-independent)
+    if constexpr (AMAX) {   // calibration: integer max on the float bits (order-independent)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
@@ -162,6 +174,13 @@ __device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, co
         const int rp = tid < 2 ? tid : kBins / 2 + tid;
         zero_row16<T>(a.p1, e, rows2, rp);
     }
+}
+
+template <class T, int NT>
+__device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, const float *shist,
+                                          const float *senc) {
+    if (a.amax) enc1_pool_t<T, NT, true>(a, e, tid, shist, senc);
+    else enc1_pool_t<T, NT, false>(a, e, tid, shist, senc);
 }
 
 }  // namespace front

@@ -42,6 +42,7 @@ struct FrontSmem {
     __host__ __device__ static size_t slices(int max_tracks) { return sorted + 2 * (size_t)((max_tracks + 7) / 8 * 8); }
     __host__ __device__ static size_t total(int max_tracks) { return slices(max_tracks) + (size_t)max_tracks + 16; }
 };
+static_assert(FrontSmem::enc1 % 16 == 0, "enc1 weights are read as float4");
 
 // Hidden layers 1-5 of the FC net for one track; writes h5 (32 floats) to h_row.
 __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const float x[kFcInPad],
@@ -92,7 +93,7 @@ __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const flo
 
 // ENC1 = false: steps a-e only (the histogram), nothing written to e1/p1.
 template <int PREC, bool ENC1 = true>
-__global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_front(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     float *sfc = reinterpret_cast<float *>(smem + FrontSmem::fc);

@@ -48,6 +48,7 @@ struct TcSmem {
     __host__ __device__ static size_t slices(int mt) { return sorted + 2 * (size_t)((mt + 7) / 8 * 8); }
     __host__ __device__ static size_t total(int mt) { return slices(mt) + (size_t)mt + 16; }
 };
+static_assert(TcSmem::enc1 % 16 == 0, "enc1 weights are read as float4");
 
 __device__ __forceinline__ uint4 pack8_bf16(const float *v) {
     uint4 r;
@@ -57,23 +58,15 @@ __device__ __forceinline__ uint4 pack8_bf16(const float *v) {
     return r;
 }
 
-// softplus(x) = max(x, 0) + log1p(u), u = exp(-|x|) in (0, 1], for the tensor-core forms.
-// log1p(u) = 2 atanh(t) with t = u / (2 + u) in (0, 1/3], summed as the odd power series
-// of atanh, 2 t (1 + t^2/3 + ... + t^12/13): the first omitted term is below 2e-8
-// relative, under the error of the fast exponential (about 1e-6 relative at |x| = 20).
-// Large |x| needs no special case: u underflows smoothly and t ~ u / 2.
+// softplus(x) = max(x, 0) + log(1 + u), u = exp(-|x|) in (0, 1], for the tensor-core forms
+// (their FC operands are bf16): the hardware exp2/log2 approximations give it in a few
+// instructions with an absolute error of a few 1e-7. Below x = -15 the value is u itself
+// (log(1 + u) = u to 1e-7 relative), which keeps tiny terms positive instead of rounding
+// 1 + u to 1.
 __device__ __forceinline__ float softplus_tc(float x) {
     const float u = __expf(-fabsf(x));
-    const float t = __fdividef(u, 2.0f + u);
-    const float q = t * t;
-    float p = 1.0f / 13.0f;
-    p = fmaf(p, q, 1.0f / 11.0f);
-    p = fmaf(p, q, 1.0f / 9.0f);
-    p = fmaf(p, q, 1.0f / 7.0f);
-    p = fmaf(p, q, 1.0f / 5.0f);
-    p = fmaf(p, q, 1.0f / 3.0f);
-    p = fmaf(p, q, 1.0f);
-    return fmaf(2.0f * t, p, fmaxf(x, 0.0f));
+    const float l = fmaf(__log2f(1.0f + u), 0.69314718f, fmaxf(x, 0.0f));
+    return x < -15.0f ? u : l;
 }
 
 template <int PREC>
@@ -212,7 +205,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                         continue;
                     }
                     // output layer: warpgroup g adds its bin over pass rows [cb, ce) in order
-                    const int half = (nrow + 31) / 32 * 16;
+                    const int half = min(nrow, (nrow + 63) / 64 * 32);   // a multiple of 32
                     const int cb = g == 0 ? 0 : half, ce = g == 0 ? min(half, nrow) : nrow;
                     float acc = 0.0f, held = 0.0f;
                     int held_s = -1;

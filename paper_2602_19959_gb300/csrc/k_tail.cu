@@ -59,8 +59,10 @@ __device__ __forceinline__ void load_row16(const void *base, int64_t e, int64_t 
 
 __device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
 
-template <int PREC>
-__global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
+// CONV: the logit comes from the final conv over d1 (the float32 form); otherwise it is read
+// from a.logit_in. Without the conv the kernel fits eight CTAs per SM.
+template <int PREC, bool CONV>
+__global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
     using T = typename Elem<PREC>::T;
     __shared__ __align__(16) float sf[kThreads * kPerThread];
     __shared__ float sw[kFinalFloats];
@@ -68,14 +70,14 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    if (!a.logit_in) {
+    if constexpr (CONV) {
         for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
         __syncthreads();
     }
     // persistent: the CTA walks the launch's events
     for (int e = blockIdx.x; e < a.n_events; e += gridDim.x) {
         const int ge = a.ev_base + e;
-        if (a.logit_in) {
+        if constexpr (!CONV) {
             const float *src = a.logit_in + (size_t)(ge - a.logit_in_base) * kBins;
             for (int p = tid; p < kBins; p += kThreads) sf[p] = src[p];
         } else {
@@ -172,7 +174,8 @@ __global__ void __launch_bounds__(kThreads) k_tail(TailArgs a) {
 
 cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    // persistent grid: four CTAs per SM, each walking events
+    // persistent grid of resident CTAs (their launch bounds fix the registers: two per SM
+    // with the final conv, eight without), each walking events
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -180,11 +183,16 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 1;
     }
-    dim3 grid(a.n_events < 4 * sms ? a.n_events : 4 * sms), block(kThreads);
-    switch (precision) {
-    case PVF_FP32: k_tail<PVF_FP32><<<grid, block, 0, s>>>(a); break;
-    case PVF_BF16: k_tail<PVF_BF16><<<grid, block, 0, s>>>(a); break;
-    default: k_tail<PVF_FP8_E4M3><<<grid, block, 0, s>>>(a); break;
+    const int per_sm = a.logit_in ? 8 : 2;
+    dim3 grid(a.n_events < per_sm * sms ? a.n_events : per_sm * sms), block(kThreads);
+    if (a.logit_in) {
+        k_tail<PVF_FP32, false><<<grid, block, 0, s>>>(a);
+    } else {
+        switch (precision) {
+        case PVF_FP32: k_tail<PVF_FP32, true><<<grid, block, 0, s>>>(a); break;
+        case PVF_BF16: k_tail<PVF_BF16, true><<<grid, block, 0, s>>>(a); break;
+        default: k_tail<PVF_FP8_E4M3, true><<<grid, block, 0, s>>>(a); break;
+        }
     }
     return cudaGetLastError();
 }
