@@ -498,7 +498,7 @@ def main():
                     help="serving sample folded into the step line (0: none)")
     ap.add_argument("--serve-rate", type=float, default=120000.0)
     ap.add_argument("--serve-batch", type=int, default=128)
-    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-inflight", type=int, default=2)
     ap.add_argument("--serve-seconds-full", type=float, default=10.0)
     ap.add_argument("--rates", type=float, nargs="+", default=[20000, 60000, 120000, 200000])
     args = ap.parse_args()

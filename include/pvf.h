@@ -231,17 +231,24 @@ PVF_API pvf_status pvf_graph_destroy(pvf_graph *g);
  * Requests are events of a host-side event store, arriving at given times. Whenever
  * fewer than max_inflight batches are enqueued on the stream, the loop admits the queued
  * events that fit one in-flight slot (at most max_batch events and max_tracks_per_batch
- * tracks: the slot's memory), packs their tracks into pinned staging, and enqueues one
- * host->device copy, pvf_infer and the copies of PV counts and z lists back, all on
- * `stream`. A batch is launched as soon as a slot is free and min_batch events are
- * queued, or the oldest queued event has waited max_wait_us, or no more arrivals remain. */
+ * tracks: the slot's memory), packs their tracks into pinned staging, and enqueues on
+ * `stream` the host->device copies, the path, and the copies of PV counts and z lists
+ * back. A batch is launched as soon as a slot is free and min_batch events are queued, or
+ * the oldest queued event has waited max_wait_us, or no more arrivals remain.
+ * By default the path runs as a CUDA graph: before the first arrival the loop captures,
+ * for every slot, one graph per bucket of 1, 2, 4, ... events up to max_batch (tracks at
+ * a fixed stride of max_tracks_per_batch), and a batch of k events launches the graph of
+ * the smallest bucket >= k with the missing events empty. PVF_SERVE_STREAM_LAUNCH
+ * enqueues pvf_infer instead. */
+#define PVF_SERVE_STREAM_LAUNCH 1
 typedef struct {
     int32_t max_batch;            /* events per launch, 1..max_events of the handle      */
     int32_t max_tracks_per_batch; /* tracks per launch; every stored event must fit       */
     int32_t max_inflight;         /* batches enqueued at once, 1..16                      */
     int32_t min_batch;            /* >= 1                                                 */
     float max_wait_us;            /* batching window for the oldest queued event          */
-    int32_t reserved[3];
+    int32_t flags;                /* 0 or PVF_SERVE_STREAM_LAUNCH                         */
+    int32_t reserved[2];
 } pvf_serve_config;
 
 /* Device bytes the in-flight slots need (inputs and outputs of max_inflight batches). */
@@ -257,8 +264,9 @@ PVF_API pvf_status pvf_serve_bytes_required(const pvf_serve_config *cfg, int32_t
  *   out_pv_count[i]            its PV count (-1 = bypassed), or NULL
  *   out_pv_z                   host float[n_requests * max_pv_per_event]: its z list, or NULL
  *   out_batches                number of launches, or NULL
- * Pinned host staging (one slot's size per in-flight batch) is allocated for the call
- * and freed before it returns; no device memory is allocated. */
+ * Pinned host staging (one slot's size per in-flight batch) and the graphs are created
+ * for the call and freed before it returns; no device memory is allocated. The graphs use
+ * the handle's pool like pvf_infer, so the handle serves one call at a time. */
 PVF_API pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg,
                                     const float *const *store_f, const int32_t *store_offsets,
                                     int32_t n_store, const int64_t *arrival_ns,

@@ -134,30 +134,18 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
             hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
         }
         float v0[kC0], v1[kC0], vp[kC0];
-        // weights read four channels at a time (senc is 16-byte aligned)
-        const float4 *w4 = reinterpret_cast<const float4 *>(senc);
 #pragma unroll
-        for (int c4 = 0; c4 < kC0 / 4; ++c4) {
-            const float4 bb = w4[5 * (kC0 / 4) + c4];
-            float a0[4] = {bb.x, bb.y, bb.z, bb.w}, a1[4] = {bb.x, bb.y, bb.z, bb.w};
+        for (int co = 0; co < kC0; ++co) {
+            float a0 = senc[5 * kC0 + co], a1 = a0;
 #pragma unroll
             for (int t = 0; t < 5; ++t) {
-                const float4 w = w4[t * (kC0 / 4) + c4];
-                const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    a0[j] = fmaf(wv[j], hv[t], a0[j]);
-                    a1[j] = fmaf(wv[j], hv[t + 1], a1[j]);
-                }
+                a0 = fmaf(senc[t * kC0 + co], hv[t], a0);
+                a1 = fmaf(senc[t * kC0 + co], hv[t + 1], a1);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int co = 4 * c4 + j;
-                v0[co] = leaky(a0[j]);
-                v1[co] = leaky(a1[j]);
-                vp[co] = fmaxf(v0[co], v1[co]);
-                if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
-            }
+            v0[co] = leaky(a0);
+            v1[co] = leaky(a1);
+            vp[co] = fmaxf(v0[co], v1[co]);
+            if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
         }
         store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
         store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);

@@ -42,7 +42,6 @@ struct FrontSmem {
     __host__ __device__ static size_t slices(int max_tracks) { return sorted + 2 * (size_t)((max_tracks + 7) / 8 * 8); }
     __host__ __device__ static size_t total(int max_tracks) { return slices(max_tracks) + (size_t)max_tracks + 16; }
 };
-static_assert(FrontSmem::enc1 % 16 == 0, "enc1 weights are read as float4");
 
 // Hidden layers 1-5 of the FC net for one track; writes h5 (32 floats) to h_row.
 __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const float x[kFcInPad],

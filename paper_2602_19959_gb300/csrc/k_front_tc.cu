@@ -48,7 +48,6 @@ struct TcSmem {
     __host__ __device__ static size_t slices(int mt) { return sorted + 2 * (size_t)((mt + 7) / 8 * 8); }
     __host__ __device__ static size_t total(int mt) { return slices(mt) + (size_t)mt + 16; }
 };
-static_assert(TcSmem::enc1 % 16 == 0, "enc1 weights are read as float4");
 
 __device__ __forceinline__ uint4 pack8_bf16(const float *v) {
     uint4 r;

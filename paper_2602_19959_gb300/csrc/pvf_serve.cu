@@ -4,11 +4,16 @@
 // enqueued, the loop admits the queued events that fit one slot -- at most max_batch
 // events and max_tracks_per_batch tracks, the slot's share of the caller's device
 // memory -- packs their Structure-of-Arrays tracks into the slot's pinned staging
-// buffer, and enqueues on the single stream: one host->device copy, pvf_infer, and the
+// buffer, and enqueues on the single stream: the host->device copies, the path, and the
 // copies of the PV counts and z lists back. Batches run in stream order while the host
 // packs the next ones, so requests that arrive while others are on the GPU are taken as
 // slots free up. A CUDA event per slot is polled for completion; each request's
 // completion time is the host time at which its batch was observed done.
+//
+// The path runs as a CUDA graph per (slot, bucket): the slot's tracks sit at a fixed
+// stride of max_tracks_per_batch floats per feature, so one graph of B events serves
+// every batch of k <= B events (offsets k+1..B repeat the track count: empty events).
+// Buckets are 1, 2, 4, ... and max_batch; the graphs are captured before the clock starts.
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -19,10 +24,13 @@
 namespace pvf {
 namespace {
 
+constexpr int kMaxBuckets = 16;
+
 struct Slot {
-    unsigned char *host = nullptr;   // pinned: [9][nt] features | offsets | counts | z
+    unsigned char *host = nullptr;   // pinned: [9][MT] features | offsets | counts | z
     unsigned char *dev = nullptr;    // caller's device memory, same layout
     cudaEvent_t done = nullptr;
+    pvf_graph *graph[kMaxBuckets] = {};
     int r0 = 0, r1 = 0;              // requests [r0, r1) of this batch
     int nt = 0;                      // tracks packed
     bool busy = false;
@@ -82,12 +90,37 @@ pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg, const fl
     const size_t off_z = (off_counts + sizeof(int32_t) * MB + 255) / 256 * 256;
 
     std::vector<Slot> slots(cfg->max_inflight);
+    const bool use_graphs = !(cfg->flags & PVF_SERVE_STREAM_LAUNCH);
+    std::vector<int> buckets;            // 1, 2, 4, ... < MB, then MB
+    for (int b = 1; b < MB; b *= 2) buckets.push_back(b);
+    buckets.push_back(MB);
+    if ((int)buckets.size() > kMaxBuckets) return PVF_ERR_INVALID_ARG;
+    // fixed layout of a slot: feature f at f * MT floats, then the offsets
+    auto slot_tracks = [&](const Slot &sl) {
+        pvf_tracks_soa tr;
+        float *df = reinterpret_cast<float *>(sl.dev);
+        for (int f = 0; f < 9; ++f) tr.f[f] = df + (size_t)f * MT;
+        tr.n_tracks = MT;
+        return tr;
+    };
+    const size_t off_offsets = sizeof(float) * 9 * (size_t)MT;
     pvf_status st = PVF_OK;
     for (size_t i = 0; i < slots.size() && st == PVF_OK; ++i) {
-        slots[i].dev = static_cast<unsigned char *>(device_slots) + i * sb;
-        if (cudaHostAlloc(&slots[i].host, sb, cudaHostAllocDefault) != cudaSuccess ||
-            cudaEventCreateWithFlags(&slots[i].done, cudaEventDisableTiming) != cudaSuccess)
+        Slot &sl = slots[i];
+        sl.dev = static_cast<unsigned char *>(device_slots) + i * sb;
+        if (cudaHostAlloc(&sl.host, sb, cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
             st = PVF_ERR_CUDA;
+            break;
+        }
+        if (use_graphs) {
+            const pvf_tracks_soa tr = slot_tracks(sl);
+            int32_t *doff = reinterpret_cast<int32_t *>(sl.dev + off_offsets);
+            int32_t *dcnt = reinterpret_cast<int32_t *>(sl.dev + off_counts);
+            float *dz = reinterpret_cast<float *>(sl.dev + off_z);
+            for (size_t b = 0; b < buckets.size() && st == PVF_OK; ++b)
+                st = pvf_graph_create(h, &tr, doff, buckets[b], dz, dcnt, &sl.graph[b]);
+        }
     }
     std::vector<int32_t> batch_offsets(MB + 1);
     using clock = std::chrono::steady_clock;
@@ -139,34 +172,43 @@ pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg, const fl
                     batch_offsets[++k] = ntr;
                     ++r;
                 }
-                // pack [9][ntr] features, then the offsets, contiguously
+                size_t bi = 0;
+                while (use_graphs && buckets[bi] < k) ++bi;
+                const int kb = use_graphs ? buckets[bi] : k;     // events launched
+                for (int i = k + 1; i <= kb; ++i) batch_offsets[i] = ntr;
+                // pack feature f of the batch at f * MT floats, then the offsets
                 float *hf = reinterpret_cast<float *>(sl.host);
                 for (int f = 0; f < 9; ++f) {
-                    float *dst = hf + (size_t)f * ntr;
+                    float *dst = hf + (size_t)f * MT;
                     for (int i = 0; i < k; ++i) {
                         const int ev = request_event[q_head + i];
                         const int a = store_offsets[ev], nt = store_offsets[ev + 1] - a;
                         std::memcpy(dst + batch_offsets[i], store_f[f] + a, sizeof(float) * nt);
                     }
                 }
-                int32_t *ho = reinterpret_cast<int32_t *>(hf + (size_t)9 * ntr);
-                std::memcpy(ho, batch_offsets.data(), sizeof(int32_t) * (k + 1));
-                const size_t in_bytes = sizeof(float) * 9 * (size_t)ntr + sizeof(int32_t) * (k + 1);
-                pvf_tracks_soa tr;
-                float *df = reinterpret_cast<float *>(sl.dev);
-                for (int f = 0; f < 9; ++f) tr.f[f] = df + (size_t)f * ntr;
-                tr.n_tracks = ntr;
-                int32_t *doff = reinterpret_cast<int32_t *>(df + (size_t)9 * ntr);
+                int32_t *ho = reinterpret_cast<int32_t *>(sl.host + off_offsets);
+                std::memcpy(ho, batch_offsets.data(), sizeof(int32_t) * (kb + 1));
+                const pvf_tracks_soa tr = slot_tracks(sl);
+                int32_t *doff = reinterpret_cast<int32_t *>(sl.dev + off_offsets);
                 int32_t *dcnt = reinterpret_cast<int32_t *>(sl.dev + off_counts);
                 float *dz = reinterpret_cast<float *>(sl.dev + off_z);
-                if (ntr == 0) {      // an all-empty batch still needs valid feature pointers
-                    for (int f = 0; f < 9; ++f) tr.f[f] = df;
+                bool ok = true;
+                if (ntr > 0)   // the batch's tracks of each feature row, one strided copy
+                    ok = cudaMemcpy2DAsync(sl.dev, sizeof(float) * MT, sl.host, sizeof(float) * MT,
+                                           sizeof(float) * ntr, 9, cudaMemcpyHostToDevice, s) == cudaSuccess;
+                ok = ok && cudaMemcpyAsync(doff, ho, sizeof(int32_t) * (kb + 1), cudaMemcpyHostToDevice,
+                                           s) == cudaSuccess;
+                if (ok) {
+                    ok = use_graphs ? pvf_graph_launch(sl.graph[bi], stream_) == PVF_OK
+                                    : pvf_infer(h, &tr, doff, k, dz, dcnt, stream_) == PVF_OK;
                 }
-                if (cudaMemcpyAsync(sl.dev, sl.host, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                    pvf_infer(h, &tr, doff, k, dz, dcnt, stream_) != PVF_OK ||
-                    cudaMemcpyAsync(sl.host + off_counts, dcnt, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                    cudaMemcpyAsync(sl.host + off_z, dz, sizeof(float) * (size_t)k * max_pv, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                    cudaEventRecord(sl.done, s) != cudaSuccess) {
+                ok = ok &&
+                     cudaMemcpyAsync(sl.host + off_counts, dcnt, sizeof(int32_t) * k, cudaMemcpyDeviceToHost,
+                                     s) == cudaSuccess &&
+                     cudaMemcpyAsync(sl.host + off_z, dz, sizeof(float) * (size_t)k * max_pv,
+                                     cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                     cudaEventRecord(sl.done, s) == cudaSuccess;
+                if (!ok) {
                     st = PVF_ERR_CUDA;
                     break;
                 }
@@ -182,6 +224,7 @@ pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg, const fl
     }
     if (st != PVF_OK) cudaStreamSynchronize(s);
     for (auto &sl : slots) {
+        for (int b = 0; b < kMaxBuckets; ++b) pvf_graph_destroy(sl.graph[b]);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.host) cudaFreeHost(sl.host);
     }

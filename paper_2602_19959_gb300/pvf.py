@@ -59,7 +59,10 @@ class PvfKernelTime(ctypes.Structure):
 class PvfServeConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("max_tracks_per_batch", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("min_batch", ctypes.c_int32),
-                ("max_wait_us", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("max_wait_us", ctypes.c_float), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+SERVE_STREAM_LAUNCH = 1
 
 
 class PvfError(RuntimeError):
@@ -315,9 +318,10 @@ class PVFinder:
         return Graph(self.lib, g, (features, offsets, out))
 
     def serve_replay(self, store, arrival_ns, request_event, max_batch=128,
-                     max_tracks_per_batch=None, max_inflight=4, min_batch=1, max_wait_us=0.0,
-                     want_z=False, stream=None):
+                     max_tracks_per_batch=None, max_inflight=2, min_batch=1, max_wait_us=0.0,
+                     want_z=False, graphs=True, stream=None):
         """Continuous-batching replay (pvf_serve_replay). store: an EventBatch (host SoA).
+        graphs=False enqueues pvf_infer per batch instead of the per-bucket CUDA graphs.
         Returns (done_ns int64 [n], pv_count int32 [n], batches, z [n, max_pv] or None)."""
         import torch
         feats = np.ascontiguousarray(store.features, dtype=np.float32)
@@ -328,7 +332,7 @@ class PVFinder:
         if max_tracks_per_batch is None:
             max_tracks_per_batch = int(max(np.diff(offs).max(), 1) * max_batch)
         cfg = PvfServeConfig(max_batch, max_tracks_per_batch, max_inflight, min_batch,
-                             float(max_wait_us))
+                             float(max_wait_us), 0 if graphs else SERVE_STREAM_LAUNCH)
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_serve_bytes_required(ctypes.byref(cfg), self.max_pv, ctypes.byref(need)),
                "pvf_serve_bytes_required")
