@@ -20,9 +20,11 @@
 // tile per 128 positions into a ring of stages); warp 1 allocates TMEM and one thread
 // issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the MMAs
 // of tile i + 1); the remaining one or two warpgroups are the epilogue, one TMEM lane
-// (= output position) per thread. With two, they split the accumulator columns (for a
-// fused ConvT: warpgroup r writes output rows 2p + r), which doubles the epilogue
-// throughput of the kernels that fit one CTA per SM. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
+// (= output position) per thread. With a fused ConvT and two epilogue warpgroups they
+// split by role: one turns each conv accumulator into the ConvT's shared-memory operand,
+// the other stores the ConvT output and frees the accumulator buffer, so the operand of
+// tile i is ready while the tensor core still runs the conv of tile i + 1. Otherwise two
+// warpgroups split the accumulator columns. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include "pvf_tc.cuh"
 #include "tc_ptx.cuh"
@@ -65,9 +67,6 @@ struct Cfg {
     // TMEM accumulator buffers: the MMAs of tile i wait only for the epilogue of tile i - NB
     static constexpr int NB = NB_;
     static constexpr int EPI_COLS = COUT / EWG;              // conv columns per epilogue thread
-    // TMEM load width of the epilogue: 32 columns per wait where the split kernels have the
-    // registers; 16 keeps the many-CTA kernels' register count (and residency) low
-    static constexpr int LDW = (EWG == 2 && EPI_COLS % 32 == 0) ? 32 : 16;
     static constexpr int PA = CA / PW, PB = CB / PW, PIN = PA + PB, POUT = COUT / PW;
     // A single input plane is half an MMA's K (32 bytes): pair taps (2j, 2j+1) in one MMA
     // by pointing the K-adjacent core matrix at the next row; a 6th zero tap pads.
@@ -83,7 +82,10 @@ struct Cfg {
     static constexpr int P2 = COUT / PW;                     // K-planes of the fused GEMM
     static constexpr int W2_BYTES = EPI == EPI_UP ? P2 * N2 * 16 : 0;
     static constexpr int A2_BYTES = EPI == EPI_UP ? P2 * kTileM * 16 : 0;
-    static constexpr int COLS_BUF = COUT + N2;
+    // accumulator buffer: the fused ConvT writes its result over the conv columns, which
+    // the epilogue has read before the ConvT's operand is complete
+    static constexpr int COLS_BUF = COUT > N2 ? COUT : N2;
+    static constexpr int UP_OFF = 0;
     static constexpr int TMEM_COLS = pow2ceil(NB * COLS_BUF);
     // float parameters kept in shared memory: bias, bias2, column scales, final conv
     static constexpr int NPAR = 2 * (COUT + N2) + (EPI == EPI_FINAL ? kFinalFloats : 0);
@@ -110,6 +112,7 @@ struct Cfg {
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
     static_assert(EWG == 1 || (EWG == 2 && EPI != EPI_FINAL && EPI_COLS % 16 == 0), "column split");
+    static_assert(EPI != EPI_UP || N2 % 16 == 0, "ConvT columns in 16-column chunks");
 };
 
 struct TcArgs {
@@ -140,13 +143,15 @@ __device__ __forceinline__ void amax_fold(float *amax, int slot, const float (&v
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(amax + slot), __float_as_int(m));
 }
 
-// Barrier slots in shared memory (uint64 each). TFULL/TEMPTY follow the NB accumulator
-// buffers (tile i: buffer i % NB); A2FULL/T2FULL/GREADY follow the two shared-memory
-// buffers of the fused ConvT operand and of the final conv's exchange (tile i: i % 2).
+// Barrier slots in shared memory (uint64 each). TFULL/TEMPTY/T2FULL follow the NB
+// accumulator buffers (tile i: buffer i % NB), so none of them can complete a second
+// phase before its waiters have seen the first; A2FULL/GREADY follow the two
+// shared-memory buffers of the fused ConvT operand and of the final conv's exchange
+// (tile i: i % 2).
 template <class C> struct Bars {
     static constexpr int W = 0, FULL = 1, EMPTY = 1 + C::STAGES, TFULL = 1 + 2 * C::STAGES,
-                         TEMPTY = TFULL + C::NB, A2FULL = TEMPTY + C::NB, T2FULL = A2FULL + 2,
-                         DRAIN = T2FULL + 2, GREADY = DRAIN + 1, N = GREADY + 2;
+                         TEMPTY = TFULL + C::NB, T2FULL = TEMPTY + C::NB, A2FULL = T2FULL + C::NB,
+                         DRAIN = A2FULL + 2, GREADY = DRAIN + 1, N = GREADY + 2;
     static_assert(N * 8 + 8 <= 256, "barrier area");
 };
 
@@ -299,8 +304,8 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
                 const int bp = (i - 1) % C::NB, ap = (i - 1) & 1;
                 if (!mbar_wait(&a2full[ap], ((i - 1) >> 1) & 1, abort)) { ok = false; break; }
                 tc_fence_after();
-                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + ap * C::A2_BYTES, w2_base);
-                mma_commit(&t2full[ap]);
+                issue_up<C>(tmem + bp * C::COLS_BUF + C::UP_OFF, a2_base + ap * C::A2_BYTES, w2_base);
+                mma_commit(&t2full[bp]);
             }
         }
     }
@@ -309,8 +314,8 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
             const int bp = (i - 1) % C::NB, ap = (i - 1) & 1;
             if (mbar_wait(&a2full[ap], ((i - 1) >> 1) & 1, abort)) {
                 tc_fence_after();
-                issue_up<C>(tmem + bp * C::COLS_BUF + C::COUT, a2_base + ap * C::A2_BYTES, w2_base);
-                mma_commit(&t2full[ap]);
+                issue_up<C>(tmem + bp * C::COLS_BUF + C::UP_OFF, a2_base + ap * C::A2_BYTES, w2_base);
+                mma_commit(&t2full[bp]);
             } else {
                 ok = false;
             }
@@ -323,26 +328,115 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
     return ok;
 }
 
+// Epilogue pieces, one TMEM lane (tile row m, position p) per thread.
+// Conv columns [c_beg, c_beg + NC) of accumulator dcol: bias, LeakyReLU, then either the
+// fused ConvT's shared-memory operand (A2) or the stored output (+ the 2:1 max-pool).
+template <class C, int NC>
+__device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
+                                         const float *scs, uint32_t dcol, int c_beg, int ab, int e,
+                                         int p, int m, bool valid) {
+    constexpr int ES = C::ES;
+    constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad;
+    constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
+#pragma unroll 1
+    for (int cc = 0; cc < NC; cc += LDW) {
+        float vv[LDW];
+        if constexpr (LDW == 32) {
+            tmem_ld32(dcol + c_beg + cc, vv);
+        } else {
+            tmem_ld16(dcol + c_beg + cc, vv);
+        }
+#pragma unroll
+        for (int h = 0; h < LDW / 16; ++h) {
+            const int c0 = c_beg + cc + 16 * h;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[c0 + j];
+                v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias[c0 + j]));
+            }
+            if constexpr (C::EPI == EPI_UP) {
+                if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
+                unsigned char *a2 = smem + C::OFF_A2 + ab * C::A2_BYTES;
+                put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
+            } else {
+                if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
+                if (valid)
+                    put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
+                              (size_t)C::ROWS_E * 16, v, a.out_inv);
+                if constexpr (C::EPI == EPI_POOL) {
+                    float w[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                    if (valid && (m & 1) == 0)
+                        put16<ES>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
+                                  (size_t)ROWS_P * 16, w, a.out_inv);
+                }
+            }
+        }
+    }
+}
+
+// Fused ConvT columns [n_beg, n_beg + NC) (n = r * CUP + co: output row 2p + r, channel
+// co): bias, LeakyReLU, store; the thread of p = 0 / L - 1 (with pads) zeroes the pads.
+template <class C, int NC>
+__device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, const float *scs2,
+                                       uint32_t dcol, int n_beg, int e, int p, bool valid, bool pads) {
+    constexpr int ES = C::ES;
+    constexpr int LO = 2 * C::L;
+    constexpr int64_t ROWS_O = LO + 2 * kPad;
+    constexpr int PUP = C::CUP / C::PW;
+    constexpr int LDW = NC % 32 == 0 ? 32 : 16;
+#pragma unroll 1
+    for (int cc = 0; cc < NC; cc += LDW) {
+        float vv[LDW];
+        if constexpr (LDW == 32) {
+            tmem_ld32(dcol + C::UP_OFF + n_beg + cc, vv);
+        } else {
+            tmem_ld16(dcol + C::UP_OFF + n_beg + cc, vv);
+        }
+#pragma unroll
+        for (int h = 0; h < LDW / 16; ++h) {
+            const int c0 = n_beg + cc + 16 * h;
+            const int r = c0 / C::CUP, co0 = c0 % C::CUP;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs2[c0 + j];
+                v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias2[co0 + j]));
+            }
+            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
+            if (valid)
+                put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
+                          (size_t)ROWS_O * 16, v, a.out_inv);
+        }
+    }
+    if (pads && p == 0) {
+        zero_planes(a.out, e, PUP, ROWS_O, 0);
+        zero_planes(a.out, e, PUP, ROWS_O, 1);
+    }
+    if (pads && p == C::L - 1) {
+        zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
+        zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
+    }
+}
+
 template <class C>
 __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
                          volatile int *abort, int warp, int lane) {
     using B = Bars<C>;
     uint64_t *tfull = bar + B::TFULL, *tempty = bar + B::TEMPTY, *a2full = bar + B::A2FULL,
              *t2full = bar + B::T2FULL, *gready = bar + B::GREADY;
-    constexpr int ES = C::ES;
     const float *par = reinterpret_cast<const float *>(smem + C::OFF_PAR);
     const float *sbias = par, *sbias2 = par + C::COUT, *scs = par + C::COUT + C::N2,
                 *scs2 = scs + C::COUT, *sfin = par + 2 * (C::COUT + C::N2);
     const int q = warp & 3;                         // TMEM lane quarter of this warp
     const int m = q * 32 + lane;                    // tile row
-    const int wg = (warp - 2) >> 2;                 // epilogue warpgroup: column half
-    const int cbeg = wg * C::EPI_COLS;
+    const int wg = (warp - 2) >> 2;                 // epilogue warpgroup
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
     const int ntiles = a.n_events * C::TPE;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
-    constexpr int LO = 2 * C::L;                    // ConvT output length
-    constexpr int64_t ROWS_O = LO + 2 * kPad;
-    constexpr int PUP = C::EPI == EPI_UP ? C::CUP / C::PW : 1;
+    constexpr bool ROLES = C::EPI == EPI_UP && C::EWG == 2;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int b = i % C::NB, ab = i & 1;
@@ -351,9 +445,26 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         tile_pos<C>(t, e, p0);
         const int p = p0 + m;
         const bool valid = p >= 0 && p < C::L;
+        const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
+        if constexpr (ROLES) {
+            if (wg == 0) {      // conv accumulator -> ConvT operand
+                if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
+                tc_fence_after();
+                epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid);
+                fence_proxy_async_smem();           // A2 writes -> visible to the tensor core
+                tc_fence_before();
+                mbar_arrive(&a2full[ab]);
+            } else {            // ConvT accumulator -> output; frees the buffer
+                if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
+                tc_fence_after();
+                epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
+                tc_fence_before();
+                mbar_arrive(&tempty[b]);
+            }
+            continue;
+        }
         if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
         tc_fence_after();
-        const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
         if constexpr (C::EPI == EPI_FINAL) {
             float v[16];
             tmem_ld16(dcol, v);
@@ -388,101 +499,24 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             }
             continue;
         }
-        // this warpgroup's conv columns, LDW at a time with one wait each
-#pragma unroll 1
-        for (int cc = 0; cc < C::EPI_COLS; cc += C::LDW) {
-            float vv[C::LDW];
-            if constexpr (C::LDW == 32) {
-                tmem_ld32(dcol + cbeg + cc, vv);
-            } else {
-                tmem_ld16(dcol + cbeg + cc, vv);
-            }
-#pragma unroll
-            for (int h = 0; h < C::LDW / 16; ++h) {
-                const int c0 = cbeg + cc + 16 * h;
-                float v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[c0 + j];
-                    v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias[c0 + j]));
-                }
-                if constexpr (C::EPI == EPI_UP) {
-                    if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
-                    unsigned char *a2 = smem + C::OFF_A2 + ab * C::A2_BYTES;
-                    put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
-                } else {
-                    if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
-                    if (valid)
-                        put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
-                                  (size_t)C::ROWS_E * 16, v, a.out_inv);
-                    if constexpr (C::EPI == EPI_POOL) {
-                        float w[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
-                        if (valid && (m & 1) == 0)
-                            put16<ES>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
-                                      (size_t)ROWS_P * 16, w, a.out_inv);
-                    }
-                }
-            }
-        }
-        if constexpr (C::EPI != EPI_UP) {
-            if (p == 0 && wg == 0) {
-                zero_planes(a.out, e, C::POUT, C::ROWS_E, 0);
-                zero_planes(a.out, e, C::POUT, C::ROWS_E, 1);
-                if constexpr (C::EPI == EPI_POOL) {
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, 0);
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, 1);
-                }
-            }
-            if (p == C::L - 1 && wg == 0) {
-                zero_planes(a.out, e, C::POUT, C::ROWS_E, C::L + kPad);
-                zero_planes(a.out, e, C::POUT, C::ROWS_E, C::L + kPad + 1);
-                if constexpr (C::EPI == EPI_POOL) {
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, C::L / 2 + kPad);
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, C::L / 2 + kPad + 1);
-                }
-            }
-        } else {
-            fence_proxy_async_smem();               // A2 writes -> visible to the tensor core
+        if constexpr (C::EPI == EPI_UP) {   // one warpgroup: conv, then the ConvT
+            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid);
+            fence_proxy_async_smem();
             mbar_arrive(&a2full[ab]);
-            if (!mbar_wait(&t2full[ab], ph_a, abort)) return false;
+            if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
             tc_fence_after();
-            // ConvT columns n = r * CUP + co; warpgroup r (or the only one, both r) writes
-            // output row 2p + r
-            constexpr int N2W = C::N2 / C::EWG;
-            constexpr int LDW2 = (C::EWG == 2 && N2W % 32 == 0) ? 32 : 16;
-#pragma unroll 1
-            for (int cc = 0; cc < N2W; cc += LDW2) {
-                float vv[LDW2];
-                if constexpr (LDW2 == 32) {
-                    tmem_ld32(dcol + C::COUT + wg * N2W + cc, vv);
-                } else {
-                    tmem_ld16(dcol + C::COUT + wg * N2W + cc, vv);
+            epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
+        } else {                            // this warpgroup's conv columns
+            epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid);
+            if (wg == 0 && (p == 0 || p == C::L - 1)) {
+                const int r0 = p == 0 ? 0 : C::L + kPad;
+                zero_planes(a.out, e, C::POUT, C::ROWS_E, r0);
+                zero_planes(a.out, e, C::POUT, C::ROWS_E, r0 + 1);
+                if constexpr (C::EPI == EPI_POOL) {
+                    const int rp = p == 0 ? 0 : C::L / 2 + kPad;
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp);
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp + 1);
                 }
-#pragma unroll
-                for (int h = 0; h < LDW2 / 16; ++h) {
-                    const int c0 = wg * N2W + cc + 16 * h;
-                    const int r = c0 / C::CUP, co0 = c0 % C::CUP;
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float sc = C::PREC == PVF_BF16 ? 1.0f : scs2[c0 + j];
-                        v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias2[co0 + j]));
-                    }
-                    if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
-                    if (valid)
-                        put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
-                                  (size_t)ROWS_O * 16, v, a.out_inv);
-                }
-            }
-            if (p == 0 && wg == 0) {
-                zero_planes(a.out, e, PUP, ROWS_O, 0);
-                zero_planes(a.out, e, PUP, ROWS_O, 1);
-            }
-            if (p == C::L - 1 && wg == 0) {
-                zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
-                zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
             }
         }
         tc_fence_before();
@@ -519,12 +553,10 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
         }
         for (int b = 0; b < C::NB; ++b) {
             mbar_init(&bar[B::TFULL + b], 1);
-            mbar_init(&bar[B::TEMPTY + b], 128 * C::EWG);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&bar[B::A2FULL + b], 128 * C::EWG);
+            mbar_init(&bar[B::TEMPTY + b], C::EPI == EPI_UP ? 128 : 128 * C::EWG);
             mbar_init(&bar[B::T2FULL + b], 1);
         }
+        for (int b = 0; b < 2; ++b) mbar_init(&bar[B::A2FULL + b], 128);
         mbar_init(&bar[B::DRAIN], 1);
         mbar_init(&bar[B::GREADY], 128);
         mbar_init(&bar[B::GREADY + 1], 128);
@@ -611,7 +643,7 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 template <int PREC> struct Net {
     using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56>;    // 6 CTAs per SM
     using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80>;    // 4
-    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4, 2>;
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4, 2, 128, 4>;   // 1
     using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4>;   // 1 CTA per SM
     using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4>;   // 2
     using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4>;   // 4

@@ -65,7 +65,11 @@ def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, pr
     g.close()
 
 
-def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights):
+@pytest.mark.parametrize("graphs,max_batch,inflight", [(True, 32, 3), (True, 24, 1), (False, 32, 2)])
+def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, max_batch, inflight):
+    """Per-bucket graphs (a batch of k events runs the graph of the next bucket with the
+    missing events empty; 24 is a bucket of its own) and stream launches give every
+    request the result it has alone."""
     store = synth.generate_uneven(40, 21)
     max_pv = 96
     pv = PVFinder(weights, precision="bf16", max_events=32, max_pv_per_event=max_pv)
@@ -73,9 +77,9 @@ def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights):
     n = 300
     arrivals = np.cumsum(rng.exponential(1e9 / 60000.0, n)).astype(np.int64)   # 60k events/s
     req = rng.integers(0, store.n_events, n).astype(np.int32)
-    done, cnt, batches, z = pv.serve_replay(store, arrivals, req, max_batch=32, max_inflight=3,
-                                            want_z=True)
-    assert batches >= n // 32 and np.all(done >= arrivals)
+    done, cnt, batches, z = pv.serve_replay(store, arrivals, req, max_batch=max_batch,
+                                            max_inflight=inflight, want_z=True, graphs=graphs)
+    assert batches >= n // max_batch and np.all(done >= arrivals)
     ref_cnt, ref_z = alone(pv, store, max_pv)
     np.testing.assert_array_equal(cnt, ref_cnt[req])
     for i in range(n):
