@@ -19,12 +19,13 @@
 // Warp roles: warp 0 issues the bulk copies (weights once, then one halo'd activation
 // tile per 128 positions into a ring of stages); warp 1 allocates TMEM and one thread
 // issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the MMAs
-// of tile i + 1); the remaining one or two warpgroups are the epilogue, one TMEM lane
-// (= output position) per thread. With a fused ConvT and two epilogue warpgroups they
-// split by role: one turns each conv accumulator into the ConvT's shared-memory operand,
-// the other stores the ConvT output and frees the accumulator buffer, so the operand of
-// tile i is ready while the tensor core still runs the conv of tile i + 1. Otherwise two
-// warpgroups split the accumulator columns. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
+// of tile i + 1); the remaining one, two or four warpgroups are the epilogue, one TMEM
+// lane (= output position) per thread. With a fused ConvT and two or four epilogue
+// warpgroups they split by role: half of them turn each conv accumulator into the
+// ConvT's shared-memory operand, the other half store the ConvT output and free the
+// accumulator buffer, so the operand of tile i is ready while the tensor core still runs
+// the conv of tile i + 1; the two warpgroups of a role (if four) split its columns.
+// Otherwise two warpgroups split the accumulator columns. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include "pvf_tc.cuh"
 #include "tc_ptx.cuh"
@@ -111,7 +112,9 @@ struct Cfg {
     static_assert(NB == 2 || NB == 4, "accumulator buffers");
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
-    static_assert(EWG == 1 || (EWG == 2 && EPI != EPI_FINAL && EPI_COLS % 16 == 0), "column split");
+    static_assert(EWG == 1 || (EWG == 2 && EPI != EPI_FINAL && EPI_COLS % 16 == 0) ||
+                  (EWG == 4 && EPI == EPI_UP && (COUT / 2) % 16 == 0 && (N2 / 2) % 16 == 0),
+                  "epilogue warpgroups");
     static_assert(EPI != EPI_UP || N2 % 16 == 0, "ConvT columns in 16-column chunks");
 };
 
@@ -436,7 +439,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
     const int ntiles = a.n_events * C::TPE;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
-    constexpr bool ROLES = C::EPI == EPI_UP && C::EWG == 2;
+    constexpr bool ROLES = C::EPI == EPI_UP && C::EWG >= 2;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
         const int b = i % C::NB, ab = i & 1;
@@ -447,17 +450,20 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         const bool valid = p >= 0 && p < C::L;
         const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
         if constexpr (ROLES) {
-            if (wg == 0) {      // conv accumulator -> ConvT operand
+            constexpr int PER = C::EWG / 2;                 // warpgroups per role
+            const int part = wg % PER;
+            if (wg < PER) {     // conv accumulator -> ConvT operand
                 if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
                 tc_fence_after();
-                epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid);
+                epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
+                                           valid);
                 fence_proxy_async_smem();           // A2 writes -> visible to the tensor core
                 tc_fence_before();
                 mbar_arrive(&a2full[ab]);
             } else {            // ConvT accumulator -> output; frees the buffer
                 if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
                 tc_fence_after();
-                epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
+                epi_up<C, C::N2 / PER>(a, sbias2, scs2, dcol, part * (C::N2 / PER), e, p, valid, part == 0);
                 tc_fence_before();
                 mbar_arrive(&tempty[b]);
             }
@@ -553,10 +559,10 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
         }
         for (int b = 0; b < C::NB; ++b) {
             mbar_init(&bar[B::TFULL + b], 1);
-            mbar_init(&bar[B::TEMPTY + b], C::EPI == EPI_UP ? 128 : 128 * C::EWG);
+            mbar_init(&bar[B::TEMPTY + b], C::EPI == EPI_UP ? 128 * ((C::EWG + 1) / 2) : 128 * C::EWG);
             mbar_init(&bar[B::T2FULL + b], 1);
         }
-        for (int b = 0; b < 2; ++b) mbar_init(&bar[B::A2FULL + b], 128);
+        for (int b = 0; b < 2; ++b) mbar_init(&bar[B::A2FULL + b], 128 * ((C::EWG + 1) / 2));
         mbar_init(&bar[B::DRAIN], 1);
         mbar_init(&bar[B::GREADY], 128);
         mbar_init(&bar[B::GREADY + 1], 128);
@@ -643,7 +649,8 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 template <int PREC> struct Net {
     using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56>;    // 6 CTAs per SM
     using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80>;    // 4
-    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4, 2, 128, 4>;   // 1
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4,
+                        PREC == PVF_BF16 ? 2 : 4, 96, 4>;                                  // 1
     using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4>;   // 1 CTA per SM
     using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4>;   // 2
     using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4>;   // 4
