@@ -106,6 +106,18 @@ def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_laun
             "frac": flops / sec / cpeak, "algorithmic_flops": flops}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels
+# that can dominate a step, from one `ncu --set full` capture of a 512-event step of the
+# current kernels (its summary is kept under profiles/), scaled to a launch of 1000
+# events (traffic grows with the events). Keyed by (form, kernel, events per launch). A kernel changed since
+# that capture has no entry and reports null.
+NCU_TRAFFIC = {
+    ("bf16", "dec3_up2", 1000): (131.744256e6 + 28.122624e6) * 1000 / 512,
+    ("bf16", "dec1_final", 1000): (131.240192e6 + 4.399616e6) * 1000 / 512,
+    ("bf16", "dec2_up1", 1000): (131.399936e6 + 28.621824e6) * 1000 / 512,
+}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -392,7 +404,8 @@ def run_step(args, weights, batch, rank, world, local):
                       "bound": rf["bound"], "frac": rf["frac"]}
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
     roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks)
-    roof.update({"kernel": name, "traffic": None,
+    traffic = NCU_TRAFFIC.get((args.precision, name, args.events))
+    roof.update({"kernel": name, "traffic": traffic,
                  "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
                                 "fp32 ALU = 152 SM x 128 lanes x 2 x sm_max_mhz; fp8 = 2 x bf16)"})
     gpu_launches = int(sum(n for n, _ in prof.values()))
