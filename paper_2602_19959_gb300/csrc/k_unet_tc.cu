@@ -12,7 +12,15 @@
 //   dec2_up1  conv [32|32]->32 @2000, + ConvT 32->16
 //   dec1      conv [16|16]->16 @4000
 // The skip concat is never materialised: the two inputs are copied into adjacent
-// K-planes of the same shared-memory tile. Every conv and ConvT output goes through
+// K-planes of the same shared-memory tile.
+//
+// Tap pairing (the BF16 dec3_up2): a tcgen05.mma costs about the same for
+// N up to 64 (reading A dominates), so the small-C_out convs stack two taps' weights in N:
+// per K step, taps (0, 1) on the tile as is, taps (2, 3) on the tile two rows down and tap
+// 4 four rows down, accumulating E (taps 0, 2, 4 of row r) and O (taps 1, 3 of row r - 1)
+// side by side. The conv at row r is E[r] + O[r + 1]: a one-lane shuffle, and through
+// shared memory across the warps' lane quarters. Row 127 of a tile lacks O[128], so
+// paired tiles advance by 127 rows. Three MMAs per K step replace five. Every conv and ConvT output goes through
 // LeakyReLU(0.01) in the epilogue; the fused ConvT reads the conv tile from shared
 // memory, so the deepest level's activations (e4, d3, d2) never reach global memory.
 //
@@ -40,7 +48,6 @@ namespace {
 using namespace tc;
 
 constexpr int kTileM = 128;
-constexpr int kFinalStride = kTileM - 4;   // dec1 + final conv: tiles overlap by 4 rows
 
 enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2, EPI_FINAL = 3 };
 
@@ -52,7 +59,7 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_, int EWG_ = 1,
-          int MAXREG_ = 128, int NB_ = 2>
+          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = PREC == PVF_BF16 ? 2 : 1;      // bytes per element
@@ -75,7 +82,11 @@ struct Cfg {
     static constexpr int TAPS = PAIR ? 6 : 5;
     static constexpr int ROWS = kTileM + TAPS - 1;           // halo'd tile rows
     static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
-    static constexpr int STRIDE = EPI == EPI_FINAL ? kFinalStride : kTileM;
+    static constexpr bool PAIRED = PAIRED_;                 // taps stacked in pairs along N
+    // output rows per tile: row 127 of a paired tile lacks O[128]; the fused final conv
+    // also needs two rows on each side
+    static constexpr int ROWS_OK = PAIRED ? kTileM - 1 : kTileM;
+    static constexpr int STRIDE = EPI == EPI_FINAL ? ROWS_OK - 2 * kPad : ROWS_OK;
     static constexpr int TPE = (L + STRIDE - 1) / STRIDE;    // tiles per event
     static constexpr int A_STAGE = align_up(PIN * ROWS * 16, 128);
     static constexpr int W_BYTES = TAPS * PIN * COUT * 16;
@@ -85,7 +96,8 @@ struct Cfg {
     static constexpr int A2_BYTES = EPI == EPI_UP ? P2 * kTileM * 16 : 0;
     // accumulator buffer: the fused ConvT writes its result over the conv columns, which
     // the epilogue has read before the ConvT's operand is complete
-    static constexpr int COLS_BUF = COUT > N2 ? COUT : N2;
+    static constexpr int CONV_COLS = PAIRED ? 2 * COUT : COUT;      // E | O when paired
+    static constexpr int COLS_BUF = CONV_COLS > N2 ? CONV_COLS : N2;
     static constexpr int UP_OFF = 0;
     static constexpr int TMEM_COLS = pow2ceil(NB * COLS_BUF);
     // float parameters kept in shared memory: bias, bias2, column scales, final conv
@@ -97,7 +109,10 @@ struct Cfg {
     static constexpr int OFF_A2 = OFF_A + STAGES * A_STAGE;
     static constexpr int OFF_G = align_up(OFF_A2 + 2 * A2_BYTES, 128);
     static constexpr int G_BYTES = EPI == EPI_FINAL ? 2 * 5 * kTileM * 4 : 0;
-    static constexpr int OFF_BAR = align_up(OFF_G + G_BYTES, 128);
+    // paired: each lane quarter's first O row, for the quarter above (two buffers)
+    static constexpr int OFF_X = align_up(OFF_G + G_BYTES, 128);
+    static constexpr int X_BYTES = PAIRED ? 2 * 4 * COUT * 4 : 0;
+    static constexpr int OFF_BAR = align_up(OFF_X + X_BYTES, 128);
     static constexpr int SMEM = OFF_BAR + 256;
     static constexpr uint32_t FMT = PREC == PVF_BF16 ? 1u : 0u;
     static constexpr uint32_t IDESC1 = idesc_f32acc(kTileM, COUT, FMT);
@@ -108,8 +123,11 @@ struct Cfg {
     static_assert(EPI != EPI_UP || P2 % 2 == 0, "fused GEMM K planes come in pairs");
     static_assert(EPI != EPI_FINAL || COUT == kC0, "final conv reads c0 channels");
     static_assert(TMEM_COLS <= 512, "TMEM columns");
+    static_assert(OFF_PAR % 16 == 0 && COUT % 4 == 0 && N2 % 4 == 0, "parameters read as float4");
     static_assert(STAGES >= 2 && STAGES <= 6, "stages");
     static_assert(NB == 2 || NB == 4, "accumulator buffers");
+    static_assert(!PAIRED || (!PAIR && PIN % 2 == 0 && EWG <= 2 && 2 * COUT <= 256 && EPI != EPI_POOL),
+                  "tap pairing");
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
     static_assert(EWG == 1 || (EWG == 2 && EPI != EPI_FINAL && EPI_COLS % 16 == 0) ||
@@ -154,7 +172,7 @@ __device__ __forceinline__ void amax_fold(float *amax, int slot, const float (&v
 template <class C> struct Bars {
     static constexpr int W = 0, FULL = 1, EMPTY = 1 + C::STAGES, TFULL = 1 + 2 * C::STAGES,
                          TEMPTY = TFULL + C::NB, T2FULL = TEMPTY + C::NB, A2FULL = T2FULL + C::NB,
-                         DRAIN = A2FULL + 2, GREADY = DRAIN + 1, N = GREADY + 2;
+                         DRAIN = A2FULL + 2, GREADY = DRAIN + 1, XREADY = GREADY + 2, N = XREADY + 2;
     static_assert(N * 8 + 8 <= 256, "barrier area");
 };
 
@@ -162,7 +180,7 @@ template <class C>
 __device__ __forceinline__ void tile_pos(int t, int &e, int &p0) {
     e = t / C::TPE;
     const int k = t % C::TPE;
-    p0 = C::EPI == EPI_FINAL ? k * kFinalStride - kPad : k * kTileM;
+    p0 = C::EPI == EPI_FINAL ? k * C::STRIDE - kPad : k * C::STRIDE;
 }
 
 // Quantises 16 values to the form's element type and stores them as 16 / PW plane rows.
@@ -242,8 +260,28 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
 }
 
 template <class C>
+__device__ __forceinline__ void mma_t(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, bool acc) {
+    if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, idesc, acc);
+    else mma_fp8(d, ad, bd, idesc, acc);
+}
+
+template <class C>
 __device__ __forceinline__ void issue_conv(uint32_t d, uint32_t as, uint32_t w_base) {
-    if constexpr (C::PAIR) {
+    if constexpr (C::PAIRED) {
+        // weights: group g (taps 2g, 2g + 1; g = 2: tap 4) at w_base + g * GROUP, planes of N_g rows
+        constexpr uint32_t N01 = 2 * C::COUT, GROUP = C::PIN * N01 * 16;
+        constexpr uint32_t ID01 = idesc_f32acc(kTileM, N01, C::FMT), ID4 = idesc_f32acc(kTileM, C::COUT, C::FMT);
+#pragma unroll
+        for (int kb = 0; kb < C::PIN / 2; ++kb) {
+            const uint32_t a = as + 2 * kb * C::ROWS * 16;
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+                mma_t<C>(d, smem_desc(a + 2 * g * 16, C::ROWS * 16, 128),
+                         smem_desc(w_base + g * GROUP + 2 * kb * N01 * 16, N01 * 16, 128), ID01, (kb | g) != 0);
+            mma_t<C>(d, smem_desc(a + 4 * 16, C::ROWS * 16, 128),
+                     smem_desc(w_base + 2 * GROUP + 2 * kb * C::COUT * 16, C::COUT * 16, 128), ID4, true);
+        }
+    } else if constexpr (C::PAIR) {
 #pragma unroll
         for (int j = 0; j < C::TAPS / 2; ++j) {
             const uint64_t ad = smem_desc(as + 2 * j * 16, 16, 128);
@@ -331,20 +369,73 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
     return ok;
 }
 
+// 16 consecutive parameters from shared memory in four 16-byte loads (p 16-byte aligned):
+// the epilogues read their biases, scales and final-conv weights per tile, and scalar
+// broadcast loads made the shared-memory pipe the bottleneck of the final conv.
+__device__ __forceinline__ void lds16(const float *p, float (&v)[16]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 x = q[i];
+        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+    }
+}
+
+// Paired taps: conv columns [c0, c0 + W) of row m = E[m] + O[m + 1]. O[m + 1] comes from
+// the next lane, or for lane 31 from the next quarter's published first row (sx).
+template <class C, int W>
+__device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *sx, int q, int lane,
+                                            float (&v)[W]) {
+    float o[W];
+    if constexpr (W == 32) {
+        tmem_ld32(dcol + c0, v);
+        tmem_ld32(dcol + C::COUT + c0, o);
+    } else {
+        tmem_ld16(dcol + c0, v);
+        tmem_ld16(dcol + C::COUT + c0, o);
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        float on = __shfl_down_sync(0xffffffffu, o[j], 1);
+        if (lane == 31) on = q < 3 ? sx[(q + 1) * C::COUT + c0 + j] : 0.0f;
+        v[j] += on;
+    }
+}
+
+// Paired taps: lane 0 of each quarter publishes its O row (all COUT columns) into sx, then
+// the threads of the conv epilogue meet on xready. Returns false on a timed-out wait.
+template <class C>
+__device__ __forceinline__ bool paired_publish(uint32_t dcol, float *sx, int q, int lane, uint64_t *xready,
+                                               uint32_t parity, volatile int *abort) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < C::COUT; c0 += 16) {
+        float o[16];
+        tmem_ld16(dcol + C::COUT + c0, o);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sx[q * C::COUT + c0 + j] = o[j];
+        }
+    }
+    mbar_arrive(xready);
+    return mbar_wait(xready, parity, abort);
+}
+
 // Epilogue pieces, one TMEM lane (tile row m, position p) per thread.
 // Conv columns [c_beg, c_beg + NC) of accumulator dcol: bias, LeakyReLU, then either the
 // fused ConvT's shared-memory operand (A2) or the stored output (+ the 2:1 max-pool).
 template <class C, int NC>
 __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
                                          const float *scs, uint32_t dcol, int c_beg, int ab, int e,
-                                         int p, int m, bool valid) {
+                                         int p, int m, bool valid, const float *sx = nullptr) {
     constexpr int ES = C::ES;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad;
-    constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
+    constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) && !C::PAIRED ? 32 : 16;
 #pragma unroll 1
     for (int cc = 0; cc < NC; cc += LDW) {
         float vv[LDW];
-        if constexpr (LDW == 32) {
+        if constexpr (C::PAIRED) {
+            paired_cols<C, LDW>(dcol, c_beg + cc, sx, m >> 5, m & 31, vv);
+        } else if constexpr (LDW == 32) {
             tmem_ld32(dcol + c_beg + cc, vv);
         } else {
             tmem_ld16(dcol + c_beg + cc, vv);
@@ -352,11 +443,16 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
 #pragma unroll
         for (int h = 0; h < LDW / 16; ++h) {
             const int c0 = c_beg + cc + 16 * h;
-            float v[16];
+            float v[16], bj[16];
+            lds16(sbias + c0, bj);
+            if constexpr (C::PREC == PVF_BF16) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[c0 + j];
-                v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias[c0 + j]));
+                for (int j = 0; j < 16; ++j) v[j] = leaky(vv[16 * h + j] + bj[j]);
+            } else {
+                float sc[16];
+                lds16(scs + c0, sc);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = leaky(fmaf(vv[16 * h + j], sc[j], bj[j]));
             }
             if constexpr (C::EPI == EPI_UP) {
                 if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
@@ -402,11 +498,16 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
         for (int h = 0; h < LDW / 16; ++h) {
             const int c0 = n_beg + cc + 16 * h;
             const int r = c0 / C::CUP, co0 = c0 % C::CUP;
-            float v[16];
+            float v[16], bj[16];
+            lds16(sbias2 + co0, bj);
+            if constexpr (C::PREC == PVF_BF16) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs2[c0 + j];
-                v[j] = leaky(fmaf(vv[16 * h + j], sc, sbias2[co0 + j]));
+                for (int j = 0; j < 16; ++j) v[j] = leaky(vv[16 * h + j] + bj[j]);
+            } else {
+                float sc[16];
+                lds16(scs2 + c0, sc);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = leaky(fmaf(vv[16 * h + j], sc[j], bj[j]));
             }
             if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
             if (valid)
@@ -429,7 +530,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                          volatile int *abort, int warp, int lane) {
     using B = Bars<C>;
     uint64_t *tfull = bar + B::TFULL, *tempty = bar + B::TEMPTY, *a2full = bar + B::A2FULL,
-             *t2full = bar + B::T2FULL, *gready = bar + B::GREADY;
+             *t2full = bar + B::T2FULL, *gready = bar + B::GREADY, *xready = bar + B::XREADY;
     const float *par = reinterpret_cast<const float *>(smem + C::OFF_PAR);
     const float *sbias = par, *sbias2 = par + C::COUT, *scs = par + C::COUT + C::N2,
                 *scs2 = scs + C::COUT, *sfin = par + 2 * (C::COUT + C::N2);
@@ -447,16 +548,21 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         int e, p0;
         tile_pos<C>(t, e, p0);
         const int p = p0 + m;
-        const bool valid = p >= 0 && p < C::L;
+        // rows past the stride belong to the next tile (and row 127 of a paired tile is incomplete)
+        const bool valid = p >= 0 && p < C::L && m < C::ROWS_OK;
         const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
+        float *sx = reinterpret_cast<float *>(smem + C::OFF_X) + ab * 4 * C::COUT;
         if constexpr (ROLES) {
             constexpr int PER = C::EWG / 2;                 // warpgroups per role
             const int part = wg % PER;
             if (wg < PER) {     // conv accumulator -> ConvT operand
                 if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
                 tc_fence_after();
+                if constexpr (C::PAIRED) {
+                    if (!paired_publish<C>(dcol, sx, q, lane, &xready[ab], ph_a, abort)) return false;
+                }
                 epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
-                                           valid);
+                                           valid, sx);
                 fence_proxy_async_smem();           // A2 writes -> visible to the tensor core
                 tc_fence_before();
                 mbar_arrive(&a2full[ab]);
@@ -473,21 +579,36 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         tc_fence_after();
         if constexpr (C::EPI == EPI_FINAL) {
             float v[16];
-            tmem_ld16(dcol, v);
+            if constexpr (C::PAIRED) {
+                if (!paired_publish<C>(dcol, sx, q, lane, &xready[ab], ph_a, abort)) return false;
+                paired_cols<C, 16>(dcol, 0, sx, q, lane, v);
+            } else {
+                tmem_ld16(dcol, v);
+            }
             tc_fence_before();
             mbar_arrive(&tempty[b]);
             float g[5];
+            {
+                float bj[16], sc[16];
+                lds16(sbias, bj);
+                if constexpr (C::PREC == PVF_BF16) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float sc = C::PREC == PVF_BF16 ? 1.0f : scs[j];
-                v[j] = valid ? leaky(fmaf(v[j], sc, sbias[j])) : 0.0f;   // zero padding outside
+                    for (int j = 0; j < 16; ++j) sc[j] = 1.0f;
+                } else {
+                    lds16(scs, sc);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = valid ? leaky(fmaf(v[j], sc[j], bj[j])) : 0.0f;   // zero padding outside
             }
             if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
 #pragma unroll
             for (int tp = 0; tp < 5; ++tp) {
+                float wf[16];
+                lds16(sfin + tp * kC0, wf);
                 float acc = 0.0f;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc = fmaf(sfin[tp * kC0 + j], v[j], acc);
+                for (int j = 0; j < 16; ++j) acc = fmaf(wf[j], v[j], acc);
                 g[tp] = acc;
             }
             float *sg = reinterpret_cast<float *>(smem + C::OFF_G) + ab * 5 * kTileM;
@@ -496,7 +617,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             // neighbours' partial sums: a bounded mbarrier among the 128 epilogue threads
             mbar_arrive(&gready[ab]);
             if (!mbar_wait(&gready[ab], ph_a, abort)) return false;
-            if (m >= kPad && m < kTileM - kPad && valid) {
+            if (m >= kPad && m < kPad + C::STRIDE && valid) {
                 // f(p) = b + sum_t g_t(p + t - 2), in tap order
                 float f = sfin[5 * kC0];
 #pragma unroll
@@ -506,13 +627,17 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             continue;
         }
         if constexpr (C::EPI == EPI_UP) {   // one warpgroup: conv, then the ConvT
-            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid);
+            if constexpr (C::PAIRED) {
+                if (!paired_publish<C>(dcol, sx, q, lane, &xready[ab], ph_a, abort)) return false;
+            }
+            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx);
             fence_proxy_async_smem();
             mbar_arrive(&a2full[ab]);
             if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
             tc_fence_after();
             epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
         } else {                            // this warpgroup's conv columns
+            static_assert(!C::PAIRED || C::EPI == EPI_UP || C::EPI == EPI_FINAL, "paired stores");
             epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid);
             if (wg == 0 && (p == 0 || p == C::L - 1)) {
                 const int r0 = p == 0 ? 0 : C::L + kPad;
@@ -566,6 +691,8 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
         mbar_init(&bar[B::DRAIN], 1);
         mbar_init(&bar[B::GREADY], 128);
         mbar_init(&bar[B::GREADY + 1], 128);
+        mbar_init(&bar[B::XREADY], 128);          // the conv epilogue's warpgroup
+        mbar_init(&bar[B::XREADY + 1], 128);
         *abort = 0;
         fence_mbar_init();
     }
@@ -646,14 +773,20 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 
 // ---------------------------------------------------------------- weight packing (host)
 
+// Conv layers (0..5: enc2, enc3, enc4, dec3, dec2, dec1) whose taps are stacked in pairs
+// along N: where it measured faster, the BF16 dec3 (44 -> 28 MMAs per tile). The FP8 form
+// already halves the MMAs (K = 32), and dec2/dec1 are bound by their epilogue's latency,
+// which the pairing exchange lengthens.
+constexpr bool conv_paired(int li, int prec) { return li == 3 && prec == PVF_BF16; }
+
 template <int PREC> struct Net {
     using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56>;    // 6 CTAs per SM
     using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80>;    // 4
     using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4,
                         PREC == PVF_BF16 ? 2 : 4, 96, 4>;                                  // 1
-    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4>;   // 1 CTA per SM
-    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4>;   // 2
-    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4>;   // 4
+    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4, conv_paired(3, PREC)>; // 1 CTA/SM
+    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4, conv_paired(4, PREC)>; // 2
+    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4, conv_paired(5, PREC)>; // 4
 };
 
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
@@ -724,7 +857,13 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
                         for (int j = 0; j < pk.pw; ++j) {
                             const int ci = k * pk.pw + j;
                             const float w = Lw.w[((size_t)co * cin + ci) * 5 + t] / scale[co];
-                            pk.enc(w, &img[(((size_t)t * pin + k) * cout + co) * 16 + j * pk.es]);
+                            // paired: group g = t / 2 (N = 2 cout rows for taps 0-3, cout for
+                            // tap 4), plane k, row (t % 2) * cout + co; else tap-major planes
+                            const size_t row =
+                                conv_paired(li, precision) ? (size_t)(t / 2) * pin * 2 * cout +
+                                                      (size_t)k * (t < 4 ? 2 * cout : cout) + (t % 2) * cout + co
+                                                : ((size_t)t * pin + k) * cout + co;
+                            pk.enc(w, &img[row * 16 + j * pk.es]);
                         }
         } else {
             const int cin = (int)Lw.shape[0];
