@@ -118,11 +118,93 @@ __device__ __forceinline__ void track_features(const FrontArgs &a, int64_t gt, i
     for (int k = kFeatures; k < kFcInPad; ++k) x[k] = 0.0f;
 }
 
+// Stores channels [8 h, 8 h + 8) of storage row `row` of event e: half a channel-last
+// float32 row, one of the two bf16 planes, or half of the e4m3 plane's 16-byte row.
+template <class T>
+__device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_e, int64_t row, int h,
+                                            const float v[8], float inv_scale) {
+    if constexpr (sizeof(T) == 4) {
+        float4 *d = reinterpret_cast<float4 *>(reinterpret_cast<float *>(base) + (e * rows_e + row) * kC0 + 8 * h);
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else if constexpr (sizeof(T) == 2) {
+        uint4 pk;
+        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, h, 2, rows_e, row)) = pk;
+    } else {
+        uint2 pk;
+        __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv_scale);
+        *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, 0, 1, rows_e, row) + 8 * h) = pk;
+    }
+}
+
 // Step f: e1 = LeakyReLU(conv_k5(hist) + b), p1 = maxpool2(e1), stored in the form's
 // precision with the pad rows zeroed; calibration (AMAX) folds max |e1| into a.amax[0].
+// Thread tid owns channels [8 h, 8 h + 8), h = tid & 1, of every position pair it takes,
+// so its 40 weights and 8 biases stay in registers and the loop reads only the histogram
+// from shared memory; the two threads of a pair write the two halves of each row.
 template <class T, int NT, bool AMAX>
 __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, const float *shist,
                                             const float *senc) {
+    static_assert(NT % 2 == 0, "thread pairs");
+    const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
+    const float inv = a.e1_inv_scale;
+    const int h = tid & 1;
+    float w[5][8], bias[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int t = 0; t < 5; ++t) w[t][j] = senc[t * kC0 + 8 * h + j];
+        bias[j] = senc[5 * kC0 + 8 * h + j];
+    }
+    float vmax = 0.0f;
+    for (int q = tid >> 1; q < kBins / 2; q += NT / 2) {
+        float hv[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int p = 2 * q + k - 2;
+            hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
+        }
+        float v0[8], v1[8], vp[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float a0 = bias[j], a1 = bias[j];
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                a0 = fmaf(w[t][j], hv[t], a0);
+                a1 = fmaf(w[t][j], hv[t + 1], a1);
+            }
+            v0[j] = leaky(a0);
+            v1[j] = leaky(a1);
+            vp[j] = fmaxf(v0[j], v1[j]);
+            if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[j]), fabsf(v1[j])));
+        }
+        store_half8<T>(a.e1, e, rows1, 2 * q + kPad, h, v0, inv);
+        store_half8<T>(a.e1, e, rows1, 2 * q + 1 + kPad, h, v1, inv);
+        store_half8<T>(a.p1, e, rows2, q + kPad, h, vp, inv);
+    }
+    if constexpr (AMAX) {   // calibration: integer max on the float bits (order-independent)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
+    }
+    if (tid < 4) {
+        const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3
+        zero_row16<T>(a.e1, e, rows1, r);
+        const int rp = tid < 2 ? tid : kBins / 2 + tid;
+        zero_row16<T>(a.p1, e, rows2, rp);
+    }
+}
+
+// Step f with the weights read from shared memory per position pair, for the float32 front,
+// whose FC registers leave no room for them (same arithmetic, same order).
+template <class T, int NT, bool AMAX>
+__device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, int tid, const float *shist,
+                                                   const float *senc) {
     const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
     float vmax = 0.0f;
@@ -151,24 +233,30 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
         store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
         store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
     }
-    if constexpr (AMAX) {   // calibration: integer max on the float bits (order-independent)
+    if constexpr (AMAX) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
     }
     if (tid < 4) {
-        const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3
+        const int r = tid < 2 ? tid : kBins + tid;
         zero_row16<T>(a.e1, e, rows1, r);
         const int rp = tid < 2 ? tid : kBins / 2 + tid;
         zero_row16<T>(a.p1, e, rows2, rp);
     }
 }
 
-template <class T, int NT>
+// REGW: weights in registers (tensor-core front) or read from shared memory (float32 front).
+template <class T, int NT, bool REGW = true>
 __device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, const float *shist,
                                           const float *senc) {
-    if (a.amax) enc1_pool_t<T, NT, true>(a, e, tid, shist, senc);
-    else enc1_pool_t<T, NT, false>(a, e, tid, shist, senc);
+    if constexpr (REGW) {
+        if (a.amax) enc1_pool_t<T, NT, true>(a, e, tid, shist, senc);
+        else enc1_pool_t<T, NT, false>(a, e, tid, shist, senc);
+    } else {
+        if (a.amax) enc1_pool_shared_t<T, NT, true>(a, e, tid, shist, senc);
+        else enc1_pool_shared_t<T, NT, false>(a, e, tid, shist, senc);
+    }
 }
 
 }  // namespace front

@@ -92,7 +92,7 @@ __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const flo
 
 // ENC1 = false: steps a-e only (the histogram), nothing written to e1/p1.
 template <int PREC, bool ENC1 = true>
-__global__ void __launch_bounds__(kThreads, 2) k_front(FrontArgs a) {
+__global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     float *sfc = reinterpret_cast<float *>(smem + FrontSmem::fc);
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_front(FrontArgs a) {
             for (int i = tid; i < kBins / 4; i += kThreads) dst[i] = src[i];
         }
 
-        if constexpr (ENC1) enc1_pool<T, kThreads>(a, e, tid, shist, senc);
+        if constexpr (ENC1) enc1_pool<T, kThreads, false>(a, e, tid, shist, senc);
         __syncthreads();                   // shist and the sort arrays are reused next event
     }
 }
