@@ -223,22 +223,29 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                                 for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, v[t]);
                                 continue;
                             }
+                            // several segments in this chunk: one branch-free masked pass per
+                            // segment, in row order (adding zeros leaves the sum bit-identical,
+                            // and the loop body stays small enough for the instruction cache)
+                            const int cnt = min(32, ce - col);
+                            int t0 = 0;
+#pragma unroll 1
+                            while (t0 < cnt) {
+                                const int t1 = min(cnt, send - col);
+                                const uint32_t hi = t1 >= 32 ? 0xFFFFFFFFu : ((1u << t1) - 1u);
+                                const uint32_t msk = hi & ~((1u << t0) - 1u);
 #pragma unroll
-                            for (int t = 0; t < 32; ++t) {
-                                const int r = col + t;
-                                if (r < ce) {
-                                    if (r == send) {           // slice s ends: flush, move on
-                                        if (hold) { held = acc; held_s = s; hold = false; }
-                                        else if (o_bin >= 0) {
-                                            float *hp = shist + s * kSliceBins + o_bin;
-                                            *hp = __fadd_rn(*hp, acc);
-                                        }
-                                        acc = 0.0f;
-                                        s = sslice[ssorted[c0 + r]];
-                                        send = sseg[s + 1] - c0;
+                                for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, ((msk >> t) & 1u) ? v[t] : 0.0f);
+                                if (t1 < cnt) {                // slice s ends at row col + t1
+                                    if (hold) { held = acc; held_s = s; hold = false; }
+                                    else if (o_bin >= 0) {
+                                        float *hp = shist + s * kSliceBins + o_bin;
+                                        *hp = __fadd_rn(*hp, acc);
                                     }
-                                    acc = __fadd_rn(acc, v[t]);
+                                    acc = 0.0f;
+                                    s = sslice[ssorted[c0 + col + t1]];
+                                    send = sseg[s + 1] - c0;
                                 }
+                                t0 = t1;
                             }
                         }
                         if (hold) { held = acc; held_s = s; }
