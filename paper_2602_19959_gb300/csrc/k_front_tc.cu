@@ -112,6 +112,9 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // launched in stream order (its inputs come from the caller); lets the next kernel
+    // start its prologue while this one runs
+    grid_dep_launch();
     const uint32_t img = smem_u32(smem + TcSmem::img);
     const uint32_t sx = smem_u32(smem + TcSmem::x), sh = smem_u32(smem + TcSmem::h);
     unsigned char *xrow = smem + TcSmem::x + (size_t)(g * kRows + m) * 16;   // + plane * kPlane

@@ -74,6 +74,9 @@ __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
         for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
         __syncthreads();
     }
+    // the logits (or d1) are the previous kernel's output (dependent launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // persistent: the CTA walks the launch's events
     for (int e = blockIdx.x; e < a.n_events; e += gridDim.x) {
         const int ge = a.ev_base + e;
@@ -186,7 +189,7 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     const int per_sm = a.logit_in ? 8 : 2;
     dim3 grid(a.n_events < per_sm * sms ? a.n_events : per_sm * sms), block(kThreads);
     if (a.logit_in) {
-        k_tail<PVF_FP32, false><<<grid, block, 0, s>>>(a);
+        return launch_pdl(k_tail<PVF_FP32, false>, grid, block, 0, s, a);
     } else {
         switch (precision) {
         case PVF_FP32: k_tail<PVF_FP32, true><<<grid, block, 0, s>>>(a); break;

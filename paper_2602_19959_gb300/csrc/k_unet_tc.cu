@@ -704,6 +704,10 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // the prologue above only touched weights and parameters; the activations are the
+    // previous kernel's output
+    grid_dep_wait();
+    grid_dep_launch();
 
     bool ok = true;
     if (warp == 0) {
@@ -767,8 +771,7 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
     int grid = sm_count() * per_sm;
     if (grid > ntiles) grid = ntiles;
     ProfScope ps(prof, name, s);
-    k_conv_tc<C><<<grid, C::THREADS, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_conv_tc<C>, dim3(grid), dim3(C::THREADS), (size_t)smem, s, a);
 }
 
 // ---------------------------------------------------------------- weight packing (host)

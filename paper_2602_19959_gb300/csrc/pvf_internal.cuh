@@ -9,6 +9,8 @@
 //     Producers write their own pad rows, so buffers can be reused by later layers.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -168,6 +170,26 @@ struct ProfScope {
     }
     ~ProfScope() { if (h) h->end(h->ctx, s); }
 };
+
+// Launch with programmatic stream serialization: the kernel may start while the previous
+// kernel of the stream finishes; it must call griddepcontrol.wait before reading that
+// kernel's output, and triggers its own dependents only after that wait, so at most two
+// kernels share the GPU and the earlier one is always fully resident.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Host-side launchers (defined in the kernel translation units).
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem_bytes, cudaStream_t s);

@@ -28,6 +28,14 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
+// ------------------------------------------------------------------ dependent launch
+// Programmatic dependent launch (kernels launched with the programmatic stream
+// serialization attribute): wait until the previous kernel in the stream has completed
+// and its writes are visible; then allow the next kernel to launch. Both are no-ops for
+// a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ mbarrier
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
