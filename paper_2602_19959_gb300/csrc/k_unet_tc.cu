@@ -124,6 +124,7 @@ struct Cfg {
     static_assert(EPI != EPI_FINAL || COUT == kC0, "final conv reads c0 channels");
     static_assert(TMEM_COLS <= 512, "TMEM columns");
     static_assert(OFF_PAR % 16 == 0 && COUT % 4 == 0 && N2 % 4 == 0, "parameters read as float4");
+    static_assert(OFF_X % 16 == 0, "paired exchange in float4");
     static_assert(STAGES >= 2 && STAGES <= 6, "stages");
     static_assert(NB == 2 || NB == 4, "accumulator buffers");
     static_assert(!PAIRED || (!PAIR && PIN % 2 == 0 && EWG <= 2 && 2 * COUT <= 256 && EPI != EPI_POOL),
@@ -395,11 +396,17 @@ __device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *
         tmem_ld16(dcol + C::COUT + c0, o);
     }
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        float on = __shfl_down_sync(0xffffffffu, o[j], 1);
-        if (lane == 31) on = q < 3 ? sx[(q + 1) * C::COUT + c0 + j] : 0.0f;
-        v[j] += on;
+    for (int j = 0; j < W; ++j) o[j] = __shfl_down_sync(0xffffffffu, o[j], 1);
+    if (lane == 31) {     // row 32 q + 31: its O[m + 1] is the next quarter's first row
+        const float4 *n4 = reinterpret_cast<const float4 *>(sx + (q + 1) * C::COUT + c0);
+#pragma unroll
+        for (int j4 = 0; j4 < W / 4; ++j4) {
+            const float4 x = q < 3 ? n4[j4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            o[4 * j4] = x.x; o[4 * j4 + 1] = x.y; o[4 * j4 + 2] = x.z; o[4 * j4 + 3] = x.w;
+        }
     }
+#pragma unroll
+    for (int j = 0; j < W; ++j) v[j] += o[j];
 }
 
 // Paired taps: lane 0 of each quarter publishes its O row (all COUT columns) into sx, then
@@ -407,13 +414,17 @@ __device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *
 template <class C>
 __device__ __forceinline__ bool paired_publish(uint32_t dcol, float *sx, int q, int lane, uint64_t *xready,
                                                uint32_t parity, volatile int *abort) {
+    constexpr int W = C::COUT % 32 == 0 ? 32 : 16;
 #pragma unroll 1
-    for (int c0 = 0; c0 < C::COUT; c0 += 16) {
-        float o[16];
-        tmem_ld16(dcol + C::COUT + c0, o);
+    for (int c0 = 0; c0 < C::COUT; c0 += W) {
+        float o[W];
+        if constexpr (W == 32) tmem_ld32(dcol + C::COUT + c0, o);
+        else tmem_ld16(dcol + C::COUT + c0, o);
         if (lane == 0) {
+            float4 *d4 = reinterpret_cast<float4 *>(sx + q * C::COUT + c0);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) sx[q * C::COUT + c0 + j] = o[j];
+            for (int j4 = 0; j4 < W / 4; ++j4)
+                d4[j4] = make_float4(o[4 * j4], o[4 * j4 + 1], o[4 * j4 + 2], o[4 * j4 + 3]);
         }
     }
     mbar_arrive(xready);
@@ -429,7 +440,7 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
                                          int p, int m, bool valid, const float *sx = nullptr) {
     constexpr int ES = C::ES;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad;
-    constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) && !C::PAIRED ? 32 : 16;
+    constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
 #pragma unroll 1
     for (int cc = 0; cc < NC; cc += LDW) {
         float vv[LDW];
