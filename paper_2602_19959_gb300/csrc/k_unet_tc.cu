@@ -14,7 +14,7 @@
 // The skip concat is never materialised: the two inputs are copied into adjacent
 // K-planes of the same shared-memory tile.
 //
-// Tap pairing (the BF16 dec3_up2): a tcgen05.mma costs about the same for
+// Tap pairing (the BF16 dec3_up2 and dec2_up1): a tcgen05.mma costs about the same for
 // N up to 64 (reading A dominates), so the small-C_out convs stack two taps' weights in N:
 // per K step, taps (0, 1) on the tile as is, taps (2, 3) on the tile two rows down and tap
 // 4 four rows down, accumulating E (taps 0, 2, 4 of row r) and O (taps 1, 3 of row r - 1)
@@ -788,10 +788,10 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 // ---------------------------------------------------------------- weight packing (host)
 
 // Conv layers (0..5: enc2, enc3, enc4, dec3, dec2, dec1) whose taps are stacked in pairs
-// along N: where it measured faster, the BF16 dec3 (44 -> 28 MMAs per tile). The FP8 form
-// already halves the MMAs (K = 32), and dec2/dec1 are bound by their epilogue's latency,
-// which the pairing exchange lengthens.
-constexpr bool conv_paired(int li, int prec) { return li == 3 && prec == PVF_BF16; }
+// along N: where it measured faster, the BF16 dec3 (44 -> 28 MMAs per tile) and dec2. The
+// FP8 form already halves the MMAs (K = 32) and measured slower paired; dec1 is bound by
+// its epilogue.
+constexpr bool conv_paired(int li, int prec) { return (li == 3 || li == 4) && prec == PVF_BF16; }
 
 template <int PREC> struct Net {
     using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56>;    // 6 CTAs per SM
