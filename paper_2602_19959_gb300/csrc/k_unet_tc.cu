@@ -127,7 +127,8 @@ struct Cfg {
     static_assert(OFF_X % 16 == 0, "paired exchange in float4");
     static_assert(STAGES >= 2 && STAGES <= 6, "stages");
     static_assert(NB == 2 || NB == 4, "accumulator buffers");
-    static_assert(!PAIRED || (!PAIR && PIN % 2 == 0 && EWG <= 2 && 2 * COUT <= 256 && EPI != EPI_POOL),
+    static_assert(!PAIRED || (!PAIR && PIN % 2 == 0 && 2 * COUT <= 256 && EPI != EPI_POOL &&
+                              (EWG <= 2 || EPI == EPI_UP)),
                   "tap pairing");
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
@@ -409,14 +410,15 @@ __device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *
     for (int j = 0; j < W; ++j) v[j] += o[j];
 }
 
-// Paired taps: lane 0 of each quarter publishes its O row (all COUT columns) into sx, then
-// the threads of the conv epilogue meet on xready. Returns false on a timed-out wait.
-template <class C>
-__device__ __forceinline__ bool paired_publish(uint32_t dcol, float *sx, int q, int lane, uint64_t *xready,
-                                               uint32_t parity, volatile int *abort) {
-    constexpr int W = C::COUT % 32 == 0 ? 32 : 16;
+// Paired taps: lane 0 of each quarter publishes its O row (columns [c_beg, c_beg + NC))
+// into sx, then the threads of the conv epilogue meet on xready. Returns false on a
+// timed-out wait.
+template <class C, int NC>
+__device__ __forceinline__ bool paired_publish(uint32_t dcol, int c_beg, float *sx, int q, int lane,
+                                               uint64_t *xready, uint32_t parity, volatile int *abort) {
+    constexpr int W = NC % 32 == 0 ? 32 : 16;
 #pragma unroll 1
-    for (int c0 = 0; c0 < C::COUT; c0 += W) {
+    for (int c0 = c_beg; c0 < c_beg + NC; c0 += W) {
         float o[W];
         if constexpr (W == 32) tmem_ld32(dcol + C::COUT + c0, o);
         else tmem_ld16(dcol + C::COUT + c0, o);
@@ -570,7 +572,9 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                 if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
                 tc_fence_after();
                 if constexpr (C::PAIRED) {
-                    if (!paired_publish<C>(dcol, sx, q, lane, &xready[ab], ph_a, abort)) return false;
+                    if (!paired_publish<C, C::COUT / PER>(dcol, part * (C::COUT / PER), sx, q, lane, &xready[ab],
+                                                          ph_a, abort))
+                        return false;
                 }
                 epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
                                            valid, sx);
@@ -591,7 +595,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         if constexpr (C::EPI == EPI_FINAL) {
             float v[16];
             if constexpr (C::PAIRED) {
-                if (!paired_publish<C>(dcol, sx, q, lane, &xready[ab], ph_a, abort)) return false;
+                if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
                 paired_cols<C, 16>(dcol, 0, sx, q, lane, v);
             } else {
                 tmem_ld16(dcol, v);
@@ -639,7 +643,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         }
         if constexpr (C::EPI == EPI_UP) {   // one warpgroup: conv, then the ConvT
             if constexpr (C::PAIRED) {
-                if (!paired_publish<C>(dcol, sx, q, lane, &xready[ab], ph_a, abort)) return false;
+                if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
             }
             epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx);
             fence_proxy_async_smem();
@@ -702,8 +706,8 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
         mbar_init(&bar[B::DRAIN], 1);
         mbar_init(&bar[B::GREADY], 128);
         mbar_init(&bar[B::GREADY + 1], 128);
-        mbar_init(&bar[B::XREADY], 128);          // the conv epilogue's warpgroup
-        mbar_init(&bar[B::XREADY + 1], 128);
+        mbar_init(&bar[B::XREADY], 128 * ((C::EWG + 1) / 2));     // the conv epilogue's warpgroups
+        mbar_init(&bar[B::XREADY + 1], 128 * ((C::EWG + 1) / 2));
         *abort = 0;
         fence_mbar_init();
     }
