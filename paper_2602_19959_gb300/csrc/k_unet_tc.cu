@@ -24,6 +24,14 @@
 // LeakyReLU(0.01) in the epilogue; the fused ConvT reads the conv tile from shared
 // memory, so the deepest level's activations (e4, d3, d2) never reach global memory.
 //
+// Tiles: a CTA takes tiles blockIdx.x, + gridDim.x, ... In the many-CTA encoder kernels
+// (DYN) the producer instead takes the next index from a global counter and hands it to
+// the MMA thread and the epilogue through a small ring in shared memory (its own
+// mbarriers), so CTAs that progress faster take more tiles: with a static stride the six
+// CTAs sharing an SM finished their equal shares up to 50% apart. The last CTA to finish
+// resets the counter for the next launch. In the other kernels the ring's handshake per
+// tile measured slower than the imbalance it removes.
+//
 // Warp roles: warp 0 issues the bulk copies (weights once, then one halo'd activation
 // tile per 128 positions into a ring of stages); warp 1 allocates TMEM and one thread
 // issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the MMAs
@@ -59,7 +67,7 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_, int EWG_ = 1,
-          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false>
+          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = PREC == PVF_BF16 ? 2 : 1;      // bytes per element
@@ -83,6 +91,7 @@ struct Cfg {
     static constexpr int ROWS = kTileM + TAPS - 1;           // halo'd tile rows
     static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
     static constexpr bool PAIRED = PAIRED_;                 // taps stacked in pairs along N
+    static constexpr bool DYN = DYN_;                       // tiles from the global counter
     // output rows per tile: row 127 of a paired tile lacks O[128]; the fused final conv
     // also needs two rows on each side
     static constexpr int ROWS_OK = PAIRED ? kTileM - 1 : kTileM;
@@ -113,7 +122,7 @@ struct Cfg {
     static constexpr int OFF_X = align_up(OFF_G + G_BYTES, 128);
     static constexpr int X_BYTES = PAIRED ? 2 * 4 * COUT * 4 : 0;
     static constexpr int OFF_BAR = align_up(OFF_X + X_BYTES, 128);
-    static constexpr int SMEM = OFF_BAR + 256;
+    static constexpr int SMEM = OFF_BAR + 512;
     static constexpr uint32_t FMT = PREC == PVF_BF16 ? 1u : 0u;
     static constexpr uint32_t IDESC1 = idesc_f32acc(kTileM, COUT, FMT);
     static constexpr uint32_t IDESC2 = idesc_f32acc(kTileM, N2 > 0 ? N2 : 16, FMT);
@@ -151,6 +160,7 @@ struct TcArgs {
     int amax_out, amax_mid;             // slots of the stored output and of A2 (kScale*)
     int n_events;
     int32_t *status;
+    int32_t *sched;                     // [2]: next tile, finished CTAs (zero between launches)
 };
 
 // Calibration: folds max |v| of 16 values (rows with valid = false count as 0) into the
@@ -171,11 +181,16 @@ __device__ __forceinline__ void amax_fold(float *amax, int slot, const float (&v
 // phase before its waiters have seen the first; A2FULL/GREADY follow the two
 // shared-memory buffers of the fused ConvT operand and of the final conv's exchange
 // (tile i: i % 2).
+constexpr int kRing = 12;    // tile-index ring: >= STAGES + NB tiles in flight
 template <class C> struct Bars {
     static constexpr int W = 0, FULL = 1, EMPTY = 1 + C::STAGES, TFULL = 1 + 2 * C::STAGES,
                          TEMPTY = TFULL + C::NB, T2FULL = TEMPTY + C::NB, A2FULL = T2FULL + C::NB,
-                         DRAIN = A2FULL + 2, GREADY = DRAIN + 1, XREADY = GREADY + 2, N = XREADY + 2;
-    static_assert(N * 8 + 8 <= 256, "barrier area");
+                         DRAIN = A2FULL + 2, GREADY = DRAIN + 1, XREADY = GREADY + 2,
+                         TIDF = XREADY + 2, TIDE = TIDF + kRing, N = TIDE + kRing;
+    // after the barriers: TMEM address slot, abort flag, then the ring of tile indices
+    static constexpr int RING_OFF = N * 8 + 16;
+    static_assert(RING_OFF + 4 * kRing <= 512, "barrier area");
+    static_assert(kRing >= C::STAGES + C::NB, "ring depth");
 };
 
 template <class C>
@@ -212,16 +227,29 @@ __device__ __forceinline__ void zero_planes(unsigned char *base, int64_t e, int 
 }
 
 template <class C>
-__device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, volatile int *abort) {
+__device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, volatile int *ring,
+                         volatile int *abort) {
     using B = Bars<C>;
-    uint64_t *wbar = bar + B::W, *full = bar + B::FULL, *empty = bar + B::EMPTY;
+    uint64_t *wbar = bar + B::W, *full = bar + B::FULL, *empty = bar + B::EMPTY, *tidf = bar + B::TIDF,
+             *tide = bar + B::TIDE;
     const int ntiles = a.n_events * C::TPE;
     mbar_arrive_expect_tx(wbar, C::W_BYTES + C::W2_BYTES);
     bulk_g2s(smem + C::OFF_W, a.w, C::W_BYTES, wbar);
     if (C::W2_BYTES) bulk_g2s(smem + C::OFF_W2, a.w2, C::W2_BYTES, wbar);
     int i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    // DYN: one tile index ahead, so the atomic's latency overlaps a tile; else a stride
+    int t_next = C::DYN ? atomicAdd(a.sched, 1) : (int)blockIdx.x;
+    for (;; ++i) {
+        const int t = t_next < ntiles ? t_next : -1;
+        if constexpr (C::DYN) {   // next tile (or -1: none left) to the MMA thread and the epilogue
+            const int r = i % kRing;
+            if (!mbar_wait(&tide[r], ((i / kRing) & 1) ^ 1, abort)) { ok = false; break; }
+            ring[r] = t;
+            mbar_arrive(&tidf[r]);
+        }
+        if (t < 0) break;
+        t_next = C::DYN ? atomicAdd(a.sched, 1) : t + (int)gridDim.x;
         const int s = i % C::STAGES;
         const uint32_t ph = (i / C::STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
@@ -321,20 +349,29 @@ __device__ __forceinline__ void issue_up(uint32_t d2, uint32_t a2, uint32_t w2_b
 // conv accumulator into the shared-memory operand of its ConvT.
 template <class C>
 __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
-                           volatile int *abort) {
+                           volatile int *ring, volatile int *abort) {
     using B = Bars<C>;
     uint64_t *wbar = bar + B::W, *full = bar + B::FULL, *empty = bar + B::EMPTY,
              *tfull = bar + B::TFULL, *tempty = bar + B::TEMPTY, *a2full = bar + B::A2FULL,
-             *t2full = bar + B::T2FULL, *drain = bar + B::DRAIN;
-    const int ntiles = a.n_events * C::TPE;
+             *t2full = bar + B::T2FULL, *drain = bar + B::DRAIN, *tidf = bar + B::TIDF, *tide = bar + B::TIDE;
     bool ok = mbar_wait(wbar, 0, abort);
     tc_fence_after();
     const uint32_t a_base = smem_u32(smem + C::OFF_A);
     const uint32_t w_base = smem_u32(smem + C::OFF_W);
     const uint32_t w2_base = smem_u32(smem + C::OFF_W2);
     const uint32_t a2_base = smem_u32(smem + C::OFF_A2);
+    const int ntiles = a.n_events * C::TPE;
     int i = 0;
-    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++i) {
+    for (; ok; ++i) {
+        if constexpr (C::DYN) {
+            const int r = i % kRing;
+            if (!mbar_wait(&tidf[r], (i / kRing) & 1, abort)) { ok = false; break; }
+            const int t = ring[r];
+            mbar_arrive(&tide[r]);
+            if (t < 0) break;
+        } else if ((int)blockIdx.x + i * (int)gridDim.x >= ntiles) {
+            break;
+        }
         const int s = i % C::STAGES, b = i % C::NB;
         const uint32_t ph_s = (i / C::STAGES) & 1, ph_b = (i / C::NB) & 1;
         if (!mbar_wait(&tempty[b], ph_b ^ 1, abort) || !mbar_wait(&full[s], ph_s, abort)) { ok = false; break; }
@@ -540,10 +577,11 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
 
 template <class C>
 __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, uint32_t tmem,
-                         volatile int *abort, int warp, int lane) {
+                         volatile int *ring, volatile int *abort, int warp, int lane) {
     using B = Bars<C>;
     uint64_t *tfull = bar + B::TFULL, *tempty = bar + B::TEMPTY, *a2full = bar + B::A2FULL,
-             *t2full = bar + B::T2FULL, *gready = bar + B::GREADY, *xready = bar + B::XREADY;
+             *t2full = bar + B::T2FULL, *gready = bar + B::GREADY, *xready = bar + B::XREADY,
+             *tidf = bar + B::TIDF, *tide = bar + B::TIDE;
     const float *par = reinterpret_cast<const float *>(smem + C::OFF_PAR);
     const float *sbias = par, *sbias2 = par + C::COUT, *scs = par + C::COUT + C::N2,
                 *scs2 = scs + C::COUT, *sfin = par + 2 * (C::COUT + C::N2);
@@ -551,11 +589,21 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
     const int m = q * 32 + lane;                    // tile row
     const int wg = (warp - 2) >> 2;                 // epilogue warpgroup
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
-    const int ntiles = a.n_events * C::TPE;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
     constexpr bool ROLES = C::EPI == EPI_UP && C::EWG >= 2;
-    int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    const int ntiles = a.n_events * C::TPE;
+    for (int i = 0;; ++i) {
+        int t = (int)blockIdx.x + i * (int)gridDim.x;
+        if constexpr (C::DYN) {
+            const int r = i % kRing;
+            if (!mbar_wait(&tidf[r], (i / kRing) & 1, abort)) return false;
+            t = ring[r];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tide[r]);
+            if (t < 0) break;
+        } else if (t >= ntiles) {
+            break;
+        }
         const int b = i % C::NB, ab = i & 1;
         const uint32_t ph_b = (i / C::NB) & 1, ph_a = (i >> 1) & 1;
         int e, p0;
@@ -678,6 +726,7 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + B::N);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *ring = reinterpret_cast<volatile int *>(reinterpret_cast<unsigned char *>(bar) + B::RING_OFF);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // biases, column scales and the final conv in shared memory
@@ -708,6 +757,10 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
         mbar_init(&bar[B::GREADY + 1], 128);
         mbar_init(&bar[B::XREADY], 128 * ((C::EWG + 1) / 2));     // the conv epilogue's warpgroups
         mbar_init(&bar[B::XREADY + 1], 128 * ((C::EWG + 1) / 2));
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&bar[B::TIDF + r], 1);                // the producer
+            mbar_init(&bar[B::TIDE + r], 1 + 4 * C::EWG);   // the MMA thread and each epilogue warp
+        }
         *abort = 0;
         fence_mbar_init();
     }
@@ -726,11 +779,11 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
 
     bool ok = true;
     if (warp == 0) {
-        if (lane == 0) ok = producer<C>(a, smem, bar, abort);
+        if (lane == 0) ok = producer<C>(a, smem, bar, ring, abort);
     } else if (warp == 1) {
-        if (lane == 0) ok = mma_issuer<C>(a, smem, bar, tmem, abort);
+        if (lane == 0) ok = mma_issuer<C>(a, smem, bar, tmem, ring, abort);
     } else {
-        ok = epilogue<C>(a, smem, bar, tmem, abort, warp, lane);
+        ok = epilogue<C>(a, smem, bar, tmem, ring, abort, warp, lane);
     }
     if (!ok) {
         *abort = 1;
@@ -740,6 +793,13 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, C::TMEM_COLS);
+    if (C::DYN && threadIdx.x == 0) {   // the last CTA to finish resets the counter for the next launch
+        __threadfence();
+        if (atomicAdd(a.sched + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(a.sched, 0);
+            atomicExch(a.sched + 1, 0);
+        }
+    }
 }
 
 int sm_count() {
@@ -798,8 +858,8 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 constexpr bool conv_paired(int li, int prec) { return (li == 3 || li == 4) && prec == PVF_BF16; }
 
 template <int PREC> struct Net {
-    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56>;    // 6 CTAs per SM
-    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80>;    // 4
+    using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56, 2, false, true>;    // 6 CTAs per SM
+    using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80, 2, false, true>;    // 4
     using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4,
                         PREC == PVF_BF16 ? 2 : 4, 96, 4>;                                  // 1
     using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4, conv_paired(3, PREC)>; // 1 CTA/SM
@@ -962,31 +1022,34 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStre
     a.n_events = ne;
     a.status = n.status;
     a.amax = n.amax;
+    // one scheduler counter pair per kernel family (each launch leaves it at zero)
+    auto sched = [&](int k) { return n.sched + 2 * k; };
+    a.sched = sched(0);
     // enc2: p1 (s0) -> e2, p2 (s1)
     a.inA = U(b.s0); a.inB = nullptr; a.out = U(b.e2); a.outp = U(b.s1);
     a.w = W(0); a.bias = n.b[0]; a.cs = cs(0); a.out_inv = inv(kScaleL2); a.amax_out = kScaleL2;
     if ((err = launch_conv<typename N::Enc2>(a, s, prof, "enc2")) != cudaSuccess) return err;
     // enc3: p2 (s1) -> e3, p3 (s0)
-    a.inA = U(b.s1); a.out = U(b.e3); a.outp = U(b.s0);
+    a.inA = U(b.s1); a.out = U(b.e3); a.outp = U(b.s0); a.sched = sched(1);
     a.w = W(1); a.bias = n.b[1]; a.cs = cs(1); a.out_inv = inv(kScaleL3); a.amax_out = kScaleL3;
     if ((err = launch_conv<typename N::Enc3>(a, s, prof, "enc3")) != cudaSuccess) return err;
     // enc4 + up3: p3 (s0) -> u3 (up)
-    a.inA = U(b.s0); a.out = U(b.up); a.outp = nullptr;
+    a.inA = U(b.s0); a.out = U(b.up); a.outp = nullptr; a.sched = sched(2);
     a.w = W(2); a.bias = n.b[2]; a.cs = cs(2); a.w2 = W(6); a.bias2 = n.b[6]; a.cs2 = cs(6);
     a.mid_inv = inv(kScaleE4); a.out_inv = inv(kScaleL3); a.amax_mid = kScaleE4; a.amax_out = kScaleL3;
     if ((err = launch_conv<typename N::Enc4Up3>(a, s, prof, "enc4_up3")) != cudaSuccess) return err;
     // dec3 + up2: [u3 (up), e3] -> u2 (deep)
-    a.inA = U(b.up); a.inB = U(b.e3); a.out = U(b.deep);
+    a.inA = U(b.up); a.inB = U(b.e3); a.out = U(b.deep); a.sched = sched(3);
     a.w = W(3); a.bias = n.b[3]; a.cs = cs(3); a.w2 = W(7); a.bias2 = n.b[7]; a.cs2 = cs(7);
     a.mid_inv = inv(kScaleD3); a.out_inv = inv(kScaleL2); a.amax_mid = kScaleD3; a.amax_out = kScaleL2;
     if ((err = launch_conv<typename N::Dec3Up2>(a, s, prof, "dec3_up2")) != cudaSuccess) return err;
     // dec2 + up1: [u2 (deep), e2] -> u1 (up)
-    a.inA = U(b.deep); a.inB = U(b.e2); a.out = U(b.up);
+    a.inA = U(b.deep); a.inB = U(b.e2); a.out = U(b.up); a.sched = sched(4);
     a.w = W(4); a.bias = n.b[4]; a.cs = cs(4); a.w2 = W(8); a.bias2 = n.b[8]; a.cs2 = cs(8);
     a.mid_inv = inv(kScaleD2); a.out_inv = inv(kScaleL1); a.amax_mid = kScaleD2; a.amax_out = kScaleL1;
     if ((err = launch_conv<typename N::Dec2Up1>(a, s, prof, "dec2_up1")) != cudaSuccess) return err;
     // dec1 + final conv: [u1 (up), e1] -> logits (float32)
-    a.inA = U(b.up); a.inB = U(b.e1); a.out = nullptr; a.w2 = nullptr; a.bias2 = nullptr;
+    a.inA = U(b.up); a.inB = U(b.e1); a.out = nullptr; a.w2 = nullptr; a.bias2 = nullptr; a.sched = sched(5);
     a.cs2 = nullptr; a.logits = b.logits; a.final_w = n.final_w; a.amax_out = kScaleD1;
     a.w = W(5); a.bias = n.b[5]; a.cs = cs(5);
     return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final");

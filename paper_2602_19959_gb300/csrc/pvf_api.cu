@@ -354,6 +354,8 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
             std::memcpy(views[i].shape, layers[i].shape, sizeof views[i].shape);
         }
         h->tc.status = reinterpret_cast<int32_t *>(h->pool + plan.status);
+        // status word at 0, calibration maxima at 64, tile schedulers at 128 (zeroed below)
+        h->tc.sched = reinterpret_cast<int32_t *>(h->pool + plan.status + 128);
         if (!tc_pack_weights(cfg->precision, views, h->act_scale, tcw, &h->tc, h->pool + plan.tcw)) {
             delete h;
             return PVF_ERR_WEIGHTS;

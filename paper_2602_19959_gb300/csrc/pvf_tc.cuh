@@ -38,6 +38,7 @@ struct TcNet {
     const unsigned char *fc_img;   // bf16 FC operand images (kFcImgBytes)
     float *amax;             // calibration capture (kNumScales floats) or null
     int32_t *status;         // device status word
+    int32_t *sched;          // 6 x 2 tile-scheduler counters (zero between launches)
 };
 
 size_t tc_weight_bytes(int precision);
