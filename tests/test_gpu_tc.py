@@ -147,6 +147,30 @@ def test_bf16_full_size_sampled(PVFinder, weights):
     assert np.all(r["count"] >= 0)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_chunked_and_repeated_launches_equal_one_launch(PVFinder, weights, precision, request):
+    """One call split into UNet chunks of 16 events, and the same handle reused for
+    different batch sizes, give bit for bit the results of a single launch: every kernel
+    (including the encoders' tile counters, which each launch leaves at zero) starts
+    from a clean state."""
+    kw = {}
+    if precision == "fp8":
+        kw["fp8_act_scales"] = request.getfixturevalue("fp8_scales")
+    b = synth.generate_uneven(48, 31)
+    one = PVFinder(weights, precision=precision, max_events=48, max_pv_per_event=MAX_PV, **kw)
+    chunked = PVFinder(weights, precision=precision, max_events=48, chunk_events=16,
+                       max_pv_per_event=MAX_PV, **kw)
+    r1 = run_full(one, b)
+    rc = run_full(chunked, b)
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(rc[k], r1[k])
+    for n in (1, 7, 48, 3):          # sizes that leave different tile counts per launch
+        rs = run_full(one, b.subset(0, n))
+        for k in ("hist", "logit", "count"):
+            np.testing.assert_array_equal(rs[k], r1[k][:n])
+    assert one.device_status() == 0 and chunked.device_status() == 0
+
+
 # ---------------------------------------------------------------- FP8 (E4M3)
 
 @pytest.fixture(scope="module")
