@@ -36,9 +36,7 @@ __device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_
         *reinterpret_cast<uint4 *>(cb + planar_off(e, 1, 2, rows_e, row)) = pk[1];
     } else {
         uint4 pk;
-        __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv_scale);
+        pack_e4m3<16>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
         unsigned char *cb = reinterpret_cast<unsigned char *>(base);
         *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 1, rows_e, row)) = pk;
     }
@@ -135,9 +133,7 @@ __device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_
         *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, h, 2, rows_e, row)) = pk;
     } else {
         uint2 pk;
-        __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv_scale);
+        pack_e4m3<8>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
         *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, 0, 1, rows_e, row) + 8 * h) = pk;
     }
 }

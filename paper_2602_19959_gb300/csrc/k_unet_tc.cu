@@ -213,9 +213,7 @@ __device__ __forceinline__ void put16(unsigned char *p0, size_t plane_stride, co
         *reinterpret_cast<uint4 *>(p0 + plane_stride) = pk[1];
     } else {
         uint4 pk;
-        __nv_fp8_e4m3 *b = reinterpret_cast<__nv_fp8_e4m3 *>(&pk);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) b[i] = __nv_fp8_e4m3(v[i] * inv);
+        pack_e4m3<16>(v, inv, reinterpret_cast<unsigned char *>(&pk));
         *reinterpret_cast<uint4 *>(p0) = pk;
     }
 }
