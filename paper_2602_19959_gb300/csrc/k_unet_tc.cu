@@ -10,9 +10,22 @@
 //   enc4_up3  conv 64->128 @500,  epilogue feeds a second GEMM: ConvT 128->64 (k2 s2)
 //   dec3_up2  conv [64|64]->64 @1000, + ConvT 64->32
 //   dec2_up1  conv [32|32]->32 @2000, + ConvT 32->16
-//   dec1      conv [16|16]->16 @4000
+//   dec1      conv [16|16]->16 @4000, + the final conv 16->1 (logits)
 // The skip concat is never materialised: the two inputs are copied into adjacent
-// K-planes of the same shared-memory tile.
+// K-planes of the same shared-memory tile. Every conv and ConvT output goes through
+// LeakyReLU(0.01) in the epilogue; the fused ConvT reads the conv tile from shared
+// memory, so the deepest level's activations (e4, d3, d2) never reach global memory.
+//
+// Warp roles: warp 0 issues the bulk copies (weights once, then one halo'd activation
+// tile per 128 positions into a ring of stages); warp 1 allocates TMEM and one thread
+// issues the MMAs into NB accumulator buffers, so the MMAs of tile i wait only for the
+// epilogue of tile i - NB; the remaining one, two or four warpgroups are the epilogue,
+// one TMEM lane (= output position) per thread. With a fused ConvT and two or four
+// epilogue warpgroups they split by role: half of them turn each conv accumulator into
+// the ConvT's shared-memory operand, the other half store the ConvT output (written over
+// the conv columns, already read) and free the buffer, so the operand of tile i is ready
+// while the tensor core still runs the conv of tile i + 1; the two warpgroups of a role
+// (if four) split its columns. Otherwise two warpgroups split the accumulator columns.
 //
 // Tap pairing (the BF16 dec3_up2 and dec2_up1): a tcgen05.mma costs about the same for
 // N up to 64 (reading A dominates), so the small-C_out convs stack two taps' weights in N:
@@ -20,9 +33,7 @@
 // 4 four rows down, accumulating E (taps 0, 2, 4 of row r) and O (taps 1, 3 of row r - 1)
 // side by side. The conv at row r is E[r] + O[r + 1]: a one-lane shuffle, and through
 // shared memory across the warps' lane quarters. Row 127 of a tile lacks O[128], so
-// paired tiles advance by 127 rows. Three MMAs per K step replace five. Every conv and ConvT output goes through
-// LeakyReLU(0.01) in the epilogue; the fused ConvT reads the conv tile from shared
-// memory, so the deepest level's activations (e4, d3, d2) never reach global memory.
+// paired tiles advance by 127 rows. Three MMAs per K step replace five.
 //
 // Tiles: a CTA takes tiles blockIdx.x, + gridDim.x, ... In the many-CTA encoder kernels
 // (DYN) the producer instead takes the next index from a global counter and hands it to
@@ -32,17 +43,10 @@
 // resets the counter for the next launch. In the other kernels the ring's handshake per
 // tile measured slower than the imbalance it removes.
 //
-// Warp roles: warp 0 issues the bulk copies (weights once, then one halo'd activation
-// tile per 128 positions into a ring of stages); warp 1 allocates TMEM and one thread
-// issues the MMAs (two accumulator buffers, so the epilogue of tile i overlaps the MMAs
-// of tile i + 1); the remaining one, two or four warpgroups are the epilogue, one TMEM
-// lane (= output position) per thread. With a fused ConvT and two or four epilogue
-// warpgroups they split by role: half of them turn each conv accumulator into the
-// ConvT's shared-memory operand, the other half store the ConvT output and free the
-// accumulator buffer, so the operand of tile i is ready while the tensor core still runs
-// the conv of tile i + 1; the two warpgroups of a role (if four) split its columns.
-// Otherwise two warpgroups split the accumulator columns. Every wait is bounded (1 s); on timeout the kernel records PVF_ERR_TIMEOUT,
-// drains its own copies and MMAs, frees TMEM and returns.
+// Launch: programmatic dependent launch. The prologue (weights, parameters, barriers,
+// TMEM) runs before griddepcontrol.wait, i.e. while the previous kernel finishes; the
+// kernel then lets the next one launch. Every wait is bounded (1 s); on timeout the
+// kernel records PVF_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
 #include "pvf_tc.cuh"
 #include "tc_ptx.cuh"
 
