@@ -11,8 +11,8 @@
 //      becomes ln(0.01 / 0.99)), which avoids the float32 saturation of sigmoid
 //      (which rounds to 1 for f > 16.6) turning distinct maxima into ties;
 //   3. z = centroid over bins [i - 3, i + 3] with weights p[j] = sigmoid(f[j]);
-//   4. ordered compaction: candidate flags are packed into bit masks by warp ballots;
-//      each thread then owns 16 consecutive bins, and a block-wide exclusive scan of
+//   4. ordered compaction: each thread owns 16 consecutive bins and tests them in
+//      registers (a 16-bit candidate mask); a block-wide exclusive scan of
 //      the per-thread counts gives each PV its slot, so PVs are written in ascending z
 //      without atomics. The true count is always reported.
 #include "pvf_internal.cuh"
@@ -104,28 +104,32 @@ __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
         }
         if (a.pv_count) {
             const bool bypass = a.ev_flag && a.ev_flag[ge] != 0;
-            // ---- candidate flags: consecutive lanes test consecutive bins (conflict-free shared
-            //      reads); a warp ballot packs 32 bins into one mask word
-            __shared__ uint32_t smask[kThreads * kPerThread / 32];
-            for (int i0 = warp * 32; i0 < kThreads * kPerThread; i0 += kThreads) {
-                const int i = i0 + lane;
-                bool c = false;
-                if (!bypass && i < kBins) {
-                    const float fi = sf[i];
-                    c = fi > kThrLogit;
-#pragma unroll
-                    for (int d = 1; d <= kPeakHalfWin; ++d) {
-                        if (i - d >= 0) c &= fi > sf[i - d];
-                        if (i + d < kBins) c &= fi >= sf[i + d];
-                    }
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, c);
-                if (lane == 0) smask[i0 >> 5] = m;
-            }
-            __syncthreads();
-            // thread tid owns bins [16 tid, 16 tid + 16): half a mask word
+            // ---- candidate flags: thread tid owns bins [16 tid, 16 tid + 16). It loads them with
+            //      their +-5 neighbours (bins 16 tid - 8 .. 16 tid + 23, 16-byte loads) into
+            //      registers and tests each bin there; bins outside [0, kBins) read as -inf, which
+            //      no finite logit fails (the same as not comparing clipped neighbours).
+            static_assert(kBins % 4 == 0 && kPerThread == 16 && kPeakHalfWin <= 8, "flag window");
             const int i0 = tid * kPerThread;
-            unsigned mask = (smask[tid >> 1] >> ((tid & 1) * 16)) & 0xFFFFu;
+            unsigned mask = 0;
+            if (!bypass && i0 < kBins) {
+                const float ninf = __int_as_float(0xff800000);
+                const float4 *s4 = reinterpret_cast<const float4 *>(sf);
+                float w[kPerThread + 16];
+#pragma unroll
+                for (int k = 0; k < (kPerThread + 16) / 4; ++k) {
+                    const int j = i0 - 8 + 4 * k;
+                    const float4 x = (j >= 0 && j + 3 < kBins) ? s4[j >> 2] : make_float4(ninf, ninf, ninf, ninf);
+                    w[4 * k] = x.x; w[4 * k + 1] = x.y; w[4 * k + 2] = x.z; w[4 * k + 3] = x.w;
+                }
+#pragma unroll
+                for (int b = 0; b < kPerThread; ++b) {
+                    const float fi = w[b + 8];
+                    bool c = i0 + b < kBins && fi > kThrLogit;
+#pragma unroll
+                    for (int d = 1; d <= kPeakHalfWin; ++d) c = c && fi > w[b + 8 - d] && fi >= w[b + 8 + d];
+                    mask |= (unsigned)c << b;
+                }
+            }
             const int cnt = __popc(mask);
             // ---- block exclusive scan of cnt
             int incl = cnt;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
                 if (!bypass && total > a.max_pv) raise_status(a.status, PVF_WARN_TRUNCATED);
             }
         }
-        __syncthreads();                       // sf, smask and swarp are reused next event
+        __syncthreads();                       // sf and swarp are reused next event
     }
 }
 
