@@ -10,7 +10,7 @@ events. `value` is device time (CUDA events on the launch stream, max over ranks
 including the host->device copy of the track features and offsets and the
 device->host copy of the PV lists.
 
-  python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16|fp8]
+  python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16|fp16|fp8]
   python bench.py --mode batch --events 50000     # one autotuned graph launch, uneven events
   python bench.py --mode serve                    # Poisson arrivals at 20k..200k events/s
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
@@ -56,7 +56,7 @@ def convT_io(L, cin, cout):
 def kernel_table(form):
     """Algorithmic work per event of each kernel family: (MAC, bytes, compute unit).
     MACs of the FC depend on the track count and are added by the caller."""
-    es = {"fp32": 4, "bf16": 2, "fp8": 1}[form]
+    es = {"fp32": 4, "bf16": 2, "fp16": 2, "fp8": 1}[form]
     t = {}
     e1 = 16 * 4004 + 16 * 2004               # e1 and p1 written by the front kernel
     t["front"] = (4000 * 16 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
@@ -405,7 +405,7 @@ def run_step(args, weights, batch, rank, world, local):
         build()
     barrier(world)
 
-    dtype = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision]
+    dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision]
     pv = make_finder(args, weights, args.precision, args.events, max_pv_per_event=args.max_pv)
     feats_h = torch.from_numpy(batch.features).pin_memory()
     offs_h = torch.from_numpy(batch.offsets).pin_memory()
@@ -452,7 +452,7 @@ def run_step(args, weights, batch, rank, world, local):
     traffic = NCU_TRAFFIC.get((args.precision, name, args.events))
     roof.update({"kernel": name, "traffic": traffic,
                  "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
-                                "fp32 ALU = 152 SM x 128 lanes x 2 x sm_max_mhz; fp8 = 2 x bf16)"})
+                                "fp32 ALU = 152 SM x 128 lanes x 2 x sm_max_mhz; fp16 = bf16; fp8 = 2 x bf16)"})
     gpu_launches = int(sum(n for n, _ in prof.values()))
 
     h2d = batch.features.nbytes + batch.offsets.nbytes
@@ -548,7 +548,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step")
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--max-pv", type=int, default=672)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -66,8 +66,11 @@ typedef enum {
 typedef enum {
     PVF_FP32 = 0,      /* CUDA-core float32 ("plain FP32 GPU form")                     */
     PVF_BF16 = 1,      /* tcgen05 tensor cores, bf16 operands, fp32 accumulation         */
-    PVF_FP8_E4M3 = 2   /* tcgen05 tensor cores, e4m3 operands with per-output-channel
+    PVF_FP8_E4M3 = 2,  /* tcgen05 tensor cores, e4m3 operands with per-output-channel
                           weight scales and per-tensor activation scales, fp32 accum.   */
+    PVF_FP16 = 3       /* tcgen05 tensor cores, f16 operands, fp32 accumulation: the
+                          mixed-precision form proposed in §5 (Table 2). Stored values beyond
+                          the f16 range saturate to +-65504 (NaN stays NaN).           */
 } pvf_precision;
 
 /* Creation-time plan (§3: TensorSpec freezing batch dimensions, channels, length and

@@ -18,7 +18,7 @@ __device__ __forceinline__ int slice_of(float z) {
 }
 
 // Stores the 16 channels of storage row `row` of event e: channel-last float32 rows for
-// the FP32 form, plane-major rows (two bf16 planes / one e4m3 plane) otherwise.
+// the FP32 form, plane-major rows (two 16-bit planes / one e4m3 plane) otherwise.
 template <class T>
 __device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_e, int64_t row,
                                             const float v[kC0], float inv_scale) {
@@ -27,13 +27,9 @@ __device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_
 #pragma unroll
         for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     } else if constexpr (sizeof(T) == 2) {
-        uint4 pk[2];
-        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(pk);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
         unsigned char *cb = reinterpret_cast<unsigned char *>(base);
-        *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)) = pk[0];
-        *reinterpret_cast<uint4 *>(cb + planar_off(e, 1, 2, rows_e, row)) = pk[1];
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)) = pack8<T>(v);
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 1, 2, rows_e, row)) = pack8<T>(v + 8);
     } else {
         uint4 pk;
         pack_e4m3<16>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
@@ -117,7 +113,7 @@ __device__ __forceinline__ void track_features(const FrontArgs &a, int64_t gt, i
 }
 
 // Stores channels [8 h, 8 h + 8) of storage row `row` of event e: half a channel-last
-// float32 row, one of the two bf16 planes, or half of the e4m3 plane's 16-byte row.
+// float32 row, one of the two 16-bit planes, or half of the e4m3 plane's 16-byte row.
 template <class T>
 __device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_e, int64_t row, int h,
                                             const float v[8], float inv_scale) {
@@ -126,11 +122,8 @@ __device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_
         d[0] = make_float4(v[0], v[1], v[2], v[3]);
         d[1] = make_float4(v[4], v[5], v[6], v[7]);
     } else if constexpr (sizeof(T) == 2) {
-        uint4 pk;
-        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(&pk);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, h, 2, rows_e, row)) = pk;
+        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, h, 2, rows_e, row)) =
+            pack8<T>(v);
     } else {
         uint2 pk;
         pack_e4m3<8>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));

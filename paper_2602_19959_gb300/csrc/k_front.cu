@@ -210,11 +210,9 @@ cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem, cudaStream_t
 
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    switch (precision) {
-    case PVF_FP32: return launch_front_t<PVF_FP32, true>(a, smem, s);
-    case PVF_BF16: return launch_front_t<PVF_BF16, true>(a, smem, s);
-    default: return launch_front_t<PVF_FP8_E4M3, true>(a, smem, s);
-    }
+    // the tensor-core forms run k_front_tc
+    if (precision != PVF_FP32) return cudaErrorInvalidValue;
+    return launch_front_t<PVF_FP32, true>(a, smem, s);
 }
 
 }  // namespace pvf

@@ -1,5 +1,6 @@
 // Steps 1-2 of the path (§2) for the tensor-core forms: the per-track FC network on
-// tcgen05 (bf16 operands, fp32 accumulation in TMEM), the deterministic histogram, and
+// tcgen05 (16-bit operands: f16 in the FP16 form, bf16 in the BF16 and FP8 forms; fp32
+// accumulation in TMEM), the deterministic histogram, and
 // enc1 + pool. A persistent grid (two CTAs per SM) walks the events, one event at a time
 // per CTA (§3: each event is processed by one thread block), so weights and TMEM are set
 // up once per CTA rather than once per event.
@@ -7,7 +8,7 @@
 // Per pass of up to 256 slice-sorted tracks (two 128-row tiles, one per warpgroup, one
 // track per TMEM lane / thread in the hidden layers):
 //   X [256 x 16] (nine features, feature 2 slice-relative, zero padded) ->
-//   5 x { MMA per tile (M = 128 tracks, N = 32) -> TMEM -> bias + LeakyReLU -> bf16 ->
+//   5 x { MMA per tile (M = 128 tracks, N = 32) -> TMEM -> bias + LeakyReLU -> 16-bit ->
 //         H [256 x 32] } ->
 //   output layer as the transposed product Out^T = W6^T H^T (one MMA, M = 128 output
 //   lanes, N = tracks of the pass), so TMEM lane = output bin and column = sorted track ->
@@ -49,16 +50,18 @@ struct TcSmem {
     __host__ __device__ static size_t total(int mt) { return slices(mt) + (size_t)mt + 16; }
 };
 
-__device__ __forceinline__ uint4 pack8_bf16(const float *v) {
-    uint4 r;
-    __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(&r);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    return r;
-}
+// FC operand type of each form and its tcgen05 kind::f16 format code (0 = f16, 1 = bf16).
+template <int PREC> struct FcOp {
+    using T = __nv_bfloat16;
+    static constexpr uint32_t FMT = 1;
+};
+template <> struct FcOp<PVF_FP16> {
+    using T = __half;
+    static constexpr uint32_t FMT = 0;
+};
 
 // softplus(x) = max(x, 0) + log(1 + u), u = exp(-|x|) in (0, 1], for the tensor-core forms
-// (their FC operands are bf16): the hardware exp2/log2 approximations give it in a few
+// (their FC operands are 16-bit): the hardware exp2/log2 approximations give it in a few
 // instructions with an absolute error of a few 1e-7. Below x = -15 the value is u itself
 // (log(1 + u) = u to 1e-7 relative), which keeps tiny terms positive instead of rounding
 // 1 + u to 1.
@@ -71,6 +74,8 @@ __device__ __forceinline__ float softplus_tc(float x) {
 template <int PREC>
 __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     using T = typename Elem<PREC>::T;
+    using FT = typename FcOp<PREC>::T;
+    constexpr uint32_t FMT = FcOp<PREC>::FMT;
     extern __shared__ __align__(128) unsigned char smem[];
     float *sbias = reinterpret_cast<float *>(smem + TcSmem::bias);
     float *senc = reinterpret_cast<float *>(smem + TcSmem::enc1);
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                 const bool active = g < ntile;         // warpgroup has a tile in this pass
                 const int r = c0 + g * kRows + m;
                 const bool live = r < nvalid;
-                if (active) {   // X row: the track's features in bf16, zero rows past the event
+                if (active) {   // X row: the track's features in 16 bits, zero rows past the event
                     float x[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) x[k] = 0.0f;
@@ -150,8 +155,8 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                         const int t = ssorted[r];
                         track_features(a, t0 + t, sslice[t], x);
                     }
-                    *reinterpret_cast<uint4 *>(xrow) = pack8_bf16(x);
-                    *reinterpret_cast<uint4 *>(xrow + kPlane) = pack8_bf16(x + 8);
+                    *reinterpret_cast<uint4 *>(xrow) = pack8<FT>(x);
+                    *reinterpret_cast<uint4 *>(xrow + kPlane) = pack8<FT>(x + 8);
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
@@ -163,25 +168,25 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                     if (tid == 0) {
                         if (l == 0) {
                             for (int tg = 0; tg < ntile; ++tg)
-                                mma_bf16(tmem + (uint32_t)(tg * 128), smem_desc(sx + tg * kRows * 16, kPlane, 128),
-                                         smem_desc(img, kFcHidden * 16, 128), idesc_f32acc(kRows, kFcHidden, 1), 0);
+                                mma_f16(tmem + (uint32_t)(tg * 128), smem_desc(sx + tg * kRows * 16, kPlane, 128),
+                                        smem_desc(img, kFcHidden * 16, 128), idesc_f32acc(kRows, kFcHidden, FMT), 0);
                         } else if (l < 5) {
                             const uint32_t w = img + fc_img_off(l);
                             for (int tg = 0; tg < ntile; ++tg) {
 #pragma unroll
                                 for (int kb = 0; kb < 2; ++kb)
-                                    mma_bf16(tmem + (uint32_t)(tg * 128),
-                                             smem_desc(sh + tg * kRows * 16 + 2 * kb * kPlane, kPlane, 128),
-                                             smem_desc(w + 2 * kb * kFcHidden * 16, kFcHidden * 16, 128),
-                                             idesc_f32acc(kRows, kFcHidden, 1), kb);
+                                    mma_f16(tmem + (uint32_t)(tg * 128),
+                                            smem_desc(sh + tg * kRows * 16 + 2 * kb * kPlane, kPlane, 128),
+                                            smem_desc(w + 2 * kb * kFcHidden * 16, kFcHidden * 16, 128),
+                                            idesc_f32acc(kRows, kFcHidden, FMT), kb);
                             }
                         } else {   // Out^T [128 lanes x n6] = W6^T (A) x H^T (B = H, K-major)
                             const uint32_t w = img + fc_img_off(5);
 #pragma unroll
                             for (int kb = 0; kb < 2; ++kb)
-                                mma_bf16(tmem, smem_desc(w + 2 * kb * kFcM6 * 16, kFcM6 * 16, 128),
-                                         smem_desc(sh + 2 * kb * kPlane, kPlane, 128),
-                                         idesc_f32acc(kFcM6, n6, 1), kb);
+                                mma_f16(tmem, smem_desc(w + 2 * kb * kFcM6 * 16, kFcM6 * 16, 128),
+                                        smem_desc(sh + 2 * kb * kPlane, kPlane, 128),
+                                        idesc_f32acc(kFcM6, n6, FMT), kb);
                         }
                         mma_commit(bar);
                     }
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                             for (int o = 0; o < kFcHidden; ++o) v[o] = leaky(v[o] + b[o]);
 #pragma unroll
                             for (int k = 0; k < 4; ++k)
-                                *reinterpret_cast<uint4 *>(hrow + k * kPlane) = pack8_bf16(v + 8 * k);
+                                *reinterpret_cast<uint4 *>(hrow + k * kPlane) = pack8<FT>(v + 8 * k);
                         }
                         fence_proxy_async_smem();
                         tc_fence_before();
@@ -319,7 +324,12 @@ cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    return precision == PVF_BF16 ? launch_front_tc_t<PVF_BF16>(a, s) : launch_front_tc_t<PVF_FP8_E4M3>(a, s);
+    switch (precision) {
+    case PVF_BF16: return launch_front_tc_t<PVF_BF16>(a, s);
+    case PVF_FP16: return launch_front_tc_t<PVF_FP16>(a, s);
+    case PVF_FP8_E4M3: return launch_front_tc_t<PVF_FP8_E4M3>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace pvf

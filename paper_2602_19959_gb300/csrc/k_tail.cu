@@ -26,7 +26,7 @@ constexpr int kPerThread = 16;    // kThreads * kPerThread >= kBins
 constexpr float kThrLogit = -4.59511985013459f;
 
 // Loads the 16 channels of storage row `row` of event e (layouts as in the front kernel:
-// channel-last float32, or plane-major bf16 / e4m3).
+// channel-last float32, or plane-major 16-bit / e4m3).
 template <class T>
 __device__ __forceinline__ void load_row16(const void *base, int64_t e, int64_t rows_e, int64_t row,
                                            float v[kC0], float scale) {
@@ -42,12 +42,9 @@ __device__ __forceinline__ void load_row16(const void *base, int64_t e, int64_t 
         const unsigned char *cb = reinterpret_cast<const unsigned char *>(base);
         uint4 pk[2] = {*reinterpret_cast<const uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)),
                        *reinterpret_cast<const uint4 *>(cb + planar_off(e, 1, 2, rows_e, row))};
-        const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(pk);
+        const T *b = reinterpret_cast<const T *>(pk);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float2 f = __bfloat1622float2(b[i]);
-            v[2 * i] = f.x; v[2 * i + 1] = f.y;
-        }
+        for (int i = 0; i < 16; ++i) v[i] = from_elem<T>(b[i], 1.0f);
     } else {
         const unsigned char *cb = reinterpret_cast<const unsigned char *>(base);
         uint4 pk = *reinterpret_cast<const uint4 *>(cb + planar_off(e, 0, 1, rows_e, row));
@@ -192,15 +189,11 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     }
     const int per_sm = a.logit_in ? 8 : 2;
     dim3 grid(a.n_events < per_sm * sms ? a.n_events : per_sm * sms), block(kThreads);
-    if (a.logit_in) {
-        return launch_pdl(k_tail<PVF_FP32, false>, grid, block, 0, s, a);
-    } else {
-        switch (precision) {
-        case PVF_FP32: k_tail<PVF_FP32, true><<<grid, block, 0, s>>>(a); break;
-        case PVF_BF16: k_tail<PVF_BF16, true><<<grid, block, 0, s>>>(a); break;
-        default: k_tail<PVF_FP8_E4M3, true><<<grid, block, 0, s>>>(a); break;
-        }
-    }
+    if (a.logit_in) return launch_pdl(k_tail<PVF_FP32, false>, grid, block, 0, s, a);
+    // the final conv runs here in the FP32 form only (the tensor-core forms run it in
+    // dec1's epilogue and pass logits)
+    if (precision != PVF_FP32) return cudaErrorInvalidValue;
+    k_tail<PVF_FP32, true><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -2,7 +2,7 @@
 // every k5 convolution is an implicit GEMM over channels, M = 128 positions of one
 // event, N = C_out, K = 5 taps x C_in, issued as tcgen05.mma with the accumulator in
 // TMEM. The paper projects the gain of tensor cores and reduced precision (§5, Table 2);
-// here they are the BF16 and FP8 (E4M3) forms.
+// here they are the BF16, FP16 and FP8 (E4M3) forms.
 //
 // Kernel families (each a persistent, warp-specialised kernel):
 //   enc2      conv 16->32  @2000, epilogue also writes the 2:1 max-pool
@@ -27,7 +27,7 @@
 // while the tensor core still runs the conv of tile i + 1; the two warpgroups of a role
 // (if four) split its columns. Otherwise two warpgroups split the accumulator columns.
 //
-// Tap pairing (the BF16 dec3_up2 and dec2_up1): a tcgen05.mma costs about the same for
+// Tap pairing (the 16-bit forms' dec3_up2 and dec2_up1): a tcgen05.mma costs about the same for
 // N up to 64 (reading A dominates), so the small-C_out convs stack two taps' weights in N:
 // per K step, taps (0, 1) on the tile as is, taps (2, 3) on the tile two rows down and tap
 // 4 four rows down, accumulating E (taps 0, 2, 4 of row r) and O (taps 1, 3 of row r - 1)
@@ -74,7 +74,7 @@ template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, in
           int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false>
 struct Cfg {
     static constexpr int PREC = PREC_;
-    static constexpr int ES = PREC == PVF_BF16 ? 2 : 1;      // bytes per element
+    static constexpr int ES = is16(PREC) ? 2 : 1;            // bytes per element
     static constexpr int PW = 16 / ES;                       // channels per 16-byte plane row
     static constexpr int CA = CA_, CB = CB_, CIN = CA_ + CB_, COUT = COUT_, L = L_, EPI = EPI_;
     static constexpr int CUP = CUP_;
@@ -127,6 +127,7 @@ struct Cfg {
     static constexpr int X_BYTES = PAIRED ? 2 * 4 * COUT * 4 : 0;
     static constexpr int OFF_BAR = align_up(OFF_X + X_BYTES, 128);
     static constexpr int SMEM = OFF_BAR + 512;
+    // instruction-descriptor operand format: kind::f16 0 = f16, 1 = bf16; kind::f8f6f4 0 = e4m3
     static constexpr uint32_t FMT = PREC == PVF_BF16 ? 1u : 0u;
     static constexpr uint32_t IDESC1 = idesc_f32acc(kTileM, COUT, FMT);
     static constexpr uint32_t IDESC2 = idesc_f32acc(kTileM, N2 > 0 ? N2 : 16, FMT);
@@ -157,7 +158,7 @@ struct TcArgs {
     float *logits;                      // EPI_FINAL: [n_events][L] float32
     const unsigned char *w, *w2;        // packed weights (shared-memory image)
     const float *bias, *bias2;          // float32 biases
-    const float *cs, *cs2;              // fp8: per-column dequantisation scales; bf16: null
+    const float *cs, *cs2;              // fp8: per-column dequantisation scales; 16-bit: null
     const float *final_w;               // EPI_FINAL: W[t][ci] then b (float32)
     float out_inv, mid_inv;             // fp8: 1 / scale of the stored output and of A2
     float *amax;                        // calibration: running max |x| per scale slot, or null
@@ -205,16 +206,13 @@ __device__ __forceinline__ void tile_pos(int t, int &e, int &p0) {
 }
 
 // Quantises 16 values to the form's element type and stores them as 16 / PW plane rows.
-template <int ES>
+template <int PREC>
 __device__ __forceinline__ void put16(unsigned char *p0, size_t plane_stride, const float (&v)[16],
                                       float inv) {
-    if constexpr (ES == 2) {
-        uint4 pk[2];
-        __nv_bfloat162 *b = reinterpret_cast<__nv_bfloat162 *>(pk);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) b[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        *reinterpret_cast<uint4 *>(p0) = pk[0];
-        *reinterpret_cast<uint4 *>(p0 + plane_stride) = pk[1];
+    if constexpr (is16(PREC)) {
+        using T = typename Elem<PREC>::T;
+        *reinterpret_cast<uint4 *>(p0) = pack8<T>(v);
+        *reinterpret_cast<uint4 *>(p0 + plane_stride) = pack8<T>(v + 8);
     } else {
         uint4 pk;
         pack_e4m3<16>(v, inv, reinterpret_cast<unsigned char *>(&pk));
@@ -293,7 +291,7 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
 
 template <class C>
 __device__ __forceinline__ void mma_t(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, bool acc) {
-    if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, idesc, acc);
+    if constexpr (is16(C::PREC)) mma_f16(d, ad, bd, idesc, acc);
     else mma_fp8(d, ad, bd, idesc, acc);
 }
 
@@ -318,8 +316,7 @@ __device__ __forceinline__ void issue_conv(uint32_t d, uint32_t as, uint32_t w_b
         for (int j = 0; j < C::TAPS / 2; ++j) {
             const uint64_t ad = smem_desc(as + 2 * j * 16, 16, 128);
             const uint64_t bd = smem_desc(w_base + 2 * j * C::COUT * 16, C::COUT * 16, 128);
-            if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, j != 0);
-            else mma_fp8(d, ad, bd, C::IDESC1, j != 0);
+            mma_t<C>(d, ad, bd, C::IDESC1, j != 0);
         }
     } else {
 #pragma unroll
@@ -329,8 +326,7 @@ __device__ __forceinline__ void issue_conv(uint32_t d, uint32_t as, uint32_t w_b
                 const uint64_t ad = smem_desc(as + 2 * kb * C::ROWS * 16 + tap * 16, C::ROWS * 16, 128);
                 const uint64_t bd = smem_desc(w_base + (tap * C::PIN + 2 * kb) * C::COUT * 16,
                                               C::COUT * 16, 128);
-                if constexpr (C::PREC == PVF_BF16) mma_bf16(d, ad, bd, C::IDESC1, (tap | kb) != 0);
-                else mma_fp8(d, ad, bd, C::IDESC1, (tap | kb) != 0);
+                mma_t<C>(d, ad, bd, C::IDESC1, (tap | kb) != 0);
             }
     }
 }
@@ -341,8 +337,7 @@ __device__ __forceinline__ void issue_up(uint32_t d2, uint32_t a2, uint32_t w2_b
     for (int kb = 0; kb < C::P2 / 2; ++kb) {
         const uint64_t ad = smem_desc(a2 + 2 * kb * kTileM * 16, kTileM * 16, 128);
         const uint64_t bd = smem_desc(w2_base + 2 * kb * C::N2 * 16, C::N2 * 16, 128);
-        if constexpr (C::PREC == PVF_BF16) mma_bf16(d2, ad, bd, C::IDESC2, kb != 0);
-        else mma_fp8(d2, ad, bd, C::IDESC2, kb != 0);
+        mma_t<C>(d2, ad, bd, C::IDESC2, kb != 0);
     }
 }
 
@@ -497,7 +492,7 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
             const int c0 = c_beg + cc + 16 * h;
             float v[16], bj[16];
             lds16(sbias + c0, bj);
-            if constexpr (C::PREC == PVF_BF16) {
+            if constexpr (is16(C::PREC)) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = leaky(vv[16 * h + j] + bj[j]);
             } else {
@@ -509,18 +504,18 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
             if constexpr (C::EPI == EPI_UP) {
                 if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
                 unsigned char *a2 = smem + C::OFF_A2 + ab * C::A2_BYTES;
-                put16<ES>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
+                put16<C::PREC>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
             } else {
                 if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
                 if (valid)
-                    put16<ES>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
+                    put16<C::PREC>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
                               (size_t)C::ROWS_E * 16, v, a.out_inv);
                 if constexpr (C::EPI == EPI_POOL) {
                     float w[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
                     if (valid && (m & 1) == 0)
-                        put16<ES>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
+                        put16<C::PREC>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
                                   (size_t)ROWS_P * 16, w, a.out_inv);
                 }
             }
@@ -552,7 +547,7 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
             const int r = c0 / C::CUP, co0 = c0 % C::CUP;
             float v[16], bj[16];
             lds16(sbias2 + co0, bj);
-            if constexpr (C::PREC == PVF_BF16) {
+            if constexpr (is16(C::PREC)) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = leaky(vv[16 * h + j] + bj[j]);
             } else {
@@ -563,7 +558,7 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
             }
             if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
             if (valid)
-                put16<ES>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
+                put16<C::PREC>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
                           (size_t)ROWS_O * 16, v, a.out_inv);
         }
     }
@@ -656,7 +651,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             {
                 float bj[16], sc[16];
                 lds16(sbias, bj);
-                if constexpr (C::PREC == PVF_BF16) {
+                if constexpr (is16(C::PREC)) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) sc[j] = 1.0f;
                 } else {
@@ -854,16 +849,16 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
 // ---------------------------------------------------------------- weight packing (host)
 
 // Conv layers (0..5: enc2, enc3, enc4, dec3, dec2, dec1) whose taps are stacked in pairs
-// along N: where it measured faster, the BF16 dec3 (44 -> 28 MMAs per tile) and dec2. The
+// along N: where it measured faster, the 16-bit dec3 (44 -> 28 MMAs per tile) and dec2. The
 // FP8 form already halves the MMAs (K = 32) and measured slower paired; dec1 is bound by
 // its epilogue.
-constexpr bool conv_paired(int li, int prec) { return (li == 3 || li == 4) && prec == PVF_BF16; }
+constexpr bool conv_paired(int li, int prec) { return (li == 3 || li == 4) && is16(prec); }
 
 template <int PREC> struct Net {
     using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56, 2, false, true>;    // 6 CTAs per SM
     using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80, 2, false, true>;    // 4
-    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, PREC == PVF_BF16 ? 2 : 4,
-                        PREC == PVF_BF16 ? 2 : 4, 96, 4>;                                  // 1
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, is16(PREC) ? 2 : 4,
+                        is16(PREC) ? 2 : 4, 96, 4>;                                  // 1
     using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4, conv_paired(3, PREC)>; // 1 CTA/SM
     using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4, conv_paired(4, PREC)>; // 2
     using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4, conv_paired(5, PREC)>; // 4
@@ -871,6 +866,11 @@ template <int PREC> struct Net {
 
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
 const int kBlobIndex[9] = {7, 8, 9, 11, 13, 15, 10, 12, 14};
+
+// Host f16 conversion, saturating like the kernels' stores (round to nearest even, +-65504).
+__half f16_sat(float x) {
+    return __float2half_rn(x > 65504.0f ? 65504.0f : (x < -65504.0f ? -65504.0f : x));
+}
 
 struct Packer {
     int prec, es, pw;
@@ -882,8 +882,11 @@ struct Packer {
         return off;
     }
     void enc(float x, unsigned char *dst) const {
-        if (es == 2) {
+        if (prec == PVF_BF16) {
             __nv_bfloat16 h = __float2bfloat16_rn(x);
+            std::memcpy(dst, &h, 2);
+        } else if (prec == PVF_FP16) {
+            __half h = f16_sat(x);
             std::memcpy(dst, &h, 2);
         } else {
             __nv_fp8_e4m3 q(x);
@@ -902,13 +905,13 @@ size_t tc_weight_bytes(int precision) {
     return 512 * 1024;   // packed weights (< 300 KB) + biases + fp8 column scales
 }
 
-bool tc_supported(int precision) { return precision == PVF_BF16 || precision == PVF_FP8_E4M3; }
+bool tc_supported(int precision) { return is16(precision) || precision == PVF_FP8_E4M3; }
 
 // Conv layer W[co][ci][t] -> image [tap][plane][co][PW elements] (6th tap zero when paired).
 // ConvT W[ci][co][r] -> image [plane of ci][n = r * CUP + co][PW elements].
 bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const float *act_scale,
                      std::vector<unsigned char> &out, TcNet *net, unsigned char *dev_base) {
-    Packer pk{precision, precision == PVF_BF16 ? 2 : 1, precision == PVF_BF16 ? 8 : 16, {}};
+    Packer pk{precision, is16(precision) ? 2 : 1, is16(precision) ? 8 : 16, {}};
     net->precision = precision;
     size_t off_w[9], off_b[9], off_s[9];
     for (int li = 0; li < 9; ++li) {
@@ -982,7 +985,7 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
         }
         off_s[li] = pk.put_raw(cs.data(), cs.size() * sizeof(float));
     }
-    // FC images (bf16 in both forms): element (out o, in i) of layer l at
+    // FC images (f16 in the FP16 form, bf16 in the others): element (out o, in i) of layer l at
     // ((i / 8) * R + row) * 16 + (i % 8) * 2 of the layer's image, R rows per plane;
     // row = o for layers 1-5 (R = 32), fc6_row(o) for layer 6 (R = 128)
     std::vector<unsigned char> fcimg(kFcImgBytes, 0);
@@ -992,7 +995,15 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
         const int rows = l < 5 ? kFcHidden : kFcM6;
         for (int o = 0; o < nout; ++o)
             for (int i = 0; i < nin; ++i) {
-                __nv_bfloat16 hv = __float2bfloat16_rn(Lw.w[(size_t)o * nin + i]);
+                const float wv = Lw.w[(size_t)o * nin + i];
+                uint16_t hv;
+                if (precision == PVF_FP16) {
+                    const __half h = f16_sat(wv);
+                    std::memcpy(&hv, &h, 2);
+                } else {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(wv);
+                    std::memcpy(&hv, &h, 2);
+                }
                 const int row = l < 5 ? o : fc6_row(o);
                 std::memcpy(&fcimg[fc_img_off(l) + ((i / 8) * rows + row) * 16 + (i % 8) * 2], &hv, 2);
             }
@@ -1015,8 +1026,8 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStre
                           const ProfHook *prof) {
     using N = Net<PREC>;
     const float *sc = n.act_scale;
-    auto inv = [&](int i) { return PREC == PVF_BF16 ? 1.0f : 1.0f / sc[i]; };
-    auto cs = [&](int li) { return PREC == PVF_BF16 ? nullptr : n.wscale[li]; };
+    auto inv = [&](int i) { return is16(PREC) ? 1.0f : 1.0f / sc[i]; };
+    auto cs = [&](int li) { return is16(PREC) ? nullptr : n.wscale[li]; };
     auto W = [&](int li) { return static_cast<const unsigned char *>(n.w[li]); };
     auto U = [](void *p) { return static_cast<unsigned char *>(p); };
     cudaError_t err;
@@ -1060,8 +1071,12 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStre
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, cudaStream_t s,
                            const ProfHook *prof) {
     if (n <= 0) return cudaSuccess;
-    if (net.precision == PVF_BF16) return run_tc<PVF_BF16>(net, b, n, s, prof);
-    return run_tc<PVF_FP8_E4M3>(net, b, n, s, prof);
+    switch (net.precision) {
+    case PVF_BF16: return run_tc<PVF_BF16>(net, b, n, s, prof);
+    case PVF_FP16: return run_tc<PVF_FP16>(net, b, n, s, prof);
+    case PVF_FP8_E4M3: return run_tc<PVF_FP8_E4M3>(net, b, n, s, prof);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace pvf

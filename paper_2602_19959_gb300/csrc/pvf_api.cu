@@ -94,7 +94,7 @@ pvf_status parse_blob(const void *blob, size_t bytes, std::vector<HostLayer> &la
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 size_t elem_bytes(int precision) {
-    return precision == PVF_FP32 ? 4 : precision == PVF_BF16 ? 2 : 1;
+    return precision == PVF_FP32 ? 4 : is16(precision) ? 2 : 1;
 }
 
 // Float32 weight block: FC, enc1, final, conv and ConvT layers in CUDA-core layouts.
@@ -185,7 +185,7 @@ struct Plan {
 
 pvf_status check_config(const pvf_config *c) {
     if (!c) return PVF_ERR_INVALID_ARG;
-    if (c->precision < PVF_FP32 || c->precision > PVF_FP8_E4M3) return PVF_ERR_INVALID_ARG;
+    if (c->precision < PVF_FP32 || c->precision > PVF_FP16) return PVF_ERR_INVALID_ARG;
     if (c->max_events < 1 || c->max_events > (1 << 24)) return PVF_ERR_INVALID_ARG;
     if (c->max_tracks_per_event < 1 || c->max_tracks_per_event > 8192) return PVF_ERR_INVALID_ARG;
     if (c->max_pv_per_event < 1 || c->max_pv_per_event > 1024) return PVF_ERR_INVALID_ARG;

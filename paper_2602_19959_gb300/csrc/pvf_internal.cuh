@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
 
@@ -87,11 +88,35 @@ template <int PREC> struct Elem;
 template <> struct Elem<PVF_FP32> { using T = float; };
 template <> struct Elem<PVF_BF16> { using T = __nv_bfloat16; };
 template <> struct Elem<PVF_FP8_E4M3> { using T = __nv_fp8_e4m3; };
+template <> struct Elem<PVF_FP16> { using T = __half; };
+
+// The 16-bit tensor-core forms (tcgen05 kind::f16 with bf16 or f16 operands).
+__host__ __device__ constexpr bool is16(int prec) { return prec == PVF_BF16 || prec == PVF_FP16; }
+
+// Two floats rounded to nearest even as one 32-bit pair of T (lo in the low half). The
+// f16 conversion saturates to the largest finite value, +-65504, and keeps NaN.
+template <class T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&b);
+}
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+// 8 floats as one 16-byte row of T.
+template <class T> __device__ __forceinline__ uint4 pack8(const float *v) {
+    return make_uint4(pack2<T>(v[0], v[1]), pack2<T>(v[2], v[3]), pack2<T>(v[4], v[5]), pack2<T>(v[6], v[7]));
+}
 
 template <class T> __device__ __forceinline__ T to_elem(float v, float inv_scale);
 template <> __device__ __forceinline__ float to_elem<float>(float v, float) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_elem<__nv_bfloat16>(float v, float) {
     return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half to_elem<__half>(float v, float) {
+    return __ushort_as_half((unsigned short)(pack2<__half>(v, 0.0f) & 0xFFFFu));
 }
 template <> __device__ __forceinline__ __nv_fp8_e4m3 to_elem<__nv_fp8_e4m3>(float v, float inv) {
     return __nv_fp8_e4m3(v * inv);   // saturating round-to-nearest-even
@@ -100,6 +125,9 @@ template <class T> __device__ __forceinline__ float from_elem(T v, float scale);
 template <> __device__ __forceinline__ float from_elem<float>(float v, float) { return v; }
 template <> __device__ __forceinline__ float from_elem<__nv_bfloat16>(__nv_bfloat16 v, float) {
     return __bfloat162float(v);
+}
+template <> __device__ __forceinline__ float from_elem<__half>(__half v, float) {
+    return __half2float(v);
 }
 template <> __device__ __forceinline__ float from_elem<__nv_fp8_e4m3>(__nv_fp8_e4m3 v, float s) {
     return float(v) * s;

@@ -137,7 +137,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor of tcgen05.mma: D f32, A/B K-major, dense.
-//   kind::f16     a/b format 1 = bf16
+//   kind::f16     a/b format 0 = f16, 1 = bf16 (A and B always of the same type)
 //   kind::f8f6f4  a/b format 0 = e4m3
 __host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N, uint32_t ab_format) {
     return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -146,7 +146,8 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N, uint32_t ab_fo
 
 // ------------------------------------------------------------------ MMA
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+// kind::f16: bf16 or f16 operands, as the instruction descriptor says
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"

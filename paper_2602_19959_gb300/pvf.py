@@ -29,7 +29,7 @@ PVF_ERR_UNSUPPORTED = 6
 PVF_WARN_EVENTS_SKIPPED = 16
 PVF_WARN_TRUNCATED = 17
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
 N_BINS = 4000
 N_ACT_SCALES = 16
 

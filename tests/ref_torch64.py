@@ -132,6 +132,12 @@ def q_bf16(t):
     return t.to(torch.bfloat16).to(torch.float64)
 
 
+def q_fp16(t):
+    """Round to nearest even in IEEE half precision, saturating to +-65504 as the FP16
+    form's stores do (NaN stays NaN)."""
+    return t.clamp(-65504.0, 65504.0).to(torch.float16).to(torch.float64)
+
+
 def _e4m3(t):
     """Saturating round-to-nearest-even to float8 e4m3 and back to float64."""
     return t.clamp(-448.0, 448.0).to(torch.float8_e4m3fn).to(torch.float64)

@@ -147,7 +147,7 @@ def test_bf16_full_size_sampled(PVFinder, weights):
     assert np.all(r["count"] >= 0)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
 def test_chunked_and_repeated_launches_equal_one_launch(PVFinder, weights, precision, request):
     """One call split into UNet chunks of 16 events, and the same handle reused for
     different batch sizes, give bit for bit the results of a single launch: every kernel
@@ -243,3 +243,86 @@ def test_fp8_deterministic_and_batch_invariant(fp8, ev16):
         np.testing.assert_array_equal(r1[k], r2[k])
     rs = run_full(fp8, ev16.subset(9, 12))
     np.testing.assert_array_equal(rs["logit"], r1["logit"][9:12])
+
+
+# ---------------------------------------------------------------- FP16 (the §5 proposal)
+# Same kernels as BF16 with f16 operands (10 stored mantissa bits instead of 7): every
+# rounding error is about 8x smaller, and the bounds below are set accordingly (the BF16
+# form measures a histogram error of ~4e-3 and a logit error of ~1.3e-2 of the maximum).
+
+@pytest.fixture(scope="module")
+def fp16(PVFinder, weights):
+    return PVFinder(weights, precision="fp16", max_events=64, max_pv_per_event=MAX_PV)
+
+
+def test_fp16_unet_wiring_matches_quantised_emulation(fp16, weights, ref16):
+    h32 = ref16["hist"].astype(np.float32)
+    logit = torch.zeros((16, 4000), dtype=torch.float32, device="cuda")
+    _poison_shared_memory()
+    fp16.stage_unet(torch.from_numpy(h32).cuda(), logit)
+    torch.cuda.synchronize()
+    f = logit.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(f))
+    for e in range(4):
+        want = ref.unet_quantized(weights, h32[e].astype(np.float64), ref.q_fp16)
+        scale = np.max(np.abs(want))
+        d = np.abs(f[e] - want) / scale
+        print(f"fp16 event {e}: median {np.median(d):.2e} p99 {np.quantile(d, 0.99):.2e} max {d.max():.2e}")
+        assert np.median(d) <= 1e-4
+        assert np.quantile(d, 0.99) <= 5e-4
+        assert d.max() <= 5e-3
+
+
+def test_fp16_fc_wiring_matches_quantised_emulation(fp16, weights, ev16):
+    r = run_full(fp16, ev16)
+    for e in range(6):
+        feats = ev16.features[:, ev16.offsets[e]:ev16.offsets[e + 1]]
+        want = ref.histogram_quantized(weights, feats, ref.q_fp16)
+        scale = np.max(np.abs(want))
+        d = np.abs(r["hist"][e] - want) / scale
+        print(f"fp16 fc event {e}: median {np.median(d):.2e} max {d.max():.2e}")
+        assert np.median(d) <= 1e-5
+        assert d.max() <= 5e-4
+        np.testing.assert_array_equal(r["hist"][e] == 0, want == 0)
+
+
+def test_fp16_against_oracle(fp16, ev16, ref16):
+    r = run_full(fp16, ev16)
+    hist = max(np.max(np.abs(r["hist"][e] - ref16["hist"][e])) / np.max(np.abs(ref16["hist"][e]))
+               for e in range(16))
+    rel = max(np.max(np.abs(r["logit"][e] - ref16["logit"][e])) / np.max(np.abs(ref16["logit"][e]))
+              for e in range(16))
+    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    print("fp16 histogram err / max:", hist, "per-bin logit err / max:", rel, "agreement:", a)
+    assert hist <= 4e-3
+    assert rel <= 1e-2
+    assert a["max_dz"] <= 0.1
+    assert a["exempt"] >= 0.999
+
+
+def test_fp16_deterministic_and_batch_invariant(fp16, ev16):
+    r1 = run_full(fp16, ev16)
+    r2 = run_full(fp16, ev16)
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(r1[k], r2[k])
+    rs = run_full(fp16, ev16.subset(5, 11))
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(rs[k], r1[k][5:11])
+    assert fp16.device_status() == 0
+
+
+def test_fp16_full_size_sampled(PVFinder, weights):
+    """The 1000-event workload in the launch configuration the bench times, checked against
+    the oracle on a sample of events."""
+    b = synth.generate_standard(1000, 1)
+    pv = PVFinder(weights, precision="fp16", max_events=1000, max_pv_per_event=MAX_PV)
+    r = run_full(pv, b)
+    assert pv.device_status() == 0
+    sample = [0, 500, 999]
+    sb = synth.concat_batches([b.subset(e, e + 1) for e in sample])
+    rr = oracle.infer(weights, sb.features, sb.offsets, max_pv=MAX_PV, want_logit=True,
+                      nthreads=NTHREADS)
+    for i, e in enumerate(sample):
+        assert np.max(np.abs(r["logit"][e] - rr["logit"][i])) <= 1e-2 * np.max(np.abs(rr["logit"][i]))
+    assert np.all(r["count"] >= 0)

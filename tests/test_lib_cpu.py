@@ -50,7 +50,9 @@ def test_pool_bytes_required_and_config_validation(lib):
     fp32 = P.pool_bytes_required(precision="fp32", max_events=1000)
     bf16 = P.pool_bytes_required(precision="bf16", max_events=1000)
     fp8 = P.pool_bytes_required(precision="fp8", max_events=1000)
+    fp16 = P.pool_bytes_required(precision="fp16", max_events=1000)
     assert fp32 > bf16 > fp8 > 0
+    assert fp16 == bf16                              # same 16-bit activation layout
     assert fp32 < 2 * 1024 ** 3                      # the 1000-event plan fits a 2 GB pool
     chunked = P.pool_bytes_required(precision="fp32", max_events=1000, chunk_events=100)
     assert chunked < fp32 / 5

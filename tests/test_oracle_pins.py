@@ -378,3 +378,17 @@ def test_infer_bypasses_invalid_events_and_threads_agree():
     r = oracle.infer(w, ev.features, ev.offsets, max_pv=8, max_tracks_per_event=100)
     big = ev.tracks_per_event() > 100
     assert np.all(r["pv_count"][big] == -1) and np.all(r["pv_count"][~big] >= 0)
+
+
+def test_fp16_rounding_emulation_against_binary16():
+    """The FP16 form's quantisation emulation (a wiring check for the f16 kernels) against
+    values IEEE 754 binary16 fixes: 10 stored mantissa bits with ties to even, saturation
+    at the largest finite value 65504 (as the form's stores), NaN kept, subnormals down to
+    2^-24."""
+    x = torch.tensor([1 + 2 ** -11, 1 + 3 * 2 ** -11, 1 + 2 ** -10, 65504.0, 65519.0, 1e6, -1e6,
+                      2 ** -24, 2 ** -26, 3 * 2 ** -25, 0.1], dtype=torch.float64)
+    want = [1.0, 1 + 2 ** -9, 1 + 2 ** -10, 65504.0, 65504.0, 65504.0, -65504.0,
+            2 ** -24, 0.0, 2 * 2 ** -24, 1638 * 2 ** -14]
+    got = ref.q_fp16(x).tolist()
+    assert got == want
+    assert math.isnan(ref.q_fp16(torch.tensor([float("nan")], dtype=torch.float64)).item())
