@@ -82,8 +82,10 @@ def _load():
         lib.oracle_slice_index.restype = I
         lib.oracle_fc_track.argtypes = [ctypes.POINTER(OracleWeights), P, P]
         lib.oracle_fc_track.restype = None
+        lib.oracle_second_slice.argtypes = [ctypes.c_float, I, ctypes.c_float]
+        lib.oracle_second_slice.restype = I
         lib.oracle_event_histogram.argtypes = [P, ctypes.c_int64, ctypes.c_int64,
-                                               ctypes.POINTER(OracleWeights), P]
+                                               ctypes.POINTER(OracleWeights), ctypes.c_float, P]
         lib.oracle_event_histogram.restype = I
         lib.oracle_conv1d_k5.argtypes = [P, I, I, P, P, I, P]
         lib.oracle_conv1d_k5.restype = None
@@ -97,7 +99,7 @@ def _load():
                                      ctypes.c_double, I, P, P]
         lib.oracle_peaks.restype = I
         lib.oracle_infer.argtypes = [P, P, ctypes.c_int64, I, I, ctypes.POINTER(OracleWeights),
-                                     P, P, P, P, P, P, I, ctypes.c_double, I]
+                                     P, P, P, P, P, P, I, ctypes.c_double, ctypes.c_float, I]
         lib.oracle_infer.restype = I
         _lib = lib
         return lib
@@ -163,14 +165,20 @@ def _feature_ptrs(features: np.ndarray):
     return features, ptrs
 
 
-def event_histogram(weights, features: np.ndarray):
-    """Histogram [4000] of one event given float32 features [9, n]; returns (hist, dropped)."""
+def second_slice(z, s, edge_mm) -> int:
+    """Second slice of a boundary track of slice s at float32 z (-1: none)."""
+    return _load().oracle_second_slice(ctypes.c_float(float(z)), int(s), ctypes.c_float(float(edge_mm)))
+
+
+def event_histogram(weights, features: np.ndarray, edge_mm: float = 0.0):
+    """Histogram [4000] of one event given float32 features [9, n]; returns (hist, dropped).
+    edge_mm > 0 also adds boundary tracks to their second slice."""
     lib = _load()
     w = _as_weights(weights)
     features, ptrs = _feature_ptrs(features)
     hist = np.zeros(NBINS, dtype=np.float64)
     dropped = lib.oracle_event_histogram(ptrs, 0, features.shape[1], ctypes.byref(w.struct),
-                                         _ptr(hist))
+                                         ctypes.c_float(edge_mm), _ptr(hist))
     return hist, dropped
 
 
@@ -258,10 +266,10 @@ def peaks(logit, prob=None, thr: float = THRESHOLD, hw: int = 5, hc: int = 3,
 def infer(weights, features: np.ndarray, offsets: np.ndarray, max_pv: int = 64,
           max_tracks_per_event: int = 1 << 30, want_hist: bool = False,
           want_logit: bool = False, want_prob: bool = False, nthreads: int = 1,
-          thr: float = THRESHOLD):
+          thr: float = THRESHOLD, edge_mm: float = 0.0):
     """Whole-pipeline oracle over a batch. Returns a dict with pv_z [n, max_pv],
     pv_count [n] (-1 = bypassed event), n_dropped [n], and optionally hist / logit /
-    prob ([n, 4000] each)."""
+    prob ([n, 4000] each). edge_mm: boundary-track width (0 = none)."""
     lib = _load()
     w = _as_weights(weights)
     features, ptrs = _feature_ptrs(features)
@@ -275,7 +283,8 @@ def infer(weights, features: np.ndarray, offsets: np.ndarray, max_pv: int = 64,
     prob = np.zeros((n, NBINS), dtype=np.float64) if want_prob else None
     rc = lib.oracle_infer(ptrs, _ptr(offsets), features.shape[1], n, max_tracks_per_event,
                           ctypes.byref(w.struct), _ptr(hist), _ptr(logit), _ptr(prob), _ptr(pv_z),
-                          _ptr(pv_count), _ptr(n_drop), max_pv, thr, nthreads)
+                          _ptr(pv_count), _ptr(n_drop), max_pv, thr, ctypes.c_float(edge_mm),
+                          nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_infer failed ({rc})")
     out = {"pv_z": pv_z, "pv_count": pv_count, "n_dropped": n_drop}

@@ -104,13 +104,33 @@ void oracle_fc_track(const oracle_weights *w, const double *x, double *out)
     }
 }
 
+/* The second interval of a boundary track (§3: tracks on interval boundaries belong to
+ * two intervals; the paper gives no width, so it is a parameter). A valid track of
+ * slice s whose slice-relative position zr = z - (-100 + 10 s), taken in float32
+ * round-to-nearest like the slice index, satisfies zr < edge belongs also to slice
+ * s - 1 (if s > 0); one with zr >= 10 - edge (float32) also to slice s + 1 (if s < 39).
+ * edge = 0 gives no second interval; 0 <= edge < 5, so a track has at most two.
+ * Returns the second slice, or -1. */
+int oracle_second_slice(float z, int s, float edge)
+{
+    if (s < 0 || !(edge > 0.0f)) return -1;
+    volatile float base = -100.0f + 10.0f * (float)s;
+    volatile float zr = z - base;
+    volatile float hi = 10.0f - edge;
+    if (s > 0 && zr < edge) return s - 1;
+    if (s < OR_NSLICES - 1 && zr >= hi) return s + 1;
+    return -1;
+}
+
 /* Histogram of one event (§2: "combining each track's contribution"): every valid track
- * adds its fc_out outputs to the bins of its own slice; tracks are summed in input
- * order. A track is dropped when any feature is not finite or its slice is outside
- * [0, 40). Feature 2 fed to the net is z - (-100 + 10 s), the position inside the
- * slice in mm. Returns the number of dropped tracks. */
+ * adds its fc_out outputs to the bins of its own slice and, if it is a boundary track
+ * (oracle_second_slice), the outputs of a second evaluation to the bins of its second
+ * slice; tracks are summed in input order. A track is dropped when any feature is not
+ * finite or its slice is outside [0, 40). Feature 2 fed to the net is z - (-100 + 10 s),
+ * the position relative to the start of the slice s being filled, in mm (in a second
+ * slice it lies just outside [0, 10)). Returns the number of dropped tracks. */
 int oracle_event_histogram(const float *const feats[9], int64_t begin, int64_t end,
-                           const oracle_weights *w, double *hist /* [4000] */)
+                           const oracle_weights *w, float edge, double *hist /* [4000] */)
 {
     double x[9], out[OR_MAX_OUT];
     int dropped = 0;
@@ -123,9 +143,16 @@ int oracle_event_histogram(const float *const feats[9], int64_t begin, int64_t e
         }
         int s = finite ? oracle_slice_index(feats[2][t]) : -1;
         if (s < 0) { ++dropped; continue; }
-        x[2] = x[2] - (OR_Z_LO + 10.0 * (double)s);
+        const double z = x[2];
+        x[2] = z - (OR_Z_LO + 10.0 * (double)s);
         oracle_fc_track(w, x, out);
         for (int j = 0; j < w->fc_out; ++j) hist[s * OR_SLICE_BINS + j] += out[j];
+        const int s2 = oracle_second_slice(feats[2][t], s, edge);
+        if (s2 >= 0) {
+            x[2] = z - (OR_Z_LO + 10.0 * (double)s2);
+            oracle_fc_track(w, x, out);
+            for (int j = 0; j < w->fc_out; ++j) hist[s2 * OR_SLICE_BINS + j] += out[j];
+        }
     }
     return dropped;
 }
@@ -316,6 +343,7 @@ typedef struct {
     int32_t *n_dropped;            /* nullable, [n_events] */
     int max_pv;
     double thr;
+    float edge;
     int tid, nthreads;
     int rc;
 } infer_job;
@@ -338,7 +366,7 @@ static void *infer_worker(void *arg)
             j->pv_count[e] = -1;
             continue;
         }
-        int drop = oracle_event_histogram(j->feats, a, b, j->w, hist);
+        int drop = oracle_event_histogram(j->feats, a, b, j->w, j->edge, hist);
         if (j->n_dropped) j->n_dropped[e] = drop;
         if (oracle_unet(j->w, hist, OR_NBINS, logit, prob, NULL) != 0) { j->rc = -2; break; }
         j->pv_count[e] = oracle_peaks(logit, prob, OR_NBINS, thr_logit, 5, 3, OR_Z_LO, OR_BIN_W,
@@ -352,15 +380,17 @@ static void *infer_worker(void *arg)
 }
 
 /* Full inference over a batch of events, statically round-robin over nthreads threads
- * (nthreads <= 1 runs on the calling thread). Returns 0 on success. */
+ * (nthreads <= 1 runs on the calling thread); edge is the boundary-track width in mm
+ * (oracle_second_slice, 0 = none). Returns 0 on success. */
 int oracle_infer(const float *const feats[9], const int32_t *offsets, int64_t n_tracks_total,
                  int n_events, int max_tracks_per_event, const oracle_weights *w,
                  double *hist_out, double *logit_out, double *prob_out, double *pv_z,
                  int32_t *pv_count,
-                 int32_t *n_dropped, int max_pv, double thr, int nthreads)
+                 int32_t *n_dropped, int max_pv, double thr, float edge, int nthreads)
 {
     if (n_events < 0 || max_pv < 0 || !w || (n_events > 0 && (!offsets || !pv_z || !pv_count)))
         return -1;
+    if (!(edge >= 0.0f && edge < 5.0f)) return -1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > n_events) nthreads = n_events > 0 ? n_events : 1;
     infer_job *jobs = calloc((size_t)nthreads, sizeof(infer_job));
@@ -371,7 +401,7 @@ int oracle_infer(const float *const feats[9], const int32_t *offsets, int64_t n_
         j->feats = feats; j->offsets = offsets; j->n_tracks_total = n_tracks_total;
         j->n_events = n_events; j->max_tracks_per_event = max_tracks_per_event; j->w = w;
         j->hist_out = hist_out; j->logit_out = logit_out; j->prob_out = prob_out; j->pv_z = pv_z; j->pv_count = pv_count;
-        j->n_dropped = n_dropped; j->max_pv = max_pv; j->thr = thr; j->tid = t;
+        j->n_dropped = n_dropped; j->max_pv = max_pv; j->thr = thr; j->edge = edge; j->tid = t;
         j->nthreads = nthreads; j->rc = 0;
     }
     int rc = 0;

@@ -155,6 +155,94 @@ def test_histogram_slice_relative_z_feature():
     np.testing.assert_allclose(h0[:100], oracle.fc_track(w, x), rtol=0, atol=0)
 
 
+# ----------------------------------------------------------------- boundary tracks (§3)
+# A track whose slice-relative z (float32) is below the width w also belongs to the slice
+# below; one at or above 10 - w also to the slice above; never outside slices 0..39.
+
+def _f32_below(x):
+    return float(np.nextafter(np.float32(x), np.float32(-1e9)))
+
+
+def test_second_slice_rule_hand_cases():
+    w = 0.5
+    cases = [(-89.5, 1, -1),                 # zr = 0.5: not below w
+             (_f32_below(-89.5), 1, 0),      # zr one ulp below 0.5
+             (-80.5, 1, 2),                  # zr = 9.5 = 10 - w: belongs above too
+             (_f32_below(-80.5), 1, -1),     # just below 10 - w
+             (-85.0, 1, -1),                 # middle of the slice
+             (-99.8, 0, -1),                 # no slice below 0
+             (299.7, 39, -1),                # no slice above 39
+             (290.2, 39, 38),
+             (-90.0, 1, 0)]                  # on the edge itself: zr = 0
+    for z, s, want in cases:
+        assert oracle.slice_index(z)[0] == s, z
+        assert oracle.second_slice(z, s, w) == want, (z, s)
+        assert oracle.second_slice(z, s, 0.0) == -1
+
+
+def test_boundary_histogram_closed_form_constant_fc():
+    """All FC weights zero: every evaluation gives softplus(b6) per bin, so each slice holds
+    (number of tracks counted in it) x softplus(b6); counts derived by hand, w = 1 mm."""
+    shapes = synth.layer_shapes()
+    wts = {k: (np.zeros(s[0], np.float32), np.zeros(s[1], np.float32)) for k, s in shapes.items()}
+    b6 = np.linspace(-3, 3, 100).astype(np.float32)
+    wts["fc6"] = (wts["fc6"][0], b6)
+    z = [-95.0,      # slice 0 only
+         -90.5,      # slice 0, zr 9.5 >= 9: and slice 1
+         -89.7,      # slice 1, zr 0.3 < 1: and slice 0
+         -85.0,      # slice 1 only
+         -99.5,      # slice 0, zr 0.5 < 1, but no slice below 0
+         299.5,      # slice 39, zr 9.5, but no slice above 39
+         150.2]      # slice 25, zr 0.2: and slice 24
+    f = np.zeros((9, len(z)), np.float32)
+    f[2] = z
+    hist, dropped = oracle.event_histogram(wts, f, edge_mm=1.0)
+    counts = np.zeros(40)
+    counts[0], counts[1], counts[39], counts[25], counts[24] = 4, 3, 1, 1, 1
+    want = (counts[:, None] * np.logaddexp(0.0, b6.astype(np.float64))[None, :]).reshape(-1)
+    np.testing.assert_allclose(hist, want, rtol=1e-13, atol=0)
+    assert dropped == 0
+    plain, _ = oracle.event_histogram(wts, f, edge_mm=0.0)
+    counts0 = np.zeros(40)
+    counts0[0], counts0[1], counts0[39], counts0[25] = 3, 2, 1, 1
+    np.testing.assert_allclose(plain, (counts0[:, None] * np.logaddexp(0.0, b6.astype(np.float64))).reshape(-1),
+                               rtol=1e-13, atol=0)
+
+
+def test_boundary_second_evaluation_uses_the_second_slice_offset():
+    """With random weights, a boundary track adds to its second slice the FC output for
+    the position relative to that slice (PyTorch float64 statement of the net), and its
+    own slice's bins are those of the plain histogram."""
+    wts = rand_weights(8, 0.2)
+    rng = np.random.default_rng(9)
+    for z, s, s2 in [(-79.7, 2, 1), (-60.4, 3, 4), (-89.9, 1, 0), (120.3, 22, 21)]:
+        f = rng.normal(0, 0.1, (9, 1)).astype(np.float32)
+        f[2, 0] = z
+        hist, _ = oracle.event_histogram(wts, f, edge_mm=0.5)
+        plain, _ = oracle.event_histogram(wts, f)
+        x = f[:, 0].astype(np.float64)
+        x[2] = float(np.float32(z)) - (-100.0 + 10.0 * s2)
+        want2 = ref.fc_net(wts, torch.as_tensor(x).reshape(1, 9)).numpy()[0]
+        np.testing.assert_allclose(hist[100 * s2:100 * s2 + 100], want2, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(hist[100 * s:100 * s + 100], plain[100 * s:100 * s + 100])
+        others = np.ones(40, bool)
+        others[[s, s2]] = False
+        assert np.all(hist.reshape(40, 100)[others] == 0)
+        assert (x[2] < 0) == (s2 > s) and abs(x[2] - 5) > 5   # just outside [0, 10)
+
+
+def test_boundary_infer_reduces_to_plain_at_zero_width():
+    wts = rand_weights(2, 0.1)
+    ev = synth.generate_standard(3, 4)
+    a = oracle.infer(wts, ev.features, ev.offsets, want_hist=True)
+    b = oracle.infer(wts, ev.features, ev.offsets, want_hist=True, edge_mm=0.0)
+    c = oracle.infer(wts, ev.features, ev.offsets, want_hist=True, edge_mm=0.5)
+    np.testing.assert_array_equal(a["hist"], b["hist"])
+    assert np.all(c["hist"].sum(axis=1) > a["hist"].sum(axis=1))   # softplus > 0: more terms
+    with pytest.raises(RuntimeError):
+        oracle.infer(wts, ev.features, ev.offsets, edge_mm=5.0)
+
+
 def test_histogram_drops_invalid_tracks():
     w = rand_weights(6, 0.1)
     f = np.zeros((9, 5), np.float32)
