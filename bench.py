@@ -84,14 +84,16 @@ def kernel_table(form):
     return t
 
 
-def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_launch, peaks):
+def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_launch, peaks,
+                fc_evals=None):
     """Roofline of one kernel family from its algorithmic FLOPs and bytes per launch:
-    the bound is whichever of compute and memory needs more time at its peak."""
+    the bound is whichever of compute and memory needs more time at its peak. fc_evals:
+    FC evaluations per launch (tracks plus second slices of boundary tracks)."""
     mac, per_track_b, bytes_ev, unit = kernel_table(form)[name]
     flops = 2.0 * mac * events_per_launch
     nbytes = bytes_ev * events_per_launch + per_track_b * tracks_per_launch
     if name == "front":
-        flops += 2.0 * FC_MAC_PER_TRACK * tracks_per_launch
+        flops += 2.0 * FC_MAC_PER_TRACK * (tracks_per_launch if fc_evals is None else fc_evals)
     sec = tot_ms / max(launches, 1) / 1000.0
     alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6     # FLOP/s, fp32 lanes
     tc_peak = peaks["bf16_tflops"] * 1e12 * (2.0 if form == "fp8" else 1.0)
@@ -266,13 +268,32 @@ def run_reference(args, weights, batch, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def fc_evaluations(batch, edge):
+    """FC evaluations of a batch: one per track, plus one per boundary track (a track
+    whose slice-relative z is below `edge` mm, above slice 0, or at least 10 - edge,
+    below slice 39), decided in float32 as the kernels do."""
+    n = int(np.sum(np.diff(batch.offsets)))
+    if edge <= 0:
+        return n
+    z = batch.features[2].astype(np.float32)
+    with np.errstate(invalid="ignore"):
+        s = np.floor((z + np.float32(100.0)) / np.float32(10.0))
+    ok = np.isfinite(s) & (s >= 0) & (s < 40)
+    s = np.where(ok, s, 0).astype(np.float32)
+    zr = z - (np.float32(-100.0) + np.float32(10.0) * s)
+    lo = ok & (s > 0) & (zr < np.float32(edge))
+    hi = ok & (s < 39) & (zr >= np.float32(10.0) - np.float32(edge))
+    return n + int(lo.sum() + hi.sum())
+
+
 def workload_config(args, dtype):
     return {"workload": f"PVFinder inference, {args.events} synthetic events per GPU "
                         f"(~155 tracks/event, Poisson 5.6 PVs), 4000-bin histogram, "
                         f"16/32/64/128 UNet, {dtype}",
             "events_per_gpu": args.events, "bins": 4000, "max_pv_per_event": args.max_pv,
             "l2": f"flushed between steps ({args.flush_mb} MB write)" if args.flush_mb >= 256
-                  else "not flushed (profiling run)", "form": args.precision}
+                  else "not flushed (profiling run)", "form": args.precision,
+            "boundary_mm": args.boundary_mm}
 
 
 def make_finder(args, weights, precision, events, **kw):
@@ -288,7 +309,8 @@ def make_finder(args, weights, precision, events, **kw):
         scales = pcal.calibrate(torch.from_numpy(cal.features).cuda(),
                                 torch.from_numpy(cal.offsets).cuda())
         pcal.close()
-    return PVFinder(weights, precision=precision, max_events=events, fp8_act_scales=scales, **kw)
+    return PVFinder(weights, precision=precision, max_events=events, fp8_act_scales=scales,
+                    boundary_mm=args.boundary_mm, **kw)
 
 
 def time_steps(pv, step, flush, steps, world, profile):
@@ -441,14 +463,15 @@ def run_step(args, weights, batch, rank, world, local):
     # dominant kernel and its roofline (algorithmic work / live launch duration)
     peaks, peak_src = load_peaks()
     valid_tracks = int(np.sum(np.diff(batch.offsets)))
+    fc_evals = fc_evaluations(batch, args.boundary_mm)
     kernels = {}
     total_ms = max(sum(v[1] for v in prof.values()), 1e-9)
     for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks)
+        rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks, fc_evals)
         kernels[k] = {"launches": n, "avg_us": 1000.0 * ms / max(n, 1), "share": ms / total_ms,
                       "bound": rf["bound"], "frac": rf["frac"]}
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks)
+    roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks, fc_evals)
     traffic = NCU_TRAFFIC.get((args.precision, name, args.events))
     roof.update({"kernel": name, "traffic": traffic,
                  "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
@@ -551,6 +574,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--max-pv", type=int, default=672)
+    ap.add_argument("--boundary-mm", type=float, default=0.0,
+                    help="boundary tracks fill a second slice within this width (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the plain FP32 comparison run")

@@ -82,7 +82,13 @@ typedef struct {
     int32_t max_pv_per_event;      /* output slots per event, 1..1024                       */
     int32_t chunk_events;          /* events whose UNet activations are resident at once;
                                       0 = max_events. Smaller chunks shrink the pool.       */
-    int32_t reserved[3];           /* must be 0                                             */
+    float boundary_mm;             /* §3 boundary tracks: 0 = every track fills its own
+                                      slice only. 0 < w < 5: a track whose slice-relative
+                                      z (float32, z - (-100 + 10 s)) is < w also fills slice
+                                      s - 1, one >= 10 - w (float32) also slice s + 1, with
+                                      feature 2 relative to the slice it fills; none below
+                                      slice 0 or above 39. Other values: INVALID_ARG.      */
+    int32_t reserved[2];           /* must be 0                                             */
     const float *fp8_act_scales;   /* host, PVF_FP8_E4M3 only: PVF_N_ACT_SCALES per-tensor
                                       input scales (amax / 448), or NULL to use
                                       pvf_calibrate before the first pvf_infer              */

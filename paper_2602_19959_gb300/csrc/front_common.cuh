@@ -46,9 +46,23 @@ __device__ __forceinline__ void zero_row16(void *base, int64_t e, int64_t rows_e
     store_row16<T>(base, e, rows_e, row, z, 1.0f);
 }
 
+// Sorted entries: bits 0-13 hold the track's index within the event, bits 14-15 the
+// slice the entry fills relative to the track's own: 0 its own, 1 the slice below, 2 the
+// slice above (the second slice of a boundary track, §3). sslice[t] holds the track's own
+// slice in bits 0-5 and that tag in bits 6-7; 255 marks a dropped track.
+constexpr int kEntTrack = 0x3FFF;
+__device__ __forceinline__ int entry_slice(int en, const uint8_t *sslice) {
+    const int d = en >> 14;
+    return (int)(sslice[en & kEntTrack] & 63u) - (d & 1) + (d >> 1);
+}
+
 // Steps a-c for event ge: validation (bypass flag), slice per track, stable counting
 // sort by slice. On return (after a block barrier) ssorted[0..nvalid) holds the event's
-// valid track indices grouped by slice in input order, sseg[s]..sseg[s+1] bounds slice s.
+// entries grouped by slice, sseg[s]..sseg[s+1] bounding slice s: within a slice, first
+// the slice's own valid tracks in input order, then the boundary tracks of the two
+// neighbouring slices that also fill it (a.edge > 0), in input order. A valid track of
+// slice s whose slice-relative z (float32) is below a.edge also fills s - 1 (s > 0); one
+// at or above a.edge_hi = 10 - a.edge also fills s + 1 (s < 39).
 // scnt/srun must hold 48 ints each. Every thread of the block must call this.
 template <int NT>
 __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int tid, int *scnt, int *sseg,
@@ -69,9 +83,19 @@ __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int ti
         bool finite = true;
 #pragma unroll
         for (int k = 0; k < kFeatures; ++k) finite &= isfinite(a.feat[k][gt]);
-        const int s = finite ? slice_of(a.feat[2][gt]) : -1;
-        sslice[t] = s < 0 ? 255 : (uint8_t)s;
-        if (s >= 0) atomicAdd(&scnt[s], 1);
+        const float z = a.feat[2][gt];
+        const int s = finite ? slice_of(z) : -1;
+        int tag = 0;
+        if (s >= 0) {
+            atomicAdd(&scnt[s], 1);
+            if (a.edge > 0.0f) {
+                const float zr = __fsub_rn(z, -100.0f + 10.0f * (float)s);   // as feature 2
+                if (s > 0 && zr < a.edge) tag = 1;
+                else if (s < kSlices - 1 && zr >= a.edge_hi) tag = 2;
+                if (tag) atomicAdd(&scnt[s - (tag & 1) + (tag >> 1)], 1);
+            }
+        }
+        sslice[t] = s < 0 ? 255 : (uint8_t)(s | (tag << 6));
     }
     __syncthreads();
     if (tid == 0) {
@@ -80,22 +104,36 @@ __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int ti
         sseg[kSlices] = acc;
     }
     __syncthreads();
-    // stable ranks by slice: warp 0 walks the tracks in input order
+    // stable ranks by slice: warp 0 walks the tracks in input order, once for their own
+    // slices and once more for the second slices of boundary tracks
     if (tid < 32) {
         const unsigned lane = tid;
-        for (int base = 0; base < n; base += 32) {
-            const int t = base + lane;
-            const int s = t < n ? sslice[t] : 255;
-            const unsigned peers = __match_any_sync(0xffffffffu, s);
-            const unsigned lower = peers & ((1u << lane) - 1u);
-            int before = 0;
-            if (s != 255) before = srun[s];
-            __syncwarp();
-            if (s != 255) {
-                ssorted[sseg[s] + before + __popc(lower)] = (uint16_t)t;
-                if (lower == 0) srun[s] = before + __popc(peers);
+        const int passes = a.edge > 0.0f ? 2 : 1;
+        for (int pass = 0; pass < passes; ++pass) {
+            for (int base = 0; base < n; base += 32) {
+                const int t = base + lane;
+                int s = 255, en = 0;
+                if (t < n && sslice[t] != 255) {
+                    const int own = sslice[t] & 63, tag = sslice[t] >> 6;
+                    if (pass == 0) {
+                        s = own;
+                        en = t;
+                    } else if (tag) {
+                        s = own - (tag & 1) + (tag >> 1);
+                        en = t | (tag << 14);
+                    }
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, s);
+                const unsigned lower = peers & ((1u << lane) - 1u);
+                int before = 0;
+                if (s != 255) before = srun[s];
+                __syncwarp();
+                if (s != 255) {
+                    ssorted[sseg[s] + before + __popc(lower)] = (uint16_t)en;
+                    if (lower == 0) srun[s] = before + __popc(peers);
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
     __syncthreads();

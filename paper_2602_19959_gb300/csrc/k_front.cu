@@ -9,7 +9,8 @@
 //      than max_tracks tracks;
 //   b. slice index per track, s = floor((z + 100) / 10) in float32 round-to-nearest;
 //      a track is dropped when a feature is not finite or s is outside [0, 40);
-//   c. stable counting sort of the valid tracks by slice (integer work only);
+//   c. stable counting sort of the valid tracks by slice (integer work only), with the
+//      boundary tracks' second slices (§3) when the boundary width is non-zero;
 //   d. hidden layers 1-5 of the FC net, one thread per track, in chunks of 256 sorted
 //      tracks, into a shared-memory tile of h5 vectors;
 //   e. output layer + histogram, bin-parallel: the thread owning bin j of slice s computes
@@ -38,9 +39,11 @@ struct FrontSmem {
     static constexpr size_t cnt = h5 + sizeof(float) * kChunk * kHPitch;  // 41 ints
     static constexpr size_t seg = cnt + sizeof(int) * 48;             // 41 ints
     static constexpr size_t run = seg + sizeof(int) * 48;             // 40 ints
-    static constexpr size_t sorted = run + sizeof(int) * 48;          // uint16 [max_tracks]
-    __host__ __device__ static size_t slices(int max_tracks) { return sorted + 2 * (size_t)((max_tracks + 7) / 8 * 8); }
-    __host__ __device__ static size_t total(int max_tracks) { return slices(max_tracks) + (size_t)max_tracks + 16; }
+    static constexpr size_t sorted = run + sizeof(int) * 48;          // uint16 [entries]
+    __host__ __device__ static size_t slices(int entries) { return sorted + 2 * (size_t)((entries + 7) / 8 * 8); }
+    __host__ __device__ static size_t total(int max_tracks, float edge) {
+        return slices(front_entries(max_tracks, edge)) + (size_t)max_tracks + 16;
+    }
 };
 
 // Hidden layers 1-5 of the FC net for one track; writes h5 (32 floats) to h_row.
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     int *sseg = reinterpret_cast<int *>(smem + FrontSmem::seg);
     int *srun = reinterpret_cast<int *>(smem + FrontSmem::run);
     uint16_t *ssorted = reinterpret_cast<uint16_t *>(smem + FrontSmem::sorted);
-    uint8_t *sslice = smem + FrontSmem::slices(a.max_tracks);
+    uint8_t *sslice = smem + FrontSmem::slices(front_entries(a.max_tracks, a.edge));
 
     const int tid = threadIdx.x;
     if constexpr (ENC1)
@@ -132,10 +135,9 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
             for (int c0 = 0; c0 < nvalid; c0 += kChunk) {
                 const int r = c0 + tid;
                 if (r < nvalid) {
-                    const int t = ssorted[r];
-                    const int64_t gt = t0 + t;
+                    const int en = ssorted[r];
                     float x[kFcInPad];
-                    track_features(a, gt, sslice[t], x);
+                    track_features(a, t0 + (en & kEntTrack), entry_slice(en, sslice), x);
                     fc_hidden(sfc, x, sh5 + tid * kHPitch);
                 }
                 __syncthreads();
@@ -201,7 +203,7 @@ cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
-size_t front_smem_bytes(int max_tracks) { return FrontSmem::total(max_tracks); }
+size_t front_smem_bytes(int max_tracks, float edge) { return FrontSmem::total(max_tracks, edge); }
 
 cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;

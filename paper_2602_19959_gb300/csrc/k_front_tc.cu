@@ -46,8 +46,10 @@ struct TcSmem {
     static constexpr size_t run = seg + sizeof(int) * 48;
     static constexpr size_t bar = (run + sizeof(int) * 48 + 15) / 16 * 16;   // mbarrier + slot + flag
     static constexpr size_t sorted = bar + 32;
-    __host__ __device__ static size_t slices(int mt) { return sorted + 2 * (size_t)((mt + 7) / 8 * 8); }
-    __host__ __device__ static size_t total(int mt) { return slices(mt) + (size_t)mt + 16; }
+    __host__ __device__ static size_t slices(int ne) { return sorted + 2 * (size_t)((ne + 7) / 8 * 8); }
+    __host__ __device__ static size_t total(int mt, float edge) {
+        return slices(front_entries(mt, edge)) + (size_t)mt + 16;
+    }
 };
 
 // FC operand type of each form and its tcgen05 kind::f16 format code (0 = f16, 1 = bf16).
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TcSmem::bar + 8);
     volatile int *never = reinterpret_cast<volatile int *>(smem + TcSmem::bar + 12);
     uint16_t *ssorted = reinterpret_cast<uint16_t *>(smem + TcSmem::sorted);
-    uint8_t *sslice = smem + TcSmem::slices(a.max_tracks);
+    uint8_t *sslice = smem + TcSmem::slices(front_entries(a.max_tracks, a.edge));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp >> 2;                       // tile of this warpgroup
@@ -152,8 +154,8 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) x[k] = 0.0f;
                     if (live) {
-                        const int t = ssorted[r];
-                        track_features(a, t0 + t, sslice[t], x);
+                        const int en = ssorted[r];
+                        track_features(a, t0 + (en & kEntTrack), entry_slice(en, sslice), x);
                     }
                     *reinterpret_cast<uint4 *>(xrow) = pack8<FT>(x);
                     *reinterpret_cast<uint4 *>(xrow + kPlane) = pack8<FT>(x + 8);
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                     float acc = 0.0f, held = 0.0f;
                     int held_s = -1;
                     if (cb < ce) {
-                        int s = sslice[ssorted[c0 + cb]];
+                        int s = entry_slice(ssorted[c0 + cb], sslice);
                         int send = sseg[s + 1] - c0;           // first pass row past slice s
                         bool hold = g == 1;                    // warpgroup 1 holds its first segment
 #pragma unroll 1
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                                         *hp = __fadd_rn(*hp, acc);
                                     }
                                     acc = 0.0f;
-                                    s = sslice[ssorted[c0 + col + t1]];
+                                    s = entry_slice(ssorted[c0 + col + t1], sslice);
                                     send = sseg[s + 1] - c0;
                                 }
                                 t0 = t1;
@@ -305,7 +307,7 @@ cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
     // per SM, which also fill the 512 TMEM columns), each walking events
     static size_t configured = 0;
     static int grid_cap = 0;
-    const size_t smem = TcSmem::total(a.max_tracks);
+    const size_t smem = TcSmem::total(a.max_tracks, a.edge);
     if (smem > configured) {
         cudaError_t err = cudaFuncSetAttribute(k_front_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;

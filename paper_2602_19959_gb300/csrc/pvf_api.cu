@@ -191,6 +191,7 @@ pvf_status check_config(const pvf_config *c) {
     if (c->max_pv_per_event < 1 || c->max_pv_per_event > 1024) return PVF_ERR_INVALID_ARG;
     if (c->chunk_events < 0 || c->chunk_events > c->max_events) return PVF_ERR_INVALID_ARG;
     for (int r : c->reserved) if (r != 0) return PVF_ERR_INVALID_ARG;
+    if (!(c->boundary_mm >= 0.0f && c->boundary_mm < 5.0f)) return PVF_ERR_INVALID_ARG;
     return PVF_OK;
 }
 
@@ -319,7 +320,7 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
     h->cfg.fp8_act_scales = nullptr;
     h->plan = plan;
     h->pool = static_cast<unsigned char *>(pool);
-    h->front_smem = front_smem_bytes(cfg->max_tracks_per_event);
+    h->front_smem = front_smem_bytes(cfg->max_tracks_per_event, cfg->boundary_mm);
     h->f32 = f32_layout();
     for (int i = 0; i < PVF_N_ACT_SCALES; ++i)
         h->act_scale[i] = cfg->fp8_act_scales ? cfg->fp8_act_scales[i] : 1.0f;
@@ -458,6 +459,8 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.n_events = n;
         a.ev_base = ev_base;
         a.max_tracks = h->cfg.max_tracks_per_event;
+        a.edge = h->cfg.boundary_mm;
+        a.edge_hi = 10.0f - h->cfg.boundary_mm;
         a.fc = h->fc;
         a.enc1 = h->enc1;
         a.hist_in = hist_in;

@@ -169,6 +169,8 @@ struct FrontArgs {
     int32_t n_events;            // events in this launch
     int32_t ev_base;             // global index of the launch's first event
     int32_t max_tracks;          // per-event cap
+    float edge;                  // boundary-track width in mm (0: every track in one slice)
+    float edge_hi;               // 10 - edge, rounded to float
     const float *fc;             // packed FC block (kFcFloats); its biases serve both forms
     const unsigned char *fc_img; // tensor-core forms: bf16 FC operand images (kFcImgBytes)
     const float *enc1;           // kEnc1Floats
@@ -235,7 +237,12 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 // Host-side launchers (defined in the kernel translation units).
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem_bytes, cudaStream_t s);
-size_t front_smem_bytes(int max_tracks);
+// Sorted (track, slice) entries an event may hold: boundary tracks (§3) fill a second
+// slice, so up to two per track when the boundary width is non-zero.
+__host__ __device__ __forceinline__ int front_entries(int max_tracks, float edge) {
+    return edge > 0.0f ? 2 * max_tracks : max_tracks;
+}
+size_t front_smem_bytes(int max_tracks, float edge);
 // Steps 1-2 + enc1 with the FC on tcgen05 (BF16 and FP8 forms).
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s);
 // Steps 1-2 only (validate, sort, FC, histogram into a.hist_out), float32; e1/p1 unused.

@@ -83,7 +83,7 @@ extern "C" pvf_status pvf_histogram_static(const void *weights_blob, size_t blob
     a.e1_inv_scale = 1.0f;
     a.ev_flag = out_bypass ? out_bypass : reinterpret_cast<int32_t *>(base + kOffFlags);
     a.status = nullptr;
-    if (launch_front_hist_only(a, front_smem_bytes(kStaticMaxTracks), s) != cudaSuccess)
+    if (launch_front_hist_only(a, front_smem_bytes(kStaticMaxTracks, 0.0f), s) != cudaSuccess)
         return PVF_ERR_CUDA;
     return PVF_OK;
 }

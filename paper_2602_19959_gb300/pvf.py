@@ -44,8 +44,8 @@ EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex"
 class PvfConfig(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_events", ctypes.c_int32),
                 ("max_tracks_per_event", ctypes.c_int32), ("max_pv_per_event", ctypes.c_int32),
-                ("chunk_events", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
-                ("fp8_act_scales", ctypes.c_void_p)]
+                ("chunk_events", ctypes.c_int32), ("boundary_mm", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 2), ("fp8_act_scales", ctypes.c_void_p)]
 
 
 class PvfTracks(ctypes.Structure):
@@ -133,8 +133,9 @@ def _check(code: int, where: str, allow_warn: bool = False):
 
 
 def make_config(precision="fp32", max_events=1, max_tracks_per_event=2048, max_pv_per_event=64,
-                chunk_events=0, fp8_act_scales=None):
+                chunk_events=0, fp8_act_scales=None, boundary_mm=0.0):
     cfg = PvfConfig()
+    cfg.boundary_mm = boundary_mm
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.max_events = max_events
     cfg.max_tracks_per_event = max_tracks_per_event
@@ -214,12 +215,13 @@ class PVFinder:
 
     def __init__(self, weights: dict, precision="fp32", max_events=1024,
                  max_tracks_per_event=2048, max_pv_per_event=64, chunk_events=0,
-                 fp8_act_scales=None, device=None, stream=None):
+                 fp8_act_scales=None, device=None, stream=None, boundary_mm=0.0):
         import torch
         self.lib = load()
         self.device = torch.device(device or "cuda")
         self.cfg, self._keep = make_config(precision, max_events, max_tracks_per_event,
-                                           max_pv_per_event, chunk_events, fp8_act_scales)
+                                           max_pv_per_event, chunk_events, fp8_act_scales,
+                                           boundary_mm)
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_pool_bytes_required(ctypes.byref(self.cfg), ctypes.byref(need)),
                "pvf_pool_bytes_required")

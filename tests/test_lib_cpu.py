@@ -56,8 +56,10 @@ def test_pool_bytes_required_and_config_validation(lib):
     assert fp32 < 2 * 1024 ** 3                      # the 1000-event plan fits a 2 GB pool
     chunked = P.pool_bytes_required(precision="fp32", max_events=1000, chunk_events=100)
     assert chunked < fp32 / 5
+    assert P.pool_bytes_required(precision="bf16", max_events=1000, boundary_mm=0.5) == bf16
     for bad in (dict(max_events=0), dict(max_tracks_per_event=0), dict(max_tracks_per_event=9000),
-                dict(max_pv_per_event=0), dict(chunk_events=-1), dict(precision=7)):
+                dict(max_pv_per_event=0), dict(chunk_events=-1), dict(precision=7),
+                dict(boundary_mm=-0.1), dict(boundary_mm=5.0), dict(boundary_mm=float("nan"))):
         kw = dict(precision="fp32", max_events=10)
         kw.update(bad)
         cfg, _ = P.make_config(**kw)
