@@ -50,10 +50,21 @@ __device__ __forceinline__ void zero_row16(void *base, int64_t e, int64_t rows_e
 // slice the entry fills relative to the track's own: 0 its own, 1 the slice below, 2 the
 // slice above (the second slice of a boundary track, §3). sslice[t] holds the track's own
 // slice in bits 0-5 and that tag in bits 6-7; 255 marks a dropped track.
+// Without boundary tracks (EDGE = false) an entry is the track index and sslice[t] its
+// slice: the kernels are then instantiated without any of this decoding.
 constexpr int kEntTrack = 0x3FFF;
+template <bool EDGE>
+__device__ __forceinline__ int entry_track(int en) {
+    return EDGE ? (en & kEntTrack) : en;
+}
+template <bool EDGE>
 __device__ __forceinline__ int entry_slice(int en, const uint8_t *sslice) {
-    const int d = en >> 14;
-    return (int)(sslice[en & kEntTrack] & 63u) - (d & 1) + (d >> 1);
+    if constexpr (!EDGE) {
+        return sslice[en];
+    } else {
+        const int d = en >> 14;
+        return (int)(sslice[en & kEntTrack] & 63u) - (d & 1) + (d >> 1);
+    }
 }
 
 // Steps a-c for event ge: validation (bypass flag), slice per track, stable counting
@@ -63,8 +74,9 @@ __device__ __forceinline__ int entry_slice(int en, const uint8_t *sslice) {
 // neighbouring slices that also fill it (a.edge > 0), in input order. A valid track of
 // slice s whose slice-relative z (float32) is below a.edge also fills s - 1 (s > 0); one
 // at or above a.edge_hi = 10 - a.edge also fills s + 1 (s < 39).
-// scnt/srun must hold 48 ints each. Every thread of the block must call this.
-template <int NT>
+// EDGE = false: no boundary tracks (a.edge is 0). scnt/srun must hold 48 ints each.
+// Every thread of the block must call this.
+template <int NT, bool EDGE>
 __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int tid, int *scnt, int *sseg,
                                               int *srun, uint16_t *ssorted, uint8_t *sslice,
                                               int64_t &t0_out, int &nvalid_out) {
@@ -88,7 +100,7 @@ __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int ti
         int tag = 0;
         if (s >= 0) {
             atomicAdd(&scnt[s], 1);
-            if (a.edge > 0.0f) {
+            if constexpr (EDGE) {
                 const float zr = __fsub_rn(z, -100.0f + 10.0f * (float)s);   // as feature 2
                 if (s > 0 && zr < a.edge) tag = 1;
                 else if (s < kSlices - 1 && zr >= a.edge_hi) tag = 2;
@@ -108,16 +120,17 @@ __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int ti
     // slices and once more for the second slices of boundary tracks
     if (tid < 32) {
         const unsigned lane = tid;
-        const int passes = a.edge > 0.0f ? 2 : 1;
-        for (int pass = 0; pass < passes; ++pass) {
+#pragma unroll 1
+        for (int pass = 0; pass < (EDGE ? 2 : 1); ++pass) {
             for (int base = 0; base < n; base += 32) {
                 const int t = base + lane;
-                int s = 255, en = 0;
-                if (t < n && sslice[t] != 255) {
+                int s = 255, en = t;
+                if constexpr (!EDGE) {
+                    if (t < n) s = sslice[t];
+                } else if (t < n && sslice[t] != 255) {
                     const int own = sslice[t] & 63, tag = sslice[t] >> 6;
                     if (pass == 0) {
                         s = own;
-                        en = t;
                     } else if (tag) {
                         s = own - (tag & 1) + (tag >> 1);
                         en = t | (tag << 14);

@@ -94,7 +94,8 @@ __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const flo
 }
 
 // ENC1 = false: steps a-e only (the histogram), nothing written to e1/p1.
-template <int PREC, bool ENC1 = true>
+// EDGE: boundary tracks fill a second slice (a.edge > 0).
+template <int PREC, bool ENC1, bool EDGE>
 __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     int *sseg = reinterpret_cast<int *>(smem + FrontSmem::seg);
     int *srun = reinterpret_cast<int *>(smem + FrontSmem::run);
     uint16_t *ssorted = reinterpret_cast<uint16_t *>(smem + FrontSmem::sorted);
-    uint8_t *sslice = smem + FrontSmem::slices(front_entries(a.max_tracks, a.edge));
+    uint8_t *sslice = smem + FrontSmem::slices(EDGE ? 2 * a.max_tracks : a.max_tracks);
 
     const int tid = threadIdx.x;
     if constexpr (ENC1)
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
             for (int i = tid; i < kBins; i += kThreads) shist[i] = 0.0f;
             int64_t t0;
             int nvalid;
-            validate_sort<kThreads>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
+            validate_sort<kThreads, EDGE>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
 
             // ---- d/e. hidden layers per track, then output layer + per-bin sequential sums
             const float *w6t = sfc + fc_w_off(5);
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
                 if (r < nvalid) {
                     const int en = ssorted[r];
                     float x[kFcInPad];
-                    track_features(a, t0 + (en & kEntTrack), entry_slice(en, sslice), x);
+                    track_features(a, t0 + entry_track<EDGE>(en), entry_slice<EDGE>(en, sslice), x);
                     fc_hidden(sfc, x, sh5 + tid * kHPitch);
                 }
                 __syncthreads();
@@ -179,12 +180,12 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
 
 // Persistent grid: as many CTAs as the shared memory lets reside (at most two per SM,
 // the register limit at 256 threads), capped by the number of events.
-template <int PREC, bool ENC1>
+template <int PREC, bool ENC1, bool EDGE>
 cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     static size_t configured = 0;
     static int sms = 0;
     if (smem > configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         configured = smem;
         int dev = 0;
@@ -197,7 +198,7 @@ cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;
-    k_front<PREC, ENC1><<<grid, kThreads, smem, s>>>(a);
+    k_front<PREC, ENC1, EDGE><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -207,14 +208,16 @@ size_t front_smem_bytes(int max_tracks, float edge) { return FrontSmem::total(ma
 
 cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    return launch_front_t<PVF_FP32, false>(a, smem, s);
+    if (a.edge > 0.0f) return cudaErrorInvalidValue;   // the no-allocation path has no boundary tracks
+    return launch_front_t<PVF_FP32, false, false>(a, smem, s);
 }
 
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
     // the tensor-core forms run k_front_tc
     if (precision != PVF_FP32) return cudaErrorInvalidValue;
-    return launch_front_t<PVF_FP32, true>(a, smem, s);
+    return a.edge > 0.0f ? launch_front_t<PVF_FP32, true, true>(a, smem, s)
+                         : launch_front_t<PVF_FP32, true, false>(a, smem, s);
 }
 
 }  // namespace pvf

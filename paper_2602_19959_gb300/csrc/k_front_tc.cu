@@ -73,7 +73,9 @@ __device__ __forceinline__ float softplus_tc(float x) {
     return x < -15.0f ? u : l;
 }
 
-template <int PREC>
+// EDGE: boundary tracks fill a second slice (a.edge > 0); without them the sort and the
+// entry decoding compile to the one-slice form.
+template <int PREC, bool EDGE>
 __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     using FT = typename FcOp<PREC>::T;
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TcSmem::bar + 8);
     volatile int *never = reinterpret_cast<volatile int *>(smem + TcSmem::bar + 12);
     uint16_t *ssorted = reinterpret_cast<uint16_t *>(smem + TcSmem::sorted);
-    uint8_t *sslice = smem + TcSmem::slices(front_entries(a.max_tracks, a.edge));
+    uint8_t *sslice = smem + TcSmem::slices(EDGE ? 2 * a.max_tracks : a.max_tracks);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp >> 2;                       // tile of this warpgroup
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
             for (int i = tid; i < kBins; i += kT) shist[i] = 0.0f;
             int64_t t0;
             int nvalid;
-            validate_sort<kT>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
+            validate_sort<kT, EDGE>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
             if (failed) nvalid = 0;        // a timed-out MMA ends the tensor-core work
             for (int c0 = 0; c0 < nvalid && !failed; c0 += 2 * kRows) {
                 const int ntile = nvalid - c0 > kRows ? 2 : 1;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                     for (int k = 0; k < 16; ++k) x[k] = 0.0f;
                     if (live) {
                         const int en = ssorted[r];
-                        track_features(a, t0 + (en & kEntTrack), entry_slice(en, sslice), x);
+                        track_features(a, t0 + entry_track<EDGE>(en), entry_slice<EDGE>(en, sslice), x);
                     }
                     *reinterpret_cast<uint4 *>(xrow) = pack8<FT>(x);
                     *reinterpret_cast<uint4 *>(xrow + kPlane) = pack8<FT>(x + 8);
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                     float acc = 0.0f, held = 0.0f;
                     int held_s = -1;
                     if (cb < ce) {
-                        int s = entry_slice(ssorted[c0 + cb], sslice);
+                        int s = entry_slice<EDGE>(ssorted[c0 + cb], sslice);
                         int send = sseg[s + 1] - c0;           // first pass row past slice s
                         bool hold = g == 1;                    // warpgroup 1 holds its first segment
 #pragma unroll 1
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                                         *hp = __fadd_rn(*hp, acc);
                                     }
                                     acc = 0.0f;
-                                    s = entry_slice(ssorted[c0 + col + t1], sslice);
+                                    s = entry_slice<EDGE>(ssorted[c0 + col + t1], sslice);
                                     send = sseg[s + 1] - c0;
                                 }
                                 t0 = t1;
@@ -301,15 +303,15 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
 
 }  // namespace
 
-template <int PREC>
-cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
+template <int PREC, bool EDGE>
+cudaError_t launch_front_tc_k(const FrontArgs &a, cudaStream_t s) {
     // persistent grid: as many CTAs as fit on the GPU at once (shared memory allows two
     // per SM, which also fill the 512 TMEM columns), each walking events
     static size_t configured = 0;
     static int grid_cap = 0;
     const size_t smem = TcSmem::total(a.max_tracks, a.edge);
     if (smem > configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_front_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err = cudaFuncSetAttribute(k_front_tc<PREC, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         configured = smem;
         int dev = 0, sms = 0;
@@ -320,8 +322,13 @@ cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
     const int per_sm = (int)((228 * 1024) / (smem + 1024));
     int grid = grid_cap / 2 * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
     if (grid > a.n_events) grid = a.n_events;
-    k_front_tc<PREC><<<grid, kT, smem, s>>>(a);
+    k_front_tc<PREC, EDGE><<<grid, kT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
+    return a.edge > 0.0f ? launch_front_tc_k<PREC, true>(a, s) : launch_front_tc_k<PREC, false>(a, s);
 }
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {
