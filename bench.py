@@ -114,9 +114,9 @@ def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_laun
 # events (traffic grows with the events). Keyed by (form, kernel, events per launch). A kernel changed since
 # that capture has no entry and reports null.
 NCU_TRAFFIC = {
-    ("bf16", "dec3_up2", 1000): (131.739392e6 + 28.363776e6) * 1000 / 512,
-    ("bf16", "dec1_final", 1000): (131.238144e6 + 4.410112e6) * 1000 / 512,
-    ("bf16", "dec2_up1", 1000): (131.402240e6 + 28.493568e6) * 1000 / 512,
+    ("bf16", "dec3_up2", 1000): (131.772416e6 + 27.987456e6) * 1000 / 512,
+    ("bf16", "dec1_final", 1000): (131.240704e6 + 4.577280e6) * 1000 / 512,
+    ("bf16", "dec2_up1", 1000): (131.400960e6 + 28.645632e6) * 1000 / 512,
 }
 
 
