@@ -53,43 +53,45 @@ def convT_io(L, cin, cout):
     return L * 2 * cout * cin, cin * (L + 4), cout * (2 * L + 4)
 
 
-def kernel_table(form):
-    """Algorithmic work per event of each kernel family: (MAC, bytes, compute unit).
-    MACs of the FC depend on the track count and are added by the caller."""
+def kernel_table(form, c0=16):
+    """Algorithmic work per event of each kernel family: (MAC, bytes, compute unit), for
+    UNet base width c0 (levels c0, 2 c0, 4 c0, 8 c0). MACs of the FC depend on the track
+    count and are added by the caller."""
     es = {"fp32": 4, "bf16": 2, "fp16": 2, "fp8": 1}[form]
+    c1, c2, c3, c4 = c0, 2 * c0, 4 * c0, 8 * c0
     t = {}
-    e1 = 16 * 4004 + 16 * 2004               # e1 and p1 written by the front kernel
-    t["front"] = (4000 * 16 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
-    m, r, w = conv_io(2000, 16, 32, pool=True); t["enc2"] = (m, 0, (r + w) * es, None)
-    m, r, w = conv_io(1000, 32, 64, pool=True); t["enc3"] = (m, 0, (r + w) * es, None)
+    e1 = c1 * 4004 + c1 * 2004               # e1 and p1 written by the front kernel
+    t["front"] = (4000 * c1 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
+    m, r, w = conv_io(2000, c1, c2, pool=True); t["enc2"] = (m, 0, (r + w) * es, None)
+    m, r, w = conv_io(1000, c2, c3, pool=True); t["enc3"] = (m, 0, (r + w) * es, None)
     if form == "fp32":
-        m, r, w = conv_io(500, 64, 128); t["enc4"] = (m, 0, (r + w) * es, None)
-        m, r, w = convT_io(500, 128, 64); t["up3"] = (m, 0, (r + w) * es, None)
-        m, r, w = conv_io(1000, 128, 64); t["dec3"] = (m, 0, (r + w) * es, None)
-        m, r, w = convT_io(1000, 64, 32); t["up2"] = (m, 0, (r + w) * es, None)
-        m, r, w = conv_io(2000, 64, 32); t["dec2"] = (m, 0, (r + w) * es, None)
-        m, r, w = convT_io(2000, 32, 16); t["up1"] = (m, 0, (r + w) * es, None)
-        m, r, w = conv_io(4000, 32, 16); t["dec1"] = (m, 0, (r + w) * es, None)
-        t["tail"] = (4000 * 16 * 5, 0, 16 * 4004 * es + 16000, "alu")
+        m, r, w = conv_io(500, c3, c4); t["enc4"] = (m, 0, (r + w) * es, None)
+        m, r, w = convT_io(500, c4, c3); t["up3"] = (m, 0, (r + w) * es, None)
+        m, r, w = conv_io(1000, 2 * c3, c3); t["dec3"] = (m, 0, (r + w) * es, None)
+        m, r, w = convT_io(1000, c3, c2); t["up2"] = (m, 0, (r + w) * es, None)
+        m, r, w = conv_io(2000, 2 * c2, c2); t["dec2"] = (m, 0, (r + w) * es, None)
+        m, r, w = convT_io(2000, c2, c1); t["up1"] = (m, 0, (r + w) * es, None)
+        m, r, w = conv_io(4000, 2 * c1, c1); t["dec1"] = (m, 0, (r + w) * es, None)
+        t["tail"] = (4000 * c1 * 5, 0, c1 * 4004 * es + 16000, "alu")
     else:
-        m1, r1, _ = conv_io(500, 64, 128); m2, _, w2 = convT_io(500, 128, 64)
+        m1, r1, _ = conv_io(500, c3, c4); m2, _, w2 = convT_io(500, c4, c3)
         t["enc4_up3"] = (m1 + m2, 0, (r1 + w2) * es, None)
-        m1, r1, _ = conv_io(1000, 128, 64); m2, _, w2 = convT_io(1000, 64, 32)
+        m1, r1, _ = conv_io(1000, 2 * c3, c3); m2, _, w2 = convT_io(1000, c3, c2)
         t["dec3_up2"] = (m1 + m2, 0, (r1 + w2) * es, None)
-        m1, r1, _ = conv_io(2000, 64, 32); m2, _, w2 = convT_io(2000, 32, 16)
+        m1, r1, _ = conv_io(2000, 2 * c2, c2); m2, _, w2 = convT_io(2000, c2, c1)
         t["dec2_up1"] = (m1 + m2, 0, (r1 + w2) * es, None)
-        m1, r1, _ = conv_io(4000, 32, 16)
-        t["dec1_final"] = (m1 + 4000 * 16 * 5, 0, r1 * es + 16000, None)
+        m1, r1, _ = conv_io(4000, 2 * c1, c1)
+        t["dec1_final"] = (m1 + 4000 * c1 * 5, 0, r1 * es + 16000, None)
         t["tail"] = (0, 0, 16000, "hbm")
     return t
 
 
 def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_launch, peaks,
-                fc_evals=None):
+                fc_evals=None, c0=16):
     """Roofline of one kernel family from its algorithmic FLOPs and bytes per launch:
     the bound is whichever of compute and memory needs more time at its peak. fc_evals:
     FC evaluations per launch (tracks plus second slices of boundary tracks)."""
-    mac, per_track_b, bytes_ev, unit = kernel_table(form)[name]
+    mac, per_track_b, bytes_ev, unit = kernel_table(form, c0)[name]
     flops = 2.0 * mac * events_per_launch
     nbytes = bytes_ev * events_per_launch + per_track_b * tracks_per_launch
     if name == "front":
@@ -289,11 +291,11 @@ def fc_evaluations(batch, edge):
 def workload_config(args, dtype):
     return {"workload": f"PVFinder inference, {args.events} synthetic events per GPU "
                         f"(~155 tracks/event, Poisson 5.6 PVs), 4000-bin histogram, "
-                        f"16/32/64/128 UNet, {dtype}",
+                        f"{'/'.join(str(args.unet_width * k) for k in (1, 2, 4, 8))} UNet, {dtype}",
             "events_per_gpu": args.events, "bins": 4000, "max_pv_per_event": args.max_pv,
             "l2": f"flushed between steps ({args.flush_mb} MB write)" if args.flush_mb >= 256
                   else "not flushed (profiling run)", "form": args.precision,
-            "boundary_mm": args.boundary_mm}
+            "boundary_mm": args.boundary_mm, "unet_width": args.unet_width}
 
 
 def make_finder(args, weights, precision, events, **kw):
@@ -467,11 +469,13 @@ def run_step(args, weights, batch, rank, world, local):
     kernels = {}
     total_ms = max(sum(v[1] for v in prof.values()), 1e-9)
     for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks, fc_evals)
+        rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks, fc_evals,
+                         args.unet_width)
         kernels[k] = {"launches": n, "avg_us": 1000.0 * ms / max(n, 1), "share": ms / total_ms,
                       "bound": rf["bound"], "frac": rf["frac"]}
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks, fc_evals)
+    roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks, fc_evals,
+                       args.unet_width)
     traffic = NCU_TRAFFIC.get((args.precision, name, args.events))
     roof.update({"kernel": name, "traffic": traffic,
                  "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
@@ -574,6 +578,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--max-pv", type=int, default=672)
+    ap.add_argument("--unet-width", type=int, default=16, choices=[16, 32],
+                    help="UNet base width (32: the wide variant, float32 form only)")
     ap.add_argument("--boundary-mm", type=float, default=0.0,
                     help="boundary tracks fill a second slice within this width (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -593,7 +599,9 @@ def main():
 
     import synth
     rank, world, local = dist_env()
-    weights = synth.he_weights(0)
+    if args.unet_width != 16 and args.precision != "fp32":
+        ap.error("--unet-width 32 exists in the fp32 form only")
+    weights = synth.he_weights(0, c0=args.unet_width)
     if args.impl == "reference":
         batch = synth.generate_standard(args.events, rank_workload_seed(rank))
         run_reference(args, weights, batch, rank, world)

@@ -88,7 +88,13 @@ typedef struct {
                                       s - 1, one >= 10 - w (float32) also slice s + 1, with
                                       feature 2 relative to the slice it fills; none below
                                       slice 0 or above 39. Other values: INVALID_ARG.      */
-    int32_t reserved[2];           /* must be 0                                             */
+    int32_t unet_width;            /* UNet base width c0 (levels c0, 2c0, 4c0, 8c0): 0 or 16
+                                      = the 16/32/64/128 network; 32 = the wide 32/64/128/256
+                                      variant (§5's channel-count axis), PVF_FP32 only
+                                      (tensor-core forms: UNSUPPORTED). Must match the
+                                      blob's width (else pvf_create returns ERR_WEIGHTS).
+                                      Other values: INVALID_ARG.                            */
+    int32_t reserved[1];           /* must be 0                                             */
     const float *fp8_act_scales;   /* host, PVF_FP8_E4M3 only: PVF_N_ACT_SCALES per-tensor
                                       input scales (amax / 448), or NULL to use
                                       pvf_calibrate before the first pvf_infer              */

@@ -240,11 +240,24 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
     }
 }
 
+// Channels [16 g, 16 g + 16) of storage row `row` of event e in a channel-last float32
+// tensor of C0 channels.
+template <int C0>
+__device__ __forceinline__ void store_seg16_f32(void *base, int64_t e, int64_t rows_e, int64_t row, int g,
+                                                const float v[16]) {
+    float4 *d = reinterpret_cast<float4 *>(reinterpret_cast<float *>(base) + (e * rows_e + row) * C0 + 16 * g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
 // Step f with the weights read from shared memory per position pair, for the float32 front,
-// whose FC registers leave no room for them (same arithmetic, same order).
-template <class T, int NT, bool AMAX>
+// whose FC registers leave no room for them (same arithmetic, same order). senc holds
+// W[t][co] (5 C0 floats) then b[co]; the C0 channels are produced 16 at a time. A width
+// above 16 exists only in the float32 form.
+template <class T, int NT, bool AMAX, int C0>
 __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, int tid, const float *shist,
                                                    const float *senc) {
+    static_assert(C0 % 16 == 0 && (C0 == kC0 || sizeof(T) == 4), "wide networks are float32 only");
     const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
     float vmax = 0.0f;
@@ -255,23 +268,33 @@ __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, in
             const int p = 2 * q + k - 2;
             hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
         }
-        float v0[kC0], v1[kC0], vp[kC0];
+#pragma unroll 1
+        for (int g = 0; g < C0 / 16; ++g) {
+            float v0[16], v1[16], vp[16];
 #pragma unroll
-        for (int co = 0; co < kC0; ++co) {
-            float a0 = senc[5 * kC0 + co], a1 = a0;
+            for (int j = 0; j < 16; ++j) {
+                const int co = 16 * g + j;
+                float a0 = senc[5 * C0 + co], a1 = a0;
 #pragma unroll
-            for (int t = 0; t < 5; ++t) {
-                a0 = fmaf(senc[t * kC0 + co], hv[t], a0);
-                a1 = fmaf(senc[t * kC0 + co], hv[t + 1], a1);
+                for (int t = 0; t < 5; ++t) {
+                    a0 = fmaf(senc[t * C0 + co], hv[t], a0);
+                    a1 = fmaf(senc[t * C0 + co], hv[t + 1], a1);
+                }
+                v0[j] = leaky(a0);
+                v1[j] = leaky(a1);
+                vp[j] = fmaxf(v0[j], v1[j]);
+                if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[j]), fabsf(v1[j])));
             }
-            v0[co] = leaky(a0);
-            v1[co] = leaky(a1);
-            vp[co] = fmaxf(v0[co], v1[co]);
-            if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[co]), fabsf(v1[co])));
+            if constexpr (C0 == kC0) {
+                store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
+                store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
+                store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
+            } else {
+                store_seg16_f32<C0>(a.e1, e, rows1, 2 * q + kPad, g, v0);
+                store_seg16_f32<C0>(a.e1, e, rows1, 2 * q + 1 + kPad, g, v1);
+                store_seg16_f32<C0>(a.p1, e, rows2, q + kPad, g, vp);
+            }
         }
-        store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
-        store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
-        store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
     }
     if constexpr (AMAX) {
 #pragma unroll
@@ -280,22 +303,34 @@ __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, in
     }
     if (tid < 4) {
         const int r = tid < 2 ? tid : kBins + tid;
-        zero_row16<T>(a.e1, e, rows1, r);
         const int rp = tid < 2 ? tid : kBins / 2 + tid;
-        zero_row16<T>(a.p1, e, rows2, rp);
+        if constexpr (C0 == kC0) {
+            zero_row16<T>(a.e1, e, rows1, r);
+            zero_row16<T>(a.p1, e, rows2, rp);
+        } else {
+            float z[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z[i] = 0.0f;
+            for (int g = 0; g < C0 / 16; ++g) {
+                store_seg16_f32<C0>(a.e1, e, rows1, r, g, z);
+                store_seg16_f32<C0>(a.p1, e, rows2, rp, g, z);
+            }
+        }
     }
 }
 
-// REGW: weights in registers (tensor-core front) or read from shared memory (float32 front).
-template <class T, int NT, bool REGW = true>
+// REGW: weights in registers (tensor-core front, width 16) or read from shared memory
+// (float32 front, width C0).
+template <class T, int NT, bool REGW = true, int C0 = kC0>
 __device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, const float *shist,
                                           const float *senc) {
     if constexpr (REGW) {
+        static_assert(C0 == kC0, "register weights for width 16");
         if (a.amax) enc1_pool_t<T, NT, true>(a, e, tid, shist, senc);
         else enc1_pool_t<T, NT, false>(a, e, tid, shist, senc);
     } else {
-        if (a.amax) enc1_pool_shared_t<T, NT, true>(a, e, tid, shist, senc);
-        else enc1_pool_shared_t<T, NT, false>(a, e, tid, shist, senc);
+        if (a.amax) enc1_pool_shared_t<T, NT, true, C0>(a, e, tid, shist, senc);
+        else enc1_pool_shared_t<T, NT, false, C0>(a, e, tid, shist, senc);
     }
 }
 

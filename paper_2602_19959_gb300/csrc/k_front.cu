@@ -33,8 +33,8 @@ constexpr int kHPitch = kFcHidden + 1;    // 33: conflict-free per-track rows
 struct FrontSmem {
     // byte offsets into dynamic shared memory
     static constexpr size_t fc = 0;                                   // kFcFloats floats
-    static constexpr size_t enc1 = fc + sizeof(float) * kFcFloats;    // kEnc1Floats
-    static constexpr size_t hist = (enc1 + sizeof(float) * kEnc1Floats + 15) / 16 * 16;
+    static constexpr size_t enc1 = fc + sizeof(float) * kFcFloats;    // 6 c0 floats
+    static constexpr size_t hist = (enc1 + sizeof(float) * kEnc1FloatsMax + 15) / 16 * 16;
     static constexpr size_t h5 = hist + sizeof(float) * kBins;        // kChunk x 33
     static constexpr size_t cnt = h5 + sizeof(float) * kChunk * kHPitch;  // 41 ints
     static constexpr size_t seg = cnt + sizeof(int) * 48;             // 41 ints
@@ -95,7 +95,8 @@ __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const flo
 
 // ENC1 = false: steps a-e only (the histogram), nothing written to e1/p1.
 // EDGE: boundary tracks fill a second slice (a.edge > 0).
-template <int PREC, bool ENC1, bool EDGE>
+// C0: UNet base width of the e1 / p1 tensors written here (16, or 32 in this float32 form).
+template <int PREC, bool ENC1, bool EDGE, int C0>
 __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
 
     const int tid = threadIdx.x;
     if constexpr (ENC1)
-        for (int i = tid; i < kEnc1Floats; i += kThreads) senc[i] = a.enc1[i];
+        for (int i = tid; i < 6 * C0; i += kThreads) senc[i] = a.enc1[i];
     if (!a.hist_in)
         for (int i = tid; i < kFcFloats; i += kThreads) sfc[i] = a.fc[i];
     __syncthreads();
@@ -173,19 +174,19 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
             for (int i = tid; i < kBins / 4; i += kThreads) dst[i] = src[i];
         }
 
-        if constexpr (ENC1) enc1_pool<T, kThreads, false>(a, e, tid, shist, senc);
+        if constexpr (ENC1) enc1_pool<T, kThreads, false, C0>(a, e, tid, shist, senc);
         __syncthreads();                   // shist and the sort arrays are reused next event
     }
 }
 
 // Persistent grid: as many CTAs as the shared memory lets reside (at most two per SM,
 // the register limit at 256 threads), capped by the number of events.
-template <int PREC, bool ENC1, bool EDGE>
+template <int PREC, bool ENC1, bool EDGE, int C0>
 cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     static size_t configured = 0;
     static int sms = 0;
     if (smem > configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1, EDGE, C0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         configured = smem;
         int dev = 0;
@@ -198,7 +199,7 @@ cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;
-    k_front<PREC, ENC1, EDGE><<<grid, kThreads, smem, s>>>(a);
+    k_front<PREC, ENC1, EDGE, C0><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -209,15 +210,19 @@ size_t front_smem_bytes(int max_tracks, float edge) { return FrontSmem::total(ma
 cudaError_t launch_front_hist_only(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
     if (a.edge > 0.0f) return cudaErrorInvalidValue;   // the no-allocation path has no boundary tracks
-    return launch_front_t<PVF_FP32, false, false>(a, smem, s);
+    return launch_front_t<PVF_FP32, false, false, kC0>(a, smem, s);
 }
 
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
     // the tensor-core forms run k_front_tc
     if (precision != PVF_FP32) return cudaErrorInvalidValue;
-    return a.edge > 0.0f ? launch_front_t<PVF_FP32, true, true>(a, smem, s)
-                         : launch_front_t<PVF_FP32, true, false>(a, smem, s);
+    if (a.c0 == kC0Max)
+        return a.edge > 0.0f ? launch_front_t<PVF_FP32, true, true, kC0Max>(a, smem, s)
+                             : launch_front_t<PVF_FP32, true, false, kC0Max>(a, smem, s);
+    if (a.c0 != kC0) return cudaErrorInvalidValue;
+    return a.edge > 0.0f ? launch_front_t<PVF_FP32, true, true, kC0>(a, smem, s)
+                         : launch_front_t<PVF_FP32, true, false, kC0>(a, smem, s);
 }
 
 }  // namespace pvf

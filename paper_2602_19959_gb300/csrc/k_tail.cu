@@ -1,4 +1,4 @@
-// End of step 3 and step 4 of the path (§2): the final 16 -> 1 channel k5 convolution
+// End of step 3 and step 4 of the path (§2): the final c0 -> 1 channel k5 convolution
 // (float32 in every form) and heuristic peak finding on its output.
 //
 // A persistent grid of 256-thread CTAs walks the events, one event at a time per CTA:
@@ -25,50 +25,34 @@ constexpr int kPerThread = 16;    // kThreads * kPerThread >= kBins
 // ln(0.01 / 0.99) rounded to float
 constexpr float kThrLogit = -4.59511985013459f;
 
-// Loads the 16 channels of storage row `row` of event e (layouts as in the front kernel:
-// channel-last float32, or plane-major 16-bit / e4m3).
-template <class T>
-__device__ __forceinline__ void load_row16(const void *base, int64_t e, int64_t rows_e, int64_t row,
-                                           float v[kC0], float scale) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 *s = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(base) +
-                                                           (e * rows_e + row) * kC0);
+// Loads channels [16 g, 16 g + 16) of storage row `row` of event e of the channel-last
+// float32 tensor d1 with C0 channels.
+template <int C0>
+__device__ __forceinline__ void load_seg16_f32(const void *base, int64_t e, int64_t rows_e, int64_t row,
+                                               int g, float v[16]) {
+    const float4 *s = reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(base) +
+                                                       (e * rows_e + row) * C0 + 16 * g);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float4 x = s[i];
-            v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
-        }
-    } else if constexpr (sizeof(T) == 2) {
-        const unsigned char *cb = reinterpret_cast<const unsigned char *>(base);
-        uint4 pk[2] = {*reinterpret_cast<const uint4 *>(cb + planar_off(e, 0, 2, rows_e, row)),
-                       *reinterpret_cast<const uint4 *>(cb + planar_off(e, 1, 2, rows_e, row))};
-        const T *b = reinterpret_cast<const T *>(pk);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = from_elem<T>(b[i], 1.0f);
-    } else {
-        const unsigned char *cb = reinterpret_cast<const unsigned char *>(base);
-        uint4 pk = *reinterpret_cast<const uint4 *>(cb + planar_off(e, 0, 1, rows_e, row));
-        const __nv_fp8_e4m3 *b = reinterpret_cast<const __nv_fp8_e4m3 *>(&pk);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = float(b[i]) * scale;
+    for (int i = 0; i < 4; ++i) {
+        float4 x = s[i];
+        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
     }
 }
 
 __device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
 
-// CONV: the logit comes from the final conv over d1 (the float32 form); otherwise it is read
-// from a.logit_in. Without the conv the kernel fits eight CTAs per SM.
-template <int PREC, bool CONV>
+// CONV: the logit comes from the final conv over d1 (the float32 form, base width C0);
+// otherwise it is read from a.logit_in. Without the conv the kernel fits eight CTAs per SM.
+template <bool CONV, int C0>
 __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
-    using T = typename Elem<PREC>::T;
     __shared__ __align__(16) float sf[kThreads * kPerThread];
-    __shared__ float sw[kFinalFloats];
+    __shared__ float sw[kFinalFloatsMax];
     __shared__ int swarp[kThreads / 32];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if constexpr (CONV) {
-        for (int i = tid; i < kFinalFloats; i += kThreads) sw[i] = a.final_w[i];
+        for (int i = tid; i < 5 * C0 + 1; i += kThreads) sw[i] = a.final_w[i];
         __syncthreads();
     }
     // the logits (or d1) are the previous kernel's output (dependent launch)
@@ -83,13 +67,16 @@ __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
         } else {
             const int64_t rows1 = padded_rows(kBins);
             for (int p = tid; p < kBins; p += kThreads) {
-                float acc = sw[5 * kC0];
+                float acc = sw[5 * C0];
 #pragma unroll
                 for (int t = 0; t < 5; ++t) {
-                    float v[kC0];
-                    load_row16<T>(a.d1, e, rows1, p + t, v, a.d1_scale);   // storage row p + t = position p + t - 2
 #pragma unroll
-                    for (int ci = 0; ci < kC0; ++ci) acc = fmaf(sw[t * kC0 + ci], v[ci], acc);
+                    for (int g = 0; g < C0 / 16; ++g) {
+                        float v[16];
+                        load_seg16_f32<C0>(a.d1, e, rows1, p + t, g, v);   // storage row p + t = position p + t - 2
+#pragma unroll
+                        for (int ci = 0; ci < 16; ++ci) acc = fmaf(sw[t * C0 + 16 * g + ci], v[ci], acc);
+                    }
                 }
                 sf[p] = acc;
             }
@@ -189,11 +176,13 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     }
     const int per_sm = a.logit_in ? 8 : 2;
     dim3 grid(a.n_events < per_sm * sms ? a.n_events : per_sm * sms), block(kThreads);
-    if (a.logit_in) return launch_pdl(k_tail<PVF_FP32, false>, grid, block, 0, s, a);
+    if (a.logit_in) return launch_pdl(k_tail<false, kC0>, grid, block, 0, s, a);
     // the final conv runs here in the FP32 form only (the tensor-core forms run it in
     // dec1's epilogue and pass logits)
     if (precision != PVF_FP32) return cudaErrorInvalidValue;
-    k_tail<PVF_FP32, true><<<grid, block, 0, s>>>(a);
+    if (a.c0 == kC0Max) k_tail<true, kC0Max><<<grid, block, 0, s>>>(a);
+    else if (a.c0 == kC0) k_tail<true, kC0><<<grid, block, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

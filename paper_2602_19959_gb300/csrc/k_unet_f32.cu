@@ -22,7 +22,9 @@ namespace {
 
 constexpr int kKC = 16;   // input channels per shared-memory chunk
 
-template <int CA, int CB, int COUT, int TP, bool POOL>
+// KC input channels per shared-memory chunk (8 where 16 would exceed the 48 KB of static
+// shared memory: the wide variant's 128- and 256-channel layers).
+template <int CA, int CB, int COUT, int TP, bool POOL, int KC = kKC>
 __global__ void __launch_bounds__((TP / 8) * (COUT / 8))
 k_conv5_f32(const float *__restrict__ inA, const float *__restrict__ inB,
             const float *__restrict__ W, const float *__restrict__ bias,
@@ -31,9 +33,10 @@ k_conv5_f32(const float *__restrict__ inA, const float *__restrict__ inB,
     constexpr int NCG = COUT / 8, NPG = TP / 8, NT = NCG * NPG;
     constexpr int XR = TP + 4;              // halo'd rows of the tile
     constexpr int XP = TP + 8;              // shared pitch (multiple of 4 floats)
-    static_assert(CA % kKC == 0 && CB % kKC == 0, "channel chunks must not straddle");
-    __shared__ __align__(16) float xs[kKC][XP];
-    __shared__ __align__(16) float ws[5][kKC][COUT];
+    static_assert(CA % KC == 0 && CB % KC == 0 && KC % 4 == 0, "channel chunks must not straddle");
+    constexpr int Q = KC / 4;               // float4 per halo'd row of a chunk
+    __shared__ __align__(16) float xs[KC][XP];
+    __shared__ __align__(16) float ws[5][KC][COUT];
 
     const int tid = threadIdx.x;
     const int cg = tid % NCG, pg = tid / NCG;
@@ -49,14 +52,14 @@ k_conv5_f32(const float *__restrict__ inA, const float *__restrict__ inB,
         for (int pi = 0; pi < 8; ++pi) acc[pi][qi] = b;
     }
 
-    for (int kc = 0; kc < CIN; kc += kKC) {
+    for (int kc = 0; kc < CIN; kc += KC) {
         const bool fromA = kc < CA;
         const int C = fromA ? CA : CB;
         const int coff = fromA ? kc : kc - CA;
         const float *src = (fromA ? inA : inB) + (size_t)e * rowsE * C + coff;
         // tile row r <-> event row p0 - 2 + r <-> storage row p0 + r
-        for (int idx = tid; idx < XR * (kKC / 4); idx += NT) {
-            const int r = idx >> 2, c4 = idx & 3;
+        for (int idx = tid; idx < XR * Q; idx += NT) {
+            const int r = idx / Q, c4 = idx % Q;
             const int64_t srow = (int64_t)p0 + r;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (srow < rowsE) v = *reinterpret_cast<const float4 *>(src + srow * C + 4 * c4);
@@ -65,15 +68,15 @@ k_conv5_f32(const float *__restrict__ inA, const float *__restrict__ inB,
             xs[4 * c4 + 2][r] = v.z;
             xs[4 * c4 + 3][r] = v.w;
         }
-        for (int idx = tid; idx < 5 * kKC * COUT / 4; idx += NT) {
-            const int t = idx / (kKC * COUT / 4), rem = idx % (kKC * COUT / 4);
+        for (int idx = tid; idx < 5 * KC * COUT / 4; idx += NT) {
+            const int t = idx / (KC * COUT / 4), rem = idx % (KC * COUT / 4);
             const int k = rem / (COUT / 4), c4 = rem % (COUT / 4);
             reinterpret_cast<float4 *>(&ws[t][k][0])[c4] =
                 reinterpret_cast<const float4 *>(W + ((size_t)t * CIN + kc + k) * COUT)[c4];
         }
         __syncthreads();
 #pragma unroll 2
-        for (int k = 0; k < kKC; ++k) {
+        for (int k = 0; k < KC; ++k) {
             float xv[12];
             const float4 *xr = reinterpret_cast<const float4 *>(&xs[k][pg * 8]);
 #pragma unroll
@@ -214,11 +217,11 @@ k_convT_f32(const float *__restrict__ in, const float *__restrict__ W,
     }
 }
 
-template <int CA, int CB, int COUT, int TP, bool POOL>
+template <int CA, int CB, int COUT, int TP, bool POOL, int KC = kKC>
 cudaError_t conv5(const void *a, const void *b, const float *W, const float *bias, void *out,
                   void *outp, int L, int n, cudaStream_t s) {
     dim3 grid((L + TP - 1) / TP, n), block((TP / 8) * (COUT / 8));
-    k_conv5_f32<CA, CB, COUT, TP, POOL><<<grid, block, 0, s>>>(
+    k_conv5_f32<CA, CB, COUT, TP, POOL, KC><<<grid, block, 0, s>>>(
         (const float *)a, (const float *)b, W, bias, (float *)out, (float *)outp, L);
     return cudaGetLastError();
 }
@@ -231,25 +234,38 @@ cudaError_t convT(const void *in, const float *W, const float *bias, void *out, 
     return cudaGetLastError();
 }
 
+// The layer sequence for base width C (levels C, 2C, 4C, 8C). Tiles halve as the channel
+// counts double, so every CTA keeps (TP / 8) x (C_out / 8) = 128 threads; in the wide
+// variant the 2C-, 4C- and 8C-input convolutions stage 8 channels per chunk so that their
+// weights fit the 48 KB of static shared memory (enc4 at C = 32: 40 KB).
+template <int C>
+cudaError_t run_f32(const ConvF32Weights &w, const UnetBuffers &b, int n, cudaStream_t s,
+                    const ProfHook *prof) {
+    constexpr int KW = C > kC0 ? 8 : kKC;
+    cudaError_t err;
+#define PVF_TRY(name, x) do { ProfScope ps_(prof, name, s); err = (x); if (err != cudaSuccess) return err; } while (0)
+    // each tensor is packed in its slot with its own per-event stride (L + 4) * C
+    PVF_TRY("enc2", (conv5<C, 0, 2 * C, 256 * 16 / C, true>(b.s0, nullptr, w.w[0], w.b[0], b.e2, b.s1, 2000, n, s)));
+    PVF_TRY("enc3", (conv5<2 * C, 0, 4 * C, 128 * 16 / C, true, KW>(b.s1, nullptr, w.w[1], w.b[1], b.e3, b.s0, 1000, n, s)));
+    PVF_TRY("enc4", (conv5<4 * C, 0, 8 * C, 64 * 16 / C, false, KW>(b.s0, nullptr, w.w[2], w.b[2], b.deep, nullptr, 500, n, s)));
+    PVF_TRY("up3", (convT<8 * C, 4 * C, 64 * 16 / C>(b.deep, w.uw[0], w.ub[0], b.up, 500, n, s)));
+    PVF_TRY("dec3", (conv5<4 * C, 4 * C, 4 * C, 128 * 16 / C, false, KW>(b.up, b.e3, w.w[3], w.b[3], b.deep, nullptr, 1000, n, s)));
+    PVF_TRY("up2", (convT<4 * C, 2 * C, 128 * 16 / C>(b.deep, w.uw[1], w.ub[1], b.up, 1000, n, s)));
+    PVF_TRY("dec2", (conv5<2 * C, 2 * C, 2 * C, 256 * 16 / C, false>(b.up, b.e2, w.w[4], w.b[4], b.deep, nullptr, 2000, n, s)));
+    PVF_TRY("up1", (convT<2 * C, C, 256 * 16 / C>(b.deep, w.uw[2], w.ub[2], b.up, 2000, n, s)));
+    PVF_TRY("dec1", (conv5<C, C, C, 512 * 16 / C, false>(b.up, b.e1, w.w[5], w.b[5], b.deep, nullptr, 4000, n, s)));
+#undef PVF_TRY
+    return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n, cudaStream_t s,
                             const ProfHook *prof) {
     if (n <= 0) return cudaSuccess;
-    cudaError_t err;
-#define PVF_TRY(name, x) do { ProfScope ps_(prof, name, s); err = (x); if (err != cudaSuccess) return err; } while (0)
-    // each tensor is packed in its slot with its own per-event stride (L + 4) * C
-    PVF_TRY("enc2", (conv5<16, 0, 32, 256, true>(b.s0, nullptr, w.w[0], w.b[0], b.e2, b.s1, 2000, n, s)));
-    PVF_TRY("enc3", (conv5<32, 0, 64, 128, true>(b.s1, nullptr, w.w[1], w.b[1], b.e3, b.s0, 1000, n, s)));
-    PVF_TRY("enc4", (conv5<64, 0, 128, 64, false>(b.s0, nullptr, w.w[2], w.b[2], b.deep, nullptr, 500, n, s)));
-    PVF_TRY("up3", (convT<128, 64, 64>(b.deep, w.uw[0], w.ub[0], b.up, 500, n, s)));
-    PVF_TRY("dec3", (conv5<64, 64, 64, 128, false>(b.up, b.e3, w.w[3], w.b[3], b.deep, nullptr, 1000, n, s)));
-    PVF_TRY("up2", (convT<64, 32, 128>(b.deep, w.uw[1], w.ub[1], b.up, 1000, n, s)));
-    PVF_TRY("dec2", (conv5<32, 32, 32, 256, false>(b.up, b.e2, w.w[4], w.b[4], b.deep, nullptr, 2000, n, s)));
-    PVF_TRY("up1", (convT<32, 16, 256>(b.deep, w.uw[2], w.ub[2], b.up, 2000, n, s)));
-    PVF_TRY("dec1", (conv5<16, 16, 16, 512, false>(b.up, b.e1, w.w[5], w.b[5], b.deep, nullptr, 4000, n, s)));
-#undef PVF_TRY
-    return cudaSuccess;
+    if (w.c0 == kC0) return run_f32<kC0>(w, b, n, s, prof);
+    if (w.c0 == kC0Max) return run_f32<kC0Max>(w, b, n, s, prof);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace pvf

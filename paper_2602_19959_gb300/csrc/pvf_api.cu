@@ -40,9 +40,10 @@ struct HostLayer {
     uint32_t shape[3];
 };
 
-// Expected (weight shape, bias length) of layer i for the supported architecture.
-void expected_shape(int i, uint32_t shape[3], uint32_t *nb) {
-    const uint32_t h = kFcHidden, c1 = 16, c2 = 32, c3 = 64, c4 = 128;
+// Expected (weight shape, bias length) of layer i for the supported architecture with
+// UNet base width c0 (16, or 32 for the wide float32 variant).
+void expected_shape(int i, int c0, uint32_t shape[3], uint32_t *nb) {
+    const uint32_t h = kFcHidden, c1 = c0, c2 = 2 * c0, c3 = 4 * c0, c4 = 8 * c0;
     static const uint32_t tbl[kNumLayers][4] = {
         {h, 9, 0, h}, {h, h, 0, h}, {h, h, 0, h}, {h, h, 0, h}, {h, h, 0, h}, {100, h, 0, 100},
         {c1, 1, 5, c1}, {c2, c1, 5, c2}, {c3, c2, 5, c3}, {c4, c3, 5, c4},
@@ -54,11 +55,17 @@ void expected_shape(int i, uint32_t shape[3], uint32_t *nb) {
     *nb = tbl[i][3];
 }
 
-pvf_status parse_blob(const void *blob, size_t bytes, std::vector<HostLayer> &layers) {
+// c0: the base width the blob must have (0: either supported width, returned in *c0_out).
+pvf_status parse_blob(const void *blob, size_t bytes, int c0, std::vector<HostLayer> &layers,
+                      int *c0_out = nullptr) {
     if (!blob || bytes < sizeof(BlobHeader)) return PVF_ERR_WEIGHTS;
     BlobHeader hd;
     std::memcpy(&hd, blob, sizeof hd);
-    if (std::memcmp(hd.magic, "PVFW", 4) != 0 || hd.version != kBlobVersion || hd.c0 != 16 ||
+    if (hd.c0 != (uint32_t)kC0 && hd.c0 != (uint32_t)kC0Max) return PVF_ERR_WEIGHTS;
+    if (c0 && hd.c0 != (uint32_t)c0) return PVF_ERR_WEIGHTS;
+    c0 = (int)hd.c0;
+    if (c0_out) *c0_out = c0;
+    if (std::memcmp(hd.magic, "PVFW", 4) != 0 || hd.version != kBlobVersion ||
         hd.fc_hidden != (uint32_t)kFcHidden || hd.fc_out != (uint32_t)kFcOut ||
         hd.n_layers != (uint32_t)kNumLayers)
         return PVF_ERR_WEIGHTS;
@@ -70,7 +77,7 @@ pvf_status parse_blob(const void *blob, size_t bytes, std::vector<HostLayer> &la
         std::memcpy(&le, base + sizeof(BlobHeader) + i * sizeof(LayerEntry), sizeof le);
         if (strncmp(le.name, kLayerNames[i], 8) != 0) return PVF_ERR_WEIGHTS;
         uint32_t shp[3], nb;
-        expected_shape(i, shp, &nb);
+        expected_shape(i, c0, shp, &nb);
         const uint32_t ndim = shp[2] ? 3 : 2;
         if (le.ndim != ndim || le.shape[0] != shp[0] || le.shape[1] != shp[1] ||
             (ndim == 3 && le.shape[2] != shp[2]) || le.n_bias != nb)
@@ -104,21 +111,21 @@ struct F32Layout {
 const int kConvLayer[6] = {7, 8, 9, 11, 13, 15};    // enc2, enc3, enc4, dec3, dec2, dec1
 const int kUpLayer[3] = {10, 12, 14};               // up3, up2, up1
 
-F32Layout f32_layout() {
+F32Layout f32_layout(int c0) {
     F32Layout L{};
     size_t o = 0;
     auto take = [&](size_t n) { size_t r = o; o += (n + 63) / 64 * 64; return r; };
     L.fc = take(kFcFloats);
-    L.enc1 = take(kEnc1Floats);
-    L.fin = take(kFinalFloats);
+    L.enc1 = take(6 * (size_t)c0);
+    L.fin = take(5 * (size_t)c0 + 1);
     uint32_t shp[3], nb;
     for (int k = 0; k < 6; ++k) {
-        expected_shape(kConvLayer[k], shp, &nb);
+        expected_shape(kConvLayer[k], c0, shp, &nb);
         L.conv_w[k] = take((size_t)shp[0] * shp[1] * 5);
         L.conv_b[k] = take(nb);
     }
     for (int k = 0; k < 3; ++k) {
-        expected_shape(kUpLayer[k], shp, &nb);
+        expected_shape(kUpLayer[k], c0, shp, &nb);
         L.up_w[k] = take((size_t)shp[0] * shp[1] * 2);
         L.up_b[k] = take(nb);
     }
@@ -126,7 +133,7 @@ F32Layout f32_layout() {
     return L;
 }
 
-void fill_f32(const std::vector<HostLayer> &Ls, const F32Layout &L, std::vector<float> &out) {
+void fill_f32(const std::vector<HostLayer> &Ls, const F32Layout &L, int c0, std::vector<float> &out) {
     out.assign(L.total, 0.0f);
     float *fc = out.data() + L.fc;
     for (int l = 0; l < 6; ++l) {
@@ -144,16 +151,16 @@ void fill_f32(const std::vector<HostLayer> &Ls, const F32Layout &L, std::vector<
     {   // enc1 W[co][0][t] -> [t][co]
         const HostLayer &H = Ls[6];
         float *d = out.data() + L.enc1;
-        for (int co = 0; co < kC0; ++co)
-            for (int t = 0; t < 5; ++t) d[t * kC0 + co] = H.w[(size_t)co * 5 + t];
-        for (int co = 0; co < kC0; ++co) d[5 * kC0 + co] = H.b[co];
+        for (int co = 0; co < c0; ++co)
+            for (int t = 0; t < 5; ++t) d[t * c0 + co] = H.w[(size_t)co * 5 + t];
+        for (int co = 0; co < c0; ++co) d[5 * c0 + co] = H.b[co];
     }
     {   // final W[0][ci][t] -> [t][ci]
         const HostLayer &H = Ls[16];
         float *d = out.data() + L.fin;
-        for (int ci = 0; ci < kC0; ++ci)
-            for (int t = 0; t < 5; ++t) d[t * kC0 + ci] = H.w[(size_t)ci * 5 + t];
-        d[5 * kC0] = H.b[0];
+        for (int ci = 0; ci < c0; ++ci)
+            for (int t = 0; t < 5; ++t) d[t * c0 + ci] = H.w[(size_t)ci * 5 + t];
+        d[5 * c0] = H.b[0];
     }
     for (int k = 0; k < 6; ++k) {   // conv W[co][ci][t] -> [t][ci][co]
         const HostLayer &H = Ls[kConvLayer[k]];
@@ -192,8 +199,12 @@ pvf_status check_config(const pvf_config *c) {
     if (c->chunk_events < 0 || c->chunk_events > c->max_events) return PVF_ERR_INVALID_ARG;
     for (int r : c->reserved) if (r != 0) return PVF_ERR_INVALID_ARG;
     if (!(c->boundary_mm >= 0.0f && c->boundary_mm < 5.0f)) return PVF_ERR_INVALID_ARG;
+    if (c->unet_width != 0 && c->unet_width != kC0 && c->unet_width != kC0Max) return PVF_ERR_INVALID_ARG;
+    if (c->unet_width == kC0Max && c->precision != PVF_FP32) return PVF_ERR_UNSUPPORTED;
     return PVF_OK;
 }
+
+int cfg_c0(const pvf_config *c) { return c->unet_width ? c->unet_width : kC0; }
 
 Plan make_plan(const pvf_config *c) {
     Plan p{};
@@ -201,12 +212,14 @@ Plan make_plan(const pvf_config *c) {
     size_t o = 0;
     p.status = o; o += 256;
     p.ev_flag = o; o = align256(o + sizeof(int32_t) * (size_t)c->max_events);
-    p.f32w = o; o = align256(o + sizeof(float) * f32_layout().total);
+    const int c0 = cfg_c0(c);
+    p.f32w = o; o = align256(o + sizeof(float) * f32_layout(c0).total);
     p.tcw = o; o = align256(o + tc_weight_bytes(c->precision));
     p.logits = o; o = align256(o + (c->precision != PVF_FP32 ? sizeof(float) * kBins * (size_t)p.chunk : 0));
     const size_t eb = elem_bytes(c->precision);
-    p.act_slot_big = align256((size_t)p.chunk * kBigElems * eb);
-    p.act_slot_small = align256((size_t)p.chunk * kSmallElems * eb);
+    // every activation tensor scales with the base width
+    p.act_slot_big = align256((size_t)p.chunk * kBigElems * (c0 / kC0) * eb);
+    p.act_slot_small = align256((size_t)p.chunk * kSmallElems * (c0 / kC0) * eb);
     p.act = o; o += 5 * p.act_slot_big + 2 * p.act_slot_small;
     p.total = o + 256;
     return p;
@@ -216,11 +229,12 @@ Plan make_plan(const pvf_config *c) {
 
 pvf_status pack_fc_from_blob(const void *blob, size_t bytes, float *out) {
     std::vector<HostLayer> layers;
-    const pvf_status st = parse_blob(blob, bytes, layers);
+    int c0 = 0;
+    const pvf_status st = parse_blob(blob, bytes, 0, layers, &c0);
     if (st != PVF_OK) return st;
     std::vector<float> f32;
-    const F32Layout L = f32_layout();
-    fill_f32(layers, L, f32);
+    const F32Layout L = f32_layout(c0);
+    fill_f32(layers, L, c0, f32);
     std::memcpy(out, f32.data() + L.fc, sizeof(float) * kFcFloats);
     return PVF_OK;
 }
@@ -261,6 +275,7 @@ struct pvf_handle {
     Plan plan;
     unsigned char *pool;
     size_t front_smem;
+    int c0;                                 // UNet base width
     F32Layout f32;
     ConvF32Weights cw;
     const float *fc, *enc1, *fin;
@@ -307,7 +322,7 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
     if (st != PVF_OK) return st;
     if (!pool || reinterpret_cast<uintptr_t>(pool) % 256) return PVF_ERR_INVALID_ARG;
     std::vector<HostLayer> layers;
-    st = parse_blob(blob, blob_bytes, layers);
+    st = parse_blob(blob, blob_bytes, cfg_c0(cfg), layers);
     if (st != PVF_OK) return st;
     const Plan plan = make_plan(cfg);
     if (pool_bytes < plan.total) return PVF_ERR_POOL_TOO_SMALL;
@@ -321,7 +336,9 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
     h->plan = plan;
     h->pool = static_cast<unsigned char *>(pool);
     h->front_smem = front_smem_bytes(cfg->max_tracks_per_event, cfg->boundary_mm);
-    h->f32 = f32_layout();
+    h->c0 = cfg_c0(cfg);
+    h->f32 = f32_layout(h->c0);
+    h->cw.c0 = h->c0;
     for (int i = 0; i < PVF_N_ACT_SCALES; ++i)
         h->act_scale[i] = cfg->fp8_act_scales ? cfg->fp8_act_scales[i] : 1.0f;
 
@@ -344,7 +361,7 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     std::vector<float> f32;
-    fill_f32(layers, h->f32, f32);
+    fill_f32(layers, h->f32, h->c0, f32);
     std::vector<unsigned char> tcw;
     cudaError_t err = cudaSuccess;
     if (cfg->precision != PVF_FP32) {
@@ -459,6 +476,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.n_events = n;
         a.ev_base = ev_base;
         a.max_tracks = h->cfg.max_tracks_per_event;
+        a.c0 = h->c0;
         a.edge = h->cfg.boundary_mm;
         a.edge_hi = 10.0f - h->cfg.boundary_mm;
         a.fc = h->fc;
@@ -498,6 +516,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         }
         t.d1_scale = h->act_scale[kScaleD1];
         t.final_w = h->fin;
+        t.c0 = h->c0;
         t.n_events = n;
         t.ev_base = ev_base;
         t.logit_out = logit_out;

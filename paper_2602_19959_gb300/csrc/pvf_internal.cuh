@@ -30,6 +30,7 @@ constexpr int kFcHidden = 32;
 constexpr int kFcOut = 100;
 constexpr int kFcInPad = 12;   // layer-1 input padded to a multiple of 4 floats
 constexpr int kC0 = 16;        // UNet base width; levels have 16, 32, 64, 128 channels
+constexpr int kC0Max = 32;     // widest variant (float32 form only): 32, 64, 128, 256
 constexpr int kPad = 2;        // zero rows on each side of an event (k5 "same" padding)
 constexpr float kZLo = -100.0f;
 constexpr float kBinW = 0.1f;
@@ -72,8 +73,10 @@ __host__ __device__ constexpr int fc_img_off(int l) {
 
 // enc1 (1 -> 16, k5) in float32: W[t][co] then b[co].
 constexpr int kEnc1Floats = 5 * kC0 + kC0;
+constexpr int kEnc1FloatsMax = 6 * kC0Max;
 // final (16 -> 1, k5) in float32: W[t][ci] then b.
 constexpr int kFinalFloats = 5 * kC0 + 1;
+constexpr int kFinalFloatsMax = 5 * kC0Max + 1;
 
 // Device status word values are pvf_status codes; kernels raise them with atomicMax
 // (an integer maximum: order-independent).
@@ -169,6 +172,7 @@ struct FrontArgs {
     int32_t n_events;            // events in this launch
     int32_t ev_base;             // global index of the launch's first event
     int32_t max_tracks;          // per-event cap
+    int32_t c0;                  // UNet base width (16, or 32 in the float32 form)
     float edge;                  // boundary-track width in mm (0: every track in one slice)
     float edge_hi;               // 10 - edge, rounded to float
     const float *fc;             // packed FC block (kFcFloats); its biases serve both forms
@@ -185,11 +189,12 @@ struct FrontArgs {
 };
 
 struct TailArgs {
-    const void *d1;              // chunk-local padded [n][4004][16], or null for logit_in
+    const void *d1;              // chunk-local padded [n][4004][c0], or null for logit_in
     const float *logit_in;       // non-null: peaks only, read logits
     int32_t logit_in_base;       // event index of logit_in's first row (0: global rows)
     float d1_scale;              // fp8 only
-    const float *final_w;        // kFinalFloats
+    const float *final_w;        // 5 c0 + 1 floats: W[t][ci], then b
+    int32_t c0;                  // width of d1 (16, or 32 in the float32 form)
     int32_t n_events;
     int32_t ev_base;
     const int32_t *ev_flag;      // nullable (all events valid)
@@ -252,6 +257,7 @@ pvf_status pack_fc_from_blob(const void *blob, size_t bytes, float *out);
 cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s);
 
 struct ConvF32Weights {
+    int c0;                       // base width: 16 or 32
     const float *w[6], *b[6];     // enc2, enc3, enc4, dec3, dec2, dec1: W[5][Cin][Cout]
     const float *uw[3], *ub[3];   // up3, up2, up1: W[Cin][2][Cout]
 };
@@ -259,6 +265,7 @@ struct ConvF32Weights {
 // enc2, enc3, enc4, up3, dec3, up2, dec2, up1, dec1, tail):
 //   big slots (kBigElems per event):   e1 | e2 | e3 | deep = e4, d3, d2, d1 | up = u3, u2, u1
 //   small slots (kSmallElems per event): s0 = p1, p3 | s1 = p2
+// (for base width 16; a width-32 network doubles both)
 // Inside its slot a tensor is packed with its own per-event stride (L + 4) * C, which is
 // never larger than the slot's per-event size.
 constexpr int64_t kBigElems = 504 * 128;    // largest of (L + 4) * C over the big tensors

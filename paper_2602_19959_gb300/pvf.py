@@ -14,7 +14,7 @@ import threading
 
 import numpy as np
 
-from .weights import pack_blob
+from .weights import pack_blob, unet_width
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpvf.so")
@@ -45,7 +45,8 @@ class PvfConfig(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_events", ctypes.c_int32),
                 ("max_tracks_per_event", ctypes.c_int32), ("max_pv_per_event", ctypes.c_int32),
                 ("chunk_events", ctypes.c_int32), ("boundary_mm", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 2), ("fp8_act_scales", ctypes.c_void_p)]
+                ("unet_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+                ("fp8_act_scales", ctypes.c_void_p)]
 
 
 class PvfTracks(ctypes.Structure):
@@ -133,9 +134,10 @@ def _check(code: int, where: str, allow_warn: bool = False):
 
 
 def make_config(precision="fp32", max_events=1, max_tracks_per_event=2048, max_pv_per_event=64,
-                chunk_events=0, fp8_act_scales=None, boundary_mm=0.0):
+                chunk_events=0, fp8_act_scales=None, boundary_mm=0.0, unet_width=0):
     cfg = PvfConfig()
     cfg.boundary_mm = boundary_mm
+    cfg.unet_width = unet_width
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.max_events = max_events
     cfg.max_tracks_per_event = max_tracks_per_event
@@ -219,9 +221,10 @@ class PVFinder:
         import torch
         self.lib = load()
         self.device = torch.device(device or "cuda")
+        # the UNet base width follows the weights (the blob records it too)
         self.cfg, self._keep = make_config(precision, max_events, max_tracks_per_event,
                                            max_pv_per_event, chunk_events, fp8_act_scales,
-                                           boundary_mm)
+                                           boundary_mm, unet_width(weights))
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_pool_bytes_required(ctypes.byref(self.cfg), ctypes.byref(need)),
                "pvf_pool_bytes_required")

@@ -1,7 +1,7 @@
 """Writer of the "PVFW" v1 weight blob that pvf_create reads.
 
 Layout (little endian):
-  header (32 B)   magic "PVFW", u32 version = 1, u32 c0 = 16, u32 fc_hidden = 32,
+  header (32 B)   magic "PVFW", u32 version = 1, u32 c0 (16 or 32), u32 fc_hidden = 32,
                   u32 fc_out = 100, u32 n_layers = 17, u32 reserved[2] = 0
   layer table     17 entries of 48 B, in the order LAYER_ORDER:
                   char name[8], u32 ndim, u32 shape[3], u32 n_bias, u32 pad,
@@ -23,9 +23,14 @@ LAYER_ORDER = ("fc1", "fc2", "fc3", "fc4", "fc5", "fc6",
                "up3", "dec3", "up2", "dec2", "up1", "dec1", "final")
 
 
+def unet_width(weights: dict) -> int:
+    """UNet base width c0 of a weight set: the output channels of enc1."""
+    return int(np.asarray(weights["enc1"][0]).shape[0])
+
+
 def pack_blob(weights: dict) -> bytes:
     """weights: {name: (W, b)} with float32-convertible arrays, all 17 layers."""
-    header = struct.pack("<4s7I", b"PVFW", 1, 16, 32, 100, len(LAYER_ORDER), 0, 0)
+    header = struct.pack("<4s7I", b"PVFW", 1, unet_width(weights), 32, 100, len(LAYER_ORDER), 0, 0)
     table_size = 48 * len(LAYER_ORDER)
     data = bytearray()
     entries = []

@@ -267,3 +267,68 @@ def test_full_size_sampled(lib, weights):
         n = r["count"][e]
         zz = r["z"][e, :n]
         assert np.all(np.diff(zz) > 0) and np.all(zz >= -100) and np.all(zz < 300)
+
+
+# ---------------------------------------------------------------- wide UNet (base width 32)
+# §5's channel-count axis: every UNet level twice as wide (32/64/128/256), four times the
+# MACs. Built in the float32 form; the same bars as the width-16 network.
+
+@pytest.fixture(scope="module")
+def wide_weights():
+    return synth.he_weights(0, bias_std=0.05, c0=32)
+
+
+@pytest.fixture(scope="module")
+def wide_ref(wide_weights):
+    ev = synth.generate_standard(8, 0)
+    return ev, oracle.infer(wide_weights, ev.features, ev.offsets, max_pv=MAX_PV, want_hist=True,
+                            want_logit=True, nthreads=NTHREADS)
+
+
+@pytest.fixture(scope="module")
+def wide_pv(lib, wide_weights):
+    return lib(wide_weights, precision="fp32", max_events=8, max_pv_per_event=MAX_PV)
+
+
+def test_wide_unet_stage_matches_oracle(wide_pv, wide_weights, wide_ref):
+    _, ref = wide_ref
+    h32 = ref["hist"].astype(np.float32)
+    logit = torch.zeros((8, 4000), dtype=torch.float32, device="cuda")
+    wide_pv.stage_unet(torch.from_numpy(h32).cuda(), logit)
+    torch.cuda.synchronize()
+    want = np.stack([oracle.unet(wide_weights, h32[e].astype(np.float64))[0] for e in range(8)])
+    assert_per_bin(logit.cpu().numpy(), want)
+
+
+def test_wide_end_to_end_matches_oracle(wide_pv, wide_ref):
+    ev, ref = wide_ref
+    r = run_full(wide_pv, ev)
+    np.testing.assert_array_equal(r["hist"] == 0, ref["hist"] == 0)
+    assert_per_bin(r["hist"], ref["hist"])
+    assert_per_bin(r["logit"], ref["logit"])
+    eps = max(4 * float(np.max(np.abs(r["logit"] - ref["logit"]))), 1e-6)
+    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"], r["count"], ref["logit"], eps)
+    print("wide fp32 agreement", a, "eps", eps)
+    assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
+    assert wide_pv.device_status() == 0
+
+
+def test_wide_bitwise_reproducible_batch_invariant_and_chunked(lib, wide_pv, wide_weights, wide_ref):
+    ev, _ = wide_ref
+    r1 = run_full(wide_pv, ev)
+    r2 = run_full(wide_pv, ev)
+    rs = run_full(wide_pv, ev.subset(2, 5))
+    chunked = lib(wide_weights, precision="fp32", max_events=8, chunk_events=3, max_pv_per_event=MAX_PV)
+    rc = run_full(chunked, ev)
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(r1[k], r2[k])
+        np.testing.assert_array_equal(rs[k], r1[k][2:5])
+        np.testing.assert_array_equal(rc[k], r1[k])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_wide_unet_tensor_core_forms_unsupported(lib, wide_weights, precision):
+    from paper_2602_19959_gb300.pvf import PvfError, PVF_ERR_UNSUPPORTED
+    with pytest.raises(PvfError) as ei:
+        lib(wide_weights, precision=precision, max_events=4)
+    assert ei.value.code == PVF_ERR_UNSUPPORTED

@@ -57,9 +57,18 @@ def test_pool_bytes_required_and_config_validation(lib):
     chunked = P.pool_bytes_required(precision="fp32", max_events=1000, chunk_events=100)
     assert chunked < fp32 / 5
     assert P.pool_bytes_required(precision="bf16", max_events=1000, boundary_mm=0.5) == bf16
+    # the wide UNet (base width 32): float32 only, twice the activation bytes
+    fp32w = P.pool_bytes_required(precision="fp32", max_events=1000, unet_width=32)
+    assert 1.9 * fp32 < fp32w < 2.1 * fp32
+    assert P.pool_bytes_required(precision="fp32", max_events=1000, unet_width=16) == fp32
+    for prec in ("bf16", "fp16", "fp8"):
+        cfg, _ = P.make_config(precision=prec, max_events=10, unet_width=32)
+        out = ctypes.c_size_t(0)
+        assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
     for bad in (dict(max_events=0), dict(max_tracks_per_event=0), dict(max_tracks_per_event=9000),
                 dict(max_pv_per_event=0), dict(chunk_events=-1), dict(precision=7),
-                dict(boundary_mm=-0.1), dict(boundary_mm=5.0), dict(boundary_mm=float("nan"))):
+                dict(boundary_mm=-0.1), dict(boundary_mm=5.0), dict(boundary_mm=float("nan")),
+                dict(unet_width=24), dict(unet_width=64), dict(unet_width=-16)):
         kw = dict(precision="fp32", max_events=10)
         kw.update(bad)
         cfg, _ = P.make_config(**kw)
@@ -90,6 +99,12 @@ def test_create_rejects_bad_arguments_without_cuda(lib):
     nb = W.pack_blob(wd)
     nbuf = ctypes.create_string_buffer(nb, len(nb))
     assert lib.pvf_create(nbuf, len(nb), 0x10000, 1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == 3
+    # a width-32 blob under a width-16 config (and the reverse): ERR_WEIGHTS, before CUDA
+    wide = W.pack_blob(synth.he_weights(0, c0=32))
+    wbuf = ctypes.create_string_buffer(wide, len(wide))
+    assert lib.pvf_create(wbuf, len(wide), 0x10000, 1 << 34, ctypes.byref(cfg), None, ctypes.byref(h)) == 3
+    cfg32, _ = P.make_config(precision="fp32", max_events=4, unet_width=32)
+    assert lib.pvf_create(buf, len(blob), 0x10000, 1 << 34, ctypes.byref(cfg32), None, ctypes.byref(h)) == 3
     # infer with a null handle
     assert lib.pvf_infer(None, None, None, 1, None, None, None) == 1
     assert lib.pvf_destroy(None) == 0

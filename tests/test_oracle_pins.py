@@ -323,31 +323,33 @@ def test_maxpool_matches_torch():
 
 # ----------------------------------------------------------------- UNet
 
-def test_unet_matches_torch_statement_short_sequence():
-    w = rand_weights(12, 0.2)
+@pytest.mark.parametrize("c0", [16, 32])
+def test_unet_matches_torch_statement_short_sequence(c0):
+    w = rand_weights(12, 0.2, c0=c0)
     x = np.abs(np.random.default_rng(13).normal(0, 5, 256))
     f, p, acts = oracle.unet(w, x, return_acts=True)
     f2, p2 = ref.unet(w, x)
     np.testing.assert_allclose(f, f2, rtol=1e-11, atol=1e-10)
     np.testing.assert_allclose(p, p2, rtol=1e-12, atol=1e-14)
-    assert acts["e4"].shape == (128, 32) and acts["d1"].shape == (16, 256)
+    assert acts["e4"].shape == (8 * c0, 32) and acts["d1"].shape == (c0, 256)
 
 
-def identity_unet_weights(a=0.5, c=-1.0):
+def identity_unet_weights(a=0.5, c=-1.0, c0=16):
     """enc1 = delta on channel 0; dec1 = delta on the skip half's channel 0 with every
     upsampled-path weight 0; final = a * delta + c; everything else 0."""
-    shapes = synth.layer_shapes()
+    shapes = synth.layer_shapes(c0)
     w = {k: (np.zeros(s[0], np.float64), np.zeros(s[1], np.float64)) for k, s in shapes.items()}
     w["enc1"][0][0, 0, 2] = 1.0
-    w["dec1"][0][0, 16 + 0, 2] = 1.0        # concat order [upsampled (0..15), skip (16..31)]
+    w["dec1"][0][0, c0 + 0, 2] = 1.0        # concat order [upsampled (0..c0-1), skip (c0..2c0-1)]
     w["final"][0][0, 0, 2] = a
     w["final"][1][0] = c
     return w
 
 
-def test_unet_identity_closed_form():
+@pytest.mark.parametrize("c0", [16, 32])
+def test_unet_identity_closed_form(c0):
     a, c = 0.5, -1.0
-    w = identity_unet_weights(a, c)
+    w = identity_unet_weights(a, c, c0)
     h = np.random.default_rng(14).normal(0, 3, 4000)
     f, p = oracle.unet(w, h)
     lr = np.where(h > 0, h, 0.01 * h)
