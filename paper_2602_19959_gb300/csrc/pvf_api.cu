@@ -44,7 +44,7 @@ struct HostLayer {
 // UNet base width c0 (16, or 32 for the wide float32 variant).
 void expected_shape(int i, int c0, uint32_t shape[3], uint32_t *nb) {
     const uint32_t h = kFcHidden, c1 = c0, c2 = 2 * c0, c3 = 4 * c0, c4 = 8 * c0;
-    static const uint32_t tbl[kNumLayers][4] = {
+    const uint32_t tbl[kNumLayers][4] = {          // built per call: it depends on c0
         {h, 9, 0, h}, {h, h, 0, h}, {h, h, 0, h}, {h, h, 0, h}, {h, h, 0, h}, {100, h, 0, 100},
         {c1, 1, 5, c1}, {c2, c1, 5, c2}, {c3, c2, 5, c3}, {c4, c3, 5, c4},
         {c4, c3, 2, c3}, {c3, 2 * c3, 5, c3}, {c3, c2, 2, c2}, {c2, 2 * c2, 5, c2},

@@ -105,6 +105,10 @@ def test_create_rejects_bad_arguments_without_cuda(lib):
     assert lib.pvf_create(wbuf, len(wide), 0x10000, 1 << 34, ctypes.byref(cfg), None, ctypes.byref(h)) == 3
     cfg32, _ = P.make_config(precision="fp32", max_events=4, unet_width=32)
     assert lib.pvf_create(buf, len(blob), 0x10000, 1 << 34, ctypes.byref(cfg32), None, ctypes.byref(h)) == 3
+    # a valid blob of either width, in any order, parses: with a pool too small, create
+    # stops at POOL_TOO_SMALL (after the blob checks, before any CUDA call)
+    for b, c in ((buf, cfg), (wbuf, cfg32), (buf, cfg), (wbuf, cfg32)):
+        assert lib.pvf_create(b, len(b.raw), 0x10000, 1024, ctypes.byref(c), None, ctypes.byref(h)) == 2
     # infer with a null handle
     assert lib.pvf_infer(None, None, None, 1, None, None, None) == 1
     assert lib.pvf_destroy(None) == 0
