@@ -861,7 +861,7 @@ template <int PREC> struct Net {
                         is16(PREC) ? 2 : 4, 96, 4>;                                  // 1
     using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4, conv_paired(3, PREC)>; // 1 CTA/SM
     using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4, conv_paired(4, PREC)>; // 2
-    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 4, 1, 80, 4, conv_paired(5, PREC)>; // 4
+    using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 3, 1, 64, 4, conv_paired(5, PREC)>; // 5
 };
 
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
