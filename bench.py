@@ -117,7 +117,6 @@ def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_laun
 # that capture has no entry and reports null.
 NCU_TRAFFIC = {
     ("bf16", "dec3_up2", 1000): (131.772416e6 + 27.987456e6) * 1000 / 512,
-    ("bf16", "dec1_final", 1000): (131.240704e6 + 4.577280e6) * 1000 / 512,
     ("bf16", "dec2_up1", 1000): (131.400960e6 + 28.645632e6) * 1000 / 512,
 }
 

@@ -172,3 +172,24 @@ def test_tensor_core_forms_against_oracle(PVFinder, weights, ev16, ref16, precis
     print(f"{precision} boundary: hist err {he:.2e} logit err {le:.2e} agreement {a}")
     assert he <= hist_tol and le <= logit_tol
     assert a["max_dz"] <= 0.1 and a["exempt"] >= 0.999
+
+
+def test_fp8_form_against_oracle(PVFinder, weights, ev16, ref16):
+    """FP8: the FC runs on bf16 operands (histogram bound as BF16), the UNet in e4m3 with
+    calibrated scales (logit bound 20% of the maximum, as without boundary tracks)."""
+    cal = synth.generate_standard(512, 1)
+    pc = PVFinder(weights, precision="bf16", max_events=512, max_pv_per_event=8)
+    feats, offs = to_cuda(cal)
+    scales = pc.calibrate(feats, offs)
+    pc.close()
+    pv = PVFinder(weights, precision="fp8", max_events=16, max_pv_per_event=MAX_PV,
+                  fp8_act_scales=scales, boundary_mm=EDGE)
+    r = run_full(pv, ev16)
+    np.testing.assert_array_equal(r["hist"] == 0, ref16["hist"] == 0)
+    he, le = rel_err(r["hist"], ref16["hist"]), rel_err(r["logit"], ref16["logit"])
+    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    print(f"fp8 boundary: hist err {he:.2e} logit err {le:.2e} agreement {a}")
+    assert he <= 3e-2 and le <= 0.2
+    assert a["max_dz"] <= 0.1 and a["exempt"] >= 0.999
+    assert pv.device_status() == 0

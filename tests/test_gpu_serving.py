@@ -65,14 +65,17 @@ def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, pr
     g.close()
 
 
-@pytest.mark.parametrize("graphs,max_batch,inflight", [(True, 32, 3), (True, 24, 1), (False, 32, 2)])
-def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, max_batch, inflight):
+@pytest.mark.parametrize("graphs,max_batch,inflight,precision",
+                         [(True, 32, 3, "bf16"), (True, 24, 1, "bf16"), (False, 32, 2, "bf16"),
+                          (True, 32, 2, "fp16")])
+def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, max_batch, inflight,
+                                                    precision):
     """Per-bucket graphs (a batch of k events runs the graph of the next bucket with the
     missing events empty; 24 is a bucket of its own) and stream launches give every
     request the result it has alone."""
     store = synth.generate_uneven(40, 21)
     max_pv = 96
-    pv = PVFinder(weights, precision="bf16", max_events=32, max_pv_per_event=max_pv)
+    pv = PVFinder(weights, precision=precision, max_events=32, max_pv_per_event=max_pv)
     rng = np.random.default_rng(5)
     n = 300
     arrivals = np.cumsum(rng.exponential(1e9 / 60000.0, n)).astype(np.int64)   # 60k events/s
