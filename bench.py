@@ -116,8 +116,9 @@ def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_laun
 # events (traffic grows with the events). Keyed by (form, kernel, events per launch). A kernel changed since
 # that capture has no entry and reports null.
 NCU_TRAFFIC = {
-    ("bf16", "dec3_up2", 1000): (131.772416e6 + 27.987456e6) * 1000 / 512,
-    ("bf16", "dec2_up1", 1000): (131.400960e6 + 28.645632e6) * 1000 / 512,
+    ("bf16", "dec3_up2", 1000): (131.740160e6 + 28.147712e6) * 1000 / 512,
+    ("bf16", "dec1_final", 1000): (131.237888e6 + 4.603136e6) * 1000 / 512,
+    ("bf16", "dec2_up1", 1000): (131.397376e6 + 28.666624e6) * 1000 / 512,
 }
 
 
