@@ -474,7 +474,6 @@ template <class C, int NC>
 __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
                                          const float *scs, uint32_t dcol, int c_beg, int ab, int e,
                                          int p, int m, bool valid, const float *sx = nullptr) {
-    constexpr int ES = C::ES;
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad;
     constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
 #pragma unroll 1
@@ -528,7 +527,6 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
 template <class C, int NC>
 __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, const float *scs2,
                                        uint32_t dcol, int n_beg, int e, int p, bool valid, bool pads) {
-    constexpr int ES = C::ES;
     constexpr int LO = 2 * C::L;
     constexpr int64_t ROWS_O = LO + 2 * kPad;
     constexpr int PUP = C::CUP / C::PW;
