@@ -1,0 +1,60 @@
+"""The benchmark's algorithmic bookkeeping (the numerators of its roofline fractions),
+checked against independent derivations: MACs from the layer shapes of the weight
+generator, and FC evaluations from the oracle's own second-slice rule."""
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import synth
+
+# positions at which each layer's output is computed (L of the output) and its kernel taps
+LAYER_L = {"enc1": 4000, "enc2": 2000, "enc3": 1000, "enc4": 500, "dec3": 1000,
+           "dec2": 2000, "dec1": 4000, "final": 4000}
+CONVT_LIN = {"up3": 500, "up2": 1000, "up1": 2000}
+
+
+def unet_macs_from_shapes(c0):
+    shapes = synth.layer_shapes(c0)
+    total = 0
+    for name, L in LAYER_L.items():
+        cout, cin, k = shapes[name][0]
+        total += L * cout * cin * k
+    for name, lin in CONVT_LIN.items():
+        cin, cout, k = shapes[name][0]
+        total += lin * cin * cout * k            # each input position feeds k = 2 outputs
+    return total
+
+
+@pytest.mark.parametrize("c0", [16, 32])
+def test_fp32_kernel_table_macs_equal_the_layer_shapes(c0):
+    t = bench.kernel_table("fp32", c0)
+    assert sum(v[0] for v in t.values()) == unet_macs_from_shapes(c0)
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp8"])
+def test_tensor_core_kernel_table_covers_the_same_macs(form):
+    t = bench.kernel_table(form, 16)
+    assert sum(v[0] for v in t.values()) == unet_macs_from_shapes(16)
+    assert unet_macs_from_shapes(16) == 122_496_000          # 245 MFLOP per event
+
+
+def test_activation_bytes_scale_with_the_element_size():
+    b16 = sum(v[2] for v in bench.kernel_table("bf16").values())
+    b8 = sum(v[2] for v in bench.kernel_table("fp8").values())
+    # everything but the float32 logits (16 KB read by the tail, written by dec1_final)
+    assert b16 - 32000 == 2 * (b8 - 32000)
+
+
+def test_fc_evaluations_follow_the_oracle_second_slice_rule():
+    b = synth.generate_standard(40, 3)
+    z = b.features[2]
+    for edge in (0.0, 0.5, 1.0):
+        want = b.n_tracks
+        for zi in z:
+            s = oracle.slice_index(zi)[0]
+            if s >= 0 and oracle.second_slice(zi, s, edge) >= 0:
+                want += 1
+        assert bench.fc_evaluations(b, edge) == want
+    assert bench.fc_evaluations(b, 0.5) > b.n_tracks
