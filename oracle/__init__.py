@@ -99,7 +99,9 @@ def _load():
                                      ctypes.c_double, I, P, P]
         lib.oracle_peaks.restype = I
         lib.oracle_infer.argtypes = [P, P, ctypes.c_int64, I, I, ctypes.POINTER(OracleWeights),
-                                     P, P, P, P, P, P, I, ctypes.c_double, ctypes.c_float, I]
+                                     P, P, P, P, P, P, I, ctypes.c_double, ctypes.c_float, I, I]
+        lib.oracle_unet_intervals.argtypes = [ctypes.POINTER(OracleWeights), P, P, P]
+        lib.oracle_unet_intervals.restype = I
         lib.oracle_infer.restype = I
         _lib = lib
         return lib
@@ -239,6 +241,19 @@ def unet(weights, hist, return_acts: bool = False):
     return (logit, prob, acts) if return_acts else (logit, prob)
 
 
+def unet_intervals(weights, hist):
+    """(logit, prob) [4000] of one event in the per-interval layout."""
+    lib = _load()
+    w = _as_weights(weights)
+    hist = _f64(hist).reshape(-1)
+    assert hist.shape[0] == NBINS
+    logit = np.zeros(NBINS, dtype=np.float64)
+    prob = np.zeros(NBINS, dtype=np.float64)
+    if lib.oracle_unet_intervals(ctypes.byref(w.struct), _ptr(hist), _ptr(logit), _ptr(prob)) != 0:
+        raise RuntimeError("oracle_unet_intervals failed")
+    return logit, prob
+
+
 def threshold_logit(thr: float = THRESHOLD) -> float:
     """The probability threshold thr expressed on the logit: ln(thr / (1 - thr))."""
     return float(np.log(thr / (1.0 - thr)))
@@ -266,10 +281,11 @@ def peaks(logit, prob=None, thr: float = THRESHOLD, hw: int = 5, hc: int = 3,
 def infer(weights, features: np.ndarray, offsets: np.ndarray, max_pv: int = 64,
           max_tracks_per_event: int = 1 << 30, want_hist: bool = False,
           want_logit: bool = False, want_prob: bool = False, nthreads: int = 1,
-          thr: float = THRESHOLD, edge_mm: float = 0.0):
+          thr: float = THRESHOLD, edge_mm: float = 0.0, per_interval: bool = False):
     """Whole-pipeline oracle over a batch. Returns a dict with pv_z [n, max_pv],
     pv_count [n] (-1 = bypassed event), n_dropped [n], and optionally hist / logit /
-    prob ([n, 4000] each). edge_mm: boundary-track width (0 = none)."""
+    prob ([n, 4000] each). edge_mm: boundary-track width (0 = none). per_interval: the
+    UNet runs on each of the 40 intervals as its own 104-bin sequence."""
     lib = _load()
     w = _as_weights(weights)
     features, ptrs = _feature_ptrs(features)
@@ -284,7 +300,7 @@ def infer(weights, features: np.ndarray, offsets: np.ndarray, max_pv: int = 64,
     rc = lib.oracle_infer(ptrs, _ptr(offsets), features.shape[1], n, max_tracks_per_event,
                           ctypes.byref(w.struct), _ptr(hist), _ptr(logit), _ptr(prob), _ptr(pv_z),
                           _ptr(pv_count), _ptr(n_drop), max_pv, thr, ctypes.c_float(edge_mm),
-                          nthreads)
+                          int(per_interval), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_infer failed ({rc})")
     out = {"pv_z": pv_z, "pv_count": pv_count, "n_dropped": n_drop}

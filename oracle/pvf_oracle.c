@@ -328,6 +328,29 @@ int oracle_peaks(const double *f, const double *p, int L, double thr_logit, int 
     return n;
 }
 
+/* Per-interval layout (§3: the CNN input has a batch dimension of 40 spatial intervals):
+ * each interval runs the UNet as its own sequence of OR_IV_LEN bins -- its 100 bins with
+ * OR_IV_PAD zero bins on each side, the fewest that survive three 2:1 poolings -- and its
+ * 100 central logits become bins [100 s, 100 s + 100) of the event's logits. prob (may be
+ * NULL) receives sigmoid of the assembled logits. Returns 0, or -2 when out of memory. */
+#define OR_IV_PAD 2
+#define OR_IV_LEN (OR_SLICE_BINS + 2 * OR_IV_PAD)
+int oracle_unet_intervals(const oracle_weights *w, const double *hist, double *logit, double *prob)
+{
+    double xw[OR_IV_LEN], fw[OR_IV_LEN];
+    for (int s = 0; s < OR_NSLICES; ++s) {
+        for (int j = 0; j < OR_IV_LEN; ++j) {
+            const int b = j - OR_IV_PAD;
+            xw[j] = (b >= 0 && b < OR_SLICE_BINS) ? hist[s * OR_SLICE_BINS + b] : 0.0;
+        }
+        if (oracle_unet(w, xw, OR_IV_LEN, fw, NULL, NULL) != 0) return -2;
+        for (int b = 0; b < OR_SLICE_BINS; ++b) logit[s * OR_SLICE_BINS + b] = fw[OR_IV_PAD + b];
+    }
+    if (prob)
+        for (int i = 0; i < OR_NBINS; ++i) prob[i] = sigmoid(logit[i]);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ whole event */
 
 typedef struct {
@@ -344,6 +367,7 @@ typedef struct {
     int max_pv;
     double thr;
     float edge;
+    int per_interval;
     int tid, nthreads;
     int rc;
 } infer_job;
@@ -368,7 +392,9 @@ static void *infer_worker(void *arg)
         }
         int drop = oracle_event_histogram(j->feats, a, b, j->w, j->edge, hist);
         if (j->n_dropped) j->n_dropped[e] = drop;
-        if (oracle_unet(j->w, hist, OR_NBINS, logit, prob, NULL) != 0) { j->rc = -2; break; }
+        const int rc = j->per_interval ? oracle_unet_intervals(j->w, hist, logit, prob)
+                                       : oracle_unet(j->w, hist, OR_NBINS, logit, prob, NULL);
+        if (rc != 0) { j->rc = -2; break; }
         j->pv_count[e] = oracle_peaks(logit, prob, OR_NBINS, thr_logit, 5, 3, OR_Z_LO, OR_BIN_W,
                                       j->max_pv, j->pv_z + (size_t)e * j->max_pv, NULL);
         if (j->hist_out) memcpy(j->hist_out + (size_t)e * OR_NBINS, hist, sizeof(double) * OR_NBINS);
@@ -381,12 +407,14 @@ static void *infer_worker(void *arg)
 
 /* Full inference over a batch of events, statically round-robin over nthreads threads
  * (nthreads <= 1 runs on the calling thread); edge is the boundary-track width in mm
- * (oracle_second_slice, 0 = none). Returns 0 on success. */
+ * (oracle_second_slice, 0 = none); per_interval selects the per-interval UNet layout
+ * (oracle_unet_intervals). Returns 0 on success. */
 int oracle_infer(const float *const feats[9], const int32_t *offsets, int64_t n_tracks_total,
                  int n_events, int max_tracks_per_event, const oracle_weights *w,
                  double *hist_out, double *logit_out, double *prob_out, double *pv_z,
                  int32_t *pv_count,
-                 int32_t *n_dropped, int max_pv, double thr, float edge, int nthreads)
+                 int32_t *n_dropped, int max_pv, double thr, float edge, int per_interval,
+                 int nthreads)
 {
     if (n_events < 0 || max_pv < 0 || !w || (n_events > 0 && (!offsets || !pv_z || !pv_count)))
         return -1;
@@ -401,7 +429,8 @@ int oracle_infer(const float *const feats[9], const int32_t *offsets, int64_t n_
         j->feats = feats; j->offsets = offsets; j->n_tracks_total = n_tracks_total;
         j->n_events = n_events; j->max_tracks_per_event = max_tracks_per_event; j->w = w;
         j->hist_out = hist_out; j->logit_out = logit_out; j->prob_out = prob_out; j->pv_z = pv_z; j->pv_count = pv_count;
-        j->n_dropped = n_dropped; j->max_pv = max_pv; j->thr = thr; j->edge = edge; j->tid = t;
+        j->n_dropped = n_dropped; j->max_pv = max_pv; j->thr = thr; j->edge = edge;
+        j->per_interval = per_interval; j->tid = t;
         j->nthreads = nthreads; j->rc = 0;
     }
     int rc = 0;

@@ -482,3 +482,60 @@ def test_fp16_rounding_emulation_against_binary16():
     got = ref.q_fp16(x).tolist()
     assert got == want
     assert math.isnan(ref.q_fp16(torch.tensor([float("nan")], dtype=torch.float64)).item())
+
+
+# ----------------------------------------------------------------- per-interval layout (§3)
+# Each interval runs the UNet as its own 104-bin sequence (its 100 bins, two zero bins on
+# each side); its 100 central logits fill the interval's bins of the event.
+
+def test_per_interval_identity_closed_form():
+    """The identity network is pointwise, so every layout must give its closed form; a
+    window offset off by one bin would shift the values."""
+    a, c = 0.5, -1.0
+    w = identity_unet_weights(a, c)
+    h = np.random.default_rng(21).normal(0, 3, 4000)
+    f, p = oracle.unet_intervals(w, h)
+    lr = np.where(h > 0, h, 0.01 * h)
+    lr2 = np.where(lr > 0, lr, 0.01 * lr)
+    np.testing.assert_allclose(f, a * lr2 + c, rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(p, 1.0 / (1.0 + np.exp(-f)), rtol=1e-15)
+
+
+def test_per_interval_matches_torch_statement_on_each_window():
+    w = rand_weights(22, 0.2)
+    h = np.abs(np.random.default_rng(23).normal(0, 5, 4000))
+    f, _ = oracle.unet_intervals(w, h)
+    for s in (0, 7, 39):
+        win = np.concatenate([np.zeros(2), h[100 * s:100 * s + 100], np.zeros(2)])
+        fw, _ = ref.unet(w, win)
+        np.testing.assert_allclose(f[100 * s:100 * s + 100], fw[2:102], rtol=1e-11, atol=1e-10)
+
+
+def test_per_interval_intervals_are_independent():
+    w = rand_weights(24, 0.2)
+    rng = np.random.default_rng(25)
+    h = np.abs(rng.normal(0, 5, 4000))
+    f0, _ = oracle.unet_intervals(w, h)
+    h2 = h.copy()
+    h2[1200:1300] = np.abs(rng.normal(0, 5, 100))        # interval 12 only
+    f1, _ = oracle.unet_intervals(w, h2)
+    changed = np.nonzero(f0 != f1)[0]
+    assert changed.size > 0 and changed.min() >= 1200 and changed.max() < 1300
+    # the whole-sequence network, by contrast, sees across the interval edges
+    g0, _ = oracle.unet(w, h)
+    g1, _ = oracle.unet(w, h2)
+    changed = np.nonzero(g0 != g1)[0]
+    assert changed.min() < 1200 and changed.max() >= 1300
+
+
+def test_per_interval_infer_uses_the_assembled_logits():
+    w = rand_weights(26, 0.1)
+    ev = synth.generate_standard(3, 27)
+    r = oracle.infer(w, ev.features, ev.offsets, max_pv=672, want_hist=True, want_logit=True,
+                     per_interval=True)
+    for e in range(3):
+        f, _ = oracle.unet_intervals(w, r["hist"][e])
+        np.testing.assert_array_equal(r["logit"][e], f)
+        n, z, _ = oracle.peaks(f, max_pv=672)    # weights via numpy's exp: z to the last ulp
+        assert r["pv_count"][e] == n
+        np.testing.assert_allclose(r["pv_z"][e, :n], z, rtol=0, atol=1e-12)
