@@ -94,7 +94,12 @@ typedef struct {
                                       (tensor-core forms: UNSUPPORTED). Must match the
                                       blob's width (else pvf_create returns ERR_WEIGHTS).
                                       Other values: INVALID_ARG.                            */
-    int32_t reserved[1];           /* must be 0                                             */
+    int32_t per_interval;          /* 0: the UNet runs over each event's 4000 bins. 1: the
+                                      §3 per-interval layout -- each of the 40 intervals runs
+                                      as its own 104-bin sequence (its 100 bins and two zero
+                                      bins on each side) and its 100 central logits fill the
+                                      interval's bins. PVF_FP32 with width 16 only (other
+                                      forms: UNSUPPORTED). Other values: INVALID_ARG.       */
     const float *fp8_act_scales;   /* host, PVF_FP8_E4M3 only: PVF_N_ACT_SCALES per-tensor
                                       input scales (amax / 448), or NULL to use
                                       pvf_calibrate before the first pvf_infer              */

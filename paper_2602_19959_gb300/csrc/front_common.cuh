@@ -319,6 +319,61 @@ __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, in
     }
 }
 
+// Step f in the per-interval layout (float32 form): e1 and p1 hold kSlices sequences per
+// event (sequence e * kSlices + s = interval s), each the conv of the interval's kIvLen-bin
+// window -- the interval's bins with kIvPad zero bins on each side -- with zero padding
+// beyond the window, as each interval runs the UNet on its own. Same arithmetic per
+// position as enc1_pool_shared_t.
+template <int NT, int C0>
+__device__ __forceinline__ void enc1_pool_windows_f32(const FrontArgs &a, int e, int tid, const float *shist,
+                                                      const float *senc) {
+    constexpr int Q = kIvLen / 2;                 // position pairs per window
+    const int64_t rows1 = padded_rows(kIvLen), rows2 = padded_rows(kIvLen / 2);
+    for (int idx = tid; idx < kSlices * Q; idx += NT) {
+        const int s = idx / Q, q = idx % Q;
+        const int64_t seq = (int64_t)e * kSlices + s;
+        float hv[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int b = 2 * q + k - 2 - kIvPad;     // bin of the interval at window position 2q + k - 2
+            hv[k] = (b >= 0 && b < kSliceBins) ? shist[s * kSliceBins + b] : 0.0f;
+        }
+#pragma unroll 1
+        for (int g = 0; g < C0 / 16; ++g) {
+            float v0[16], v1[16], vp[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int co = 16 * g + j;
+                float a0 = senc[5 * C0 + co], a1 = a0;
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    a0 = fmaf(senc[t * C0 + co], hv[t], a0);
+                    a1 = fmaf(senc[t * C0 + co], hv[t + 1], a1);
+                }
+                v0[j] = leaky(a0);
+                v1[j] = leaky(a1);
+                vp[j] = fmaxf(v0[j], v1[j]);
+            }
+            store_seg16_f32<C0>(a.e1, seq, rows1, 2 * q + kPad, g, v0);
+            store_seg16_f32<C0>(a.e1, seq, rows1, 2 * q + 1 + kPad, g, v1);
+            store_seg16_f32<C0>(a.p1, seq, rows2, q + kPad, g, vp);
+        }
+    }
+    // the pad rows of every window: 0, 1 and L + 2, L + 3
+    float z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = 0.0f;
+    for (int idx = tid; idx < kSlices * 4; idx += NT) {
+        const int s = idx >> 2, k = idx & 3;
+        const int64_t seq = (int64_t)e * kSlices + s;
+        const int r = k < 2 ? k : kIvLen + k, rp = k < 2 ? k : kIvLen / 2 + k;
+        for (int g = 0; g < C0 / 16; ++g) {
+            store_seg16_f32<C0>(a.e1, seq, rows1, r, g, z);
+            store_seg16_f32<C0>(a.p1, seq, rows2, rp, g, z);
+        }
+    }
+}
+
 // REGW: weights in registers (tensor-core front, width 16) or read from shared memory
 // (float32 front, width C0).
 template <class T, int NT, bool REGW = true, int C0 = kC0>

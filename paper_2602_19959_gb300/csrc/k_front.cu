@@ -96,7 +96,8 @@ __device__ __forceinline__ void fc_hidden(const float *__restrict__ W, const flo
 // ENC1 = false: steps a-e only (the histogram), nothing written to e1/p1.
 // EDGE: boundary tracks fill a second slice (a.edge > 0).
 // C0: UNet base width of the e1 / p1 tensors written here (16, or 32 in this float32 form).
-template <int PREC, bool ENC1, bool EDGE, int C0>
+// IV: e1 / p1 in the per-interval layout (kSlices windowed sequences per event).
+template <int PREC, bool ENC1, bool EDGE, int C0, bool IV = false>
 __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
     using T = typename Elem<PREC>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -174,19 +175,20 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
             for (int i = tid; i < kBins / 4; i += kThreads) dst[i] = src[i];
         }
 
-        if constexpr (ENC1) enc1_pool<T, kThreads, false, C0>(a, e, tid, shist, senc);
+        if constexpr (ENC1 && IV) enc1_pool_windows_f32<kThreads, C0>(a, e, tid, shist, senc);
+        else if constexpr (ENC1) enc1_pool<T, kThreads, false, C0>(a, e, tid, shist, senc);
         __syncthreads();                   // shist and the sort arrays are reused next event
     }
 }
 
 // Persistent grid: as many CTAs as the shared memory lets reside (at most two per SM,
 // the register limit at 256 threads), capped by the number of events.
-template <int PREC, bool ENC1, bool EDGE, int C0>
+template <int PREC, bool ENC1, bool EDGE, int C0, bool IV = false>
 cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     static size_t configured = 0;
     static int sms = 0;
     if (smem > configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1, EDGE, C0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1, EDGE, C0, IV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         configured = smem;
         int dev = 0;
@@ -199,7 +201,7 @@ cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;
-    k_front<PREC, ENC1, EDGE, C0><<<grid, kThreads, smem, s>>>(a);
+    k_front<PREC, ENC1, EDGE, C0, IV><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -217,6 +219,11 @@ cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem, cudaStr
     if (a.n_events <= 0) return cudaSuccess;
     // the tensor-core forms run k_front_tc
     if (precision != PVF_FP32) return cudaErrorInvalidValue;
+    if (a.iv) {   // per-interval layout: width 16
+        if (a.c0 != kC0) return cudaErrorInvalidValue;
+        return a.edge > 0.0f ? launch_front_t<PVF_FP32, true, true, kC0, true>(a, smem, s)
+                             : launch_front_t<PVF_FP32, true, false, kC0, true>(a, smem, s);
+    }
     if (a.c0 == kC0Max)
         return a.edge > 0.0f ? launch_front_t<PVF_FP32, true, true, kC0Max>(a, smem, s)
                              : launch_front_t<PVF_FP32, true, false, kC0Max>(a, smem, s);

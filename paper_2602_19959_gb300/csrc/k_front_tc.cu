@@ -333,7 +333,7 @@ cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    if (a.c0 != kC0) return cudaErrorInvalidValue;     // tensor-core forms: width 16 only
+    if (a.c0 != kC0 || a.iv) return cudaErrorInvalidValue;   // tensor-core forms: width 16, whole events
     switch (precision) {
     case PVF_BF16: return launch_front_tc_t<PVF_BF16>(a, s);
     case PVF_FP16: return launch_front_tc_t<PVF_FP16>(a, s);

@@ -43,7 +43,9 @@ __device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf
 
 // CONV: the logit comes from the final conv over d1 (the float32 form, base width C0);
 // otherwise it is read from a.logit_in. Without the conv the kernel fits eight CTAs per SM.
-template <bool CONV, int C0>
+// IV: d1 is in the per-interval layout; bin 100 s + j is position j + kIvPad of interval
+// s's sequence.
+template <bool CONV, int C0, bool IV = false>
 __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
     __shared__ __align__(16) float sf[kThreads * kPerThread];
     __shared__ float sw[kFinalFloatsMax];
@@ -65,15 +67,18 @@ __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
             const float *src = a.logit_in + (size_t)(ge - a.logit_in_base) * kBins;
             for (int p = tid; p < kBins; p += kThreads) sf[p] = src[p];
         } else {
-            const int64_t rows1 = padded_rows(kBins);
+            const int64_t rows1 = padded_rows(IV ? kIvLen : kBins);
             for (int p = tid; p < kBins; p += kThreads) {
                 float acc = sw[5 * C0];
+                // sequence and position of bin p (storage row x + t = position x + t - 2)
+                const int64_t seq = IV ? (int64_t)e * kSlices + p / kSliceBins : e;
+                const int x = IV ? p % kSliceBins + kIvPad : p;
 #pragma unroll
                 for (int t = 0; t < 5; ++t) {
-#pragma unroll
+#pragma unroll 1
                     for (int g = 0; g < C0 / 16; ++g) {
                         float v[16];
-                        load_seg16_f32<C0>(a.d1, e, rows1, p + t, g, v);   // storage row p + t = position p + t - 2
+                        load_seg16_f32<C0>(a.d1, seq, rows1, x + t, g, v);
 #pragma unroll
                         for (int ci = 0; ci < 16; ++ci) acc = fmaf(sw[t * C0 + 16 * g + ci], v[ci], acc);
                     }
@@ -180,7 +185,10 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     // the final conv runs here in the FP32 form only (the tensor-core forms run it in
     // dec1's epilogue and pass logits)
     if (precision != PVF_FP32) return cudaErrorInvalidValue;
-    if (a.c0 == kC0Max) k_tail<true, kC0Max><<<grid, block, 0, s>>>(a);
+    if (a.iv) {
+        if (a.c0 != kC0) return cudaErrorInvalidValue;
+        k_tail<true, kC0, true><<<grid, block, 0, s>>>(a);
+    } else if (a.c0 == kC0Max) k_tail<true, kC0Max><<<grid, block, 0, s>>>(a);
     else if (a.c0 == kC0) k_tail<true, kC0><<<grid, block, 0, s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();

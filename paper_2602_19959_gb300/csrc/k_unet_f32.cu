@@ -258,11 +258,37 @@ cudaError_t run_f32(const ConvF32Weights &w, const UnetBuffers &b, int n, cudaSt
     return cudaSuccess;
 }
 
+// The per-interval layout: kSlices sequences of kIvLen bins per event (104, 52, 26, 13
+// positions per level), each layer one small tile per sequence (32 threads per CTA).
+template <int C>
+cudaError_t run_f32_iv(const ConvF32Weights &w, const UnetBuffers &b, int n, cudaStream_t s,
+                       const ProfHook *prof) {
+    constexpr int L1 = kIvLen, L2 = L1 / 2, L3 = L1 / 4, L4 = L1 / 8;
+    const int ns = n * kSlices;                  // at most 64000 (the plan caps the chunk)
+    cudaError_t err;
+#define PVF_TRY(name, x) do { ProfScope ps_(prof, name, s); err = (x); if (err != cudaSuccess) return err; } while (0)
+    PVF_TRY("enc2", (conv5<C, 0, 2 * C, 64, true>(b.s0, nullptr, w.w[0], w.b[0], b.e2, b.s1, L2, ns, s)));
+    PVF_TRY("enc3", (conv5<2 * C, 0, 4 * C, 32, true>(b.s1, nullptr, w.w[1], w.b[1], b.e3, b.s0, L3, ns, s)));
+    PVF_TRY("enc4", (conv5<4 * C, 0, 8 * C, 16, false>(b.s0, nullptr, w.w[2], w.b[2], b.deep, nullptr, L4, ns, s)));
+    PVF_TRY("up3", (convT<8 * C, 4 * C, 16>(b.deep, w.uw[0], w.ub[0], b.up, L4, ns, s)));
+    PVF_TRY("dec3", (conv5<4 * C, 4 * C, 4 * C, 32, false>(b.up, b.e3, w.w[3], w.b[3], b.deep, nullptr, L3, ns, s)));
+    PVF_TRY("up2", (convT<4 * C, 2 * C, 32>(b.deep, w.uw[1], w.ub[1], b.up, L3, ns, s)));
+    PVF_TRY("dec2", (conv5<2 * C, 2 * C, 2 * C, 64, false>(b.up, b.e2, w.w[4], w.b[4], b.deep, nullptr, L2, ns, s)));
+    PVF_TRY("up1", (convT<2 * C, C, 64>(b.deep, w.uw[2], w.ub[2], b.up, L2, ns, s)));
+    PVF_TRY("dec1", (conv5<C, C, C, 128, false>(b.up, b.e1, w.w[5], w.b[5], b.deep, nullptr, L1, ns, s)));
+#undef PVF_TRY
+    return cudaSuccess;
+}
+
 }  // namespace
 
-cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n, cudaStream_t s,
+cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n, bool iv, cudaStream_t s,
                             const ProfHook *prof) {
     if (n <= 0) return cudaSuccess;
+    if (iv) {
+        if (w.c0 != kC0 || n * kSlices > 65535) return cudaErrorInvalidValue;
+        return run_f32_iv<kC0>(w, b, n, s, prof);
+    }
     if (w.c0 == kC0) return run_f32<kC0>(w, b, n, s, prof);
     if (w.c0 == kC0Max) return run_f32<kC0Max>(w, b, n, s, prof);
     return cudaErrorInvalidValue;

@@ -5,6 +5,7 @@
 // host-side validation and pointer arithmetic: the caller's Structure-of-Arrays
 // features are read in place by the first kernel, every intermediate lives at a fixed
 // offset of the caller's pool, and every launch goes to the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -197,18 +198,34 @@ pvf_status check_config(const pvf_config *c) {
     if (c->max_tracks_per_event < 1 || c->max_tracks_per_event > 8192) return PVF_ERR_INVALID_ARG;
     if (c->max_pv_per_event < 1 || c->max_pv_per_event > 1024) return PVF_ERR_INVALID_ARG;
     if (c->chunk_events < 0 || c->chunk_events > c->max_events) return PVF_ERR_INVALID_ARG;
-    for (int r : c->reserved) if (r != 0) return PVF_ERR_INVALID_ARG;
     if (!(c->boundary_mm >= 0.0f && c->boundary_mm < 5.0f)) return PVF_ERR_INVALID_ARG;
     if (c->unet_width != 0 && c->unet_width != kC0 && c->unet_width != kC0Max) return PVF_ERR_INVALID_ARG;
     if (c->unet_width == kC0Max && c->precision != PVF_FP32) return PVF_ERR_UNSUPPORTED;
+    if (c->per_interval != 0 && c->per_interval != 1) return PVF_ERR_INVALID_ARG;
+    if (c->per_interval && (c->precision != PVF_FP32 || c->unet_width == kC0Max)) return PVF_ERR_UNSUPPORTED;
     return PVF_OK;
 }
 
 int cfg_c0(const pvf_config *c) { return c->unet_width ? c->unet_width : kC0; }
 
+// Largest per-event (L + 4) * C over the tensors of the big slots (e1..e4, u1..u3, d1..d3)
+// and of the small ones (p1..p3), for sequences of L0 bins, base width c0, seqs per event.
+void slot_elems(int L0, int c0, int seqs, size_t *big, size_t *small) {
+    auto rows = [](int L) { return (size_t)(L + 2 * kPad); };
+    size_t b = 0, s = 0;
+    for (int k = 0; k < 4; ++k) b = std::max(b, rows(L0 >> k) * ((size_t)c0 << k));
+    for (int k = 1; k < 4; ++k) s = std::max(s, rows(L0 >> k) * ((size_t)c0 << (k - 1)));
+    *big = b * seqs;
+    *small = s * seqs;
+}
+
+constexpr int kMaxIvChunk = 65535 / kSlices;
+
 Plan make_plan(const pvf_config *c) {
     Plan p{};
     p.chunk = c->chunk_events ? c->chunk_events : c->max_events;
+    // per-interval layout: one grid row per sequence, kSlices per event (at most 65535)
+    if (c->per_interval && p.chunk > kMaxIvChunk) p.chunk = kMaxIvChunk;
     size_t o = 0;
     p.status = o; o += 256;
     p.ev_flag = o; o = align256(o + sizeof(int32_t) * (size_t)c->max_events);
@@ -217,9 +234,12 @@ Plan make_plan(const pvf_config *c) {
     p.tcw = o; o = align256(o + tc_weight_bytes(c->precision));
     p.logits = o; o = align256(o + (c->precision != PVF_FP32 ? sizeof(float) * kBins * (size_t)p.chunk : 0));
     const size_t eb = elem_bytes(c->precision);
-    // every activation tensor scales with the base width
-    p.act_slot_big = align256((size_t)p.chunk * kBigElems * (c0 / kC0) * eb);
-    p.act_slot_small = align256((size_t)p.chunk * kSmallElems * (c0 / kC0) * eb);
+    // every activation tensor scales with the base width; the per-interval layout holds
+    // kSlices sequences of kIvLen bins per event instead of one of kBins
+    size_t big = (size_t)kBigElems * (c0 / kC0), small = (size_t)kSmallElems * (c0 / kC0);
+    if (c->per_interval) slot_elems(kIvLen, c0, kSlices, &big, &small);
+    p.act_slot_big = align256((size_t)p.chunk * big * eb);
+    p.act_slot_small = align256((size_t)p.chunk * small * eb);
     p.act = o; o += 5 * p.act_slot_big + 2 * p.act_slot_small;
     p.total = o + 256;
     return p;
@@ -477,6 +497,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.ev_base = ev_base;
         a.max_tracks = h->cfg.max_tracks_per_event;
         a.c0 = h->c0;
+        a.iv = h->cfg.per_interval;
         a.edge = h->cfg.boundary_mm;
         a.edge_hi = 10.0f - h->cfg.boundary_mm;
         a.fc = h->fc;
@@ -498,7 +519,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         if (err != cudaSuccess) return err;
     }
     if (run_unet) {
-        if (prec == PVF_FP32) err = launch_unet_f32(h->cw, h->buf, n, s, prof);
+        if (prec == PVF_FP32) err = launch_unet_f32(h->cw, h->buf, n, h->cfg.per_interval != 0, s, prof);
         else err = launch_unet_tc(h->tc, h->buf, n, s, prof);
         if (err != cudaSuccess) return err;
     }
@@ -517,6 +538,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         t.d1_scale = h->act_scale[kScaleD1];
         t.final_w = h->fin;
         t.c0 = h->c0;
+        t.iv = h->cfg.per_interval;
         t.n_events = n;
         t.ev_base = ev_base;
         t.logit_out = logit_out;

@@ -31,6 +31,11 @@ constexpr int kFcOut = 100;
 constexpr int kFcInPad = 12;   // layer-1 input padded to a multiple of 4 floats
 constexpr int kC0 = 16;        // UNet base width; levels have 16, 32, 64, 128 channels
 constexpr int kC0Max = 32;     // widest variant (float32 form only): 32, 64, 128, 256
+// Per-interval layout (float32 form): each interval is a sequence of kIvLen bins, its
+// kSliceBins bins with kIvPad zero bins on each side (the fewest that survive 3 poolings).
+constexpr int kIvPad = 2;
+constexpr int kIvLen = kSliceBins + 2 * kIvPad;
+static_assert(kIvLen % 8 == 0, "three 2:1 poolings");
 constexpr int kPad = 2;        // zero rows on each side of an event (k5 "same" padding)
 constexpr float kZLo = -100.0f;
 constexpr float kBinW = 0.1f;
@@ -173,6 +178,7 @@ struct FrontArgs {
     int32_t ev_base;             // global index of the launch's first event
     int32_t max_tracks;          // per-event cap
     int32_t c0;                  // UNet base width (16, or 32 in the float32 form)
+    int32_t iv;                  // per-interval layout: e1 / p1 as kSlices sequences per event
     float edge;                  // boundary-track width in mm (0: every track in one slice)
     float edge_hi;               // 10 - edge, rounded to float
     const float *fc;             // packed FC block (kFcFloats); its biases serve both forms
@@ -195,6 +201,7 @@ struct TailArgs {
     float d1_scale;              // fp8 only
     const float *final_w;        // 5 c0 + 1 floats: W[t][ci], then b
     int32_t c0;                  // width of d1 (16, or 32 in the float32 form)
+    int32_t iv;                  // per-interval layout: d1 holds kSlices sequences per event
     int32_t n_events;
     int32_t ev_base;
     const int32_t *ev_flag;      // nullable (all events valid)
@@ -274,7 +281,8 @@ struct UnetBuffers {
     void *e1, *e2, *e3, *deep, *up, *s0, *s1;
     float *logits;   // tensor-core forms: final-conv output of the chunk, [n][4000]
 };
-cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n_events,
+// iv: per-interval layout (kSlices sequences of kIvLen bins per event).
+cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n_events, bool iv,
                             cudaStream_t s, const ProfHook *prof);
 
 }  // namespace pvf

@@ -45,7 +45,7 @@ class PvfConfig(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_events", ctypes.c_int32),
                 ("max_tracks_per_event", ctypes.c_int32), ("max_pv_per_event", ctypes.c_int32),
                 ("chunk_events", ctypes.c_int32), ("boundary_mm", ctypes.c_float),
-                ("unet_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+                ("unet_width", ctypes.c_int32), ("per_interval", ctypes.c_int32),
                 ("fp8_act_scales", ctypes.c_void_p)]
 
 
@@ -134,10 +134,12 @@ def _check(code: int, where: str, allow_warn: bool = False):
 
 
 def make_config(precision="fp32", max_events=1, max_tracks_per_event=2048, max_pv_per_event=64,
-                chunk_events=0, fp8_act_scales=None, boundary_mm=0.0, unet_width=0):
+                chunk_events=0, fp8_act_scales=None, boundary_mm=0.0, unet_width=0,
+                per_interval=False):
     cfg = PvfConfig()
     cfg.boundary_mm = boundary_mm
     cfg.unet_width = unet_width
+    cfg.per_interval = int(per_interval)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.max_events = max_events
     cfg.max_tracks_per_event = max_tracks_per_event
@@ -217,14 +219,15 @@ class PVFinder:
 
     def __init__(self, weights: dict, precision="fp32", max_events=1024,
                  max_tracks_per_event=2048, max_pv_per_event=64, chunk_events=0,
-                 fp8_act_scales=None, device=None, stream=None, boundary_mm=0.0):
+                 fp8_act_scales=None, device=None, stream=None, boundary_mm=0.0,
+                 per_interval=False):
         import torch
         self.lib = load()
         self.device = torch.device(device or "cuda")
         # the UNet base width follows the weights (the blob records it too)
         self.cfg, self._keep = make_config(precision, max_events, max_tracks_per_event,
                                            max_pv_per_event, chunk_events, fp8_act_scales,
-                                           boundary_mm, unet_width(weights))
+                                           boundary_mm, unet_width(weights), per_interval)
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_pool_bytes_required(ctypes.byref(self.cfg), ctypes.byref(need)),
                "pvf_pool_bytes_required")

@@ -332,3 +332,74 @@ def test_wide_unet_tensor_core_forms_unsupported(lib, wide_weights, precision):
     with pytest.raises(PvfError) as ei:
         lib(wide_weights, precision=precision, max_events=4)
     assert ei.value.code == PVF_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- per-interval layout (§3)
+# Each of the 40 intervals runs the UNet as its own 104-bin sequence (two zero bins on each
+# side); its 100 central logits fill the interval's bins. Built in the float32 form.
+
+@pytest.fixture(scope="module")
+def iv_ref(weights, ev16):
+    return oracle.infer(weights, ev16.features, ev16.offsets, max_pv=MAX_PV, want_hist=True,
+                        want_logit=True, nthreads=NTHREADS, per_interval=True)
+
+
+@pytest.fixture(scope="module")
+def iv_pv(lib, weights):
+    return lib(weights, precision="fp32", max_events=16, max_pv_per_event=MAX_PV, per_interval=True)
+
+
+def test_per_interval_unet_stage_matches_oracle(iv_pv, weights, ref16):
+    h32 = ref16["hist"].astype(np.float32)
+    logit = torch.zeros((16, 4000), dtype=torch.float32, device="cuda")
+    iv_pv.stage_unet(torch.from_numpy(h32).cuda(), logit)
+    torch.cuda.synchronize()
+    want = np.stack([oracle.unet_intervals(weights, h32[e].astype(np.float64))[0] for e in range(16)])
+    assert_per_bin(logit.cpu().numpy(), want)
+
+
+def test_per_interval_end_to_end_matches_oracle(iv_pv, ev16, iv_ref, ref16):
+    r = run_full(iv_pv, ev16)
+    assert_per_bin(r["hist"], ref16["hist"])            # the histogram does not depend on the layout
+    assert_per_bin(r["logit"], iv_ref["logit"])
+    assert np.max(np.abs(iv_ref["logit"] - ref16["logit"])) > 1e-3      # a different network output
+    eps = max(4 * float(np.max(np.abs(r["logit"] - iv_ref["logit"]))), 1e-6)
+    a = pv_agreement(iv_ref["pv_z"], iv_ref["pv_count"], r["z"], r["count"], iv_ref["logit"], eps)
+    print("per-interval fp32 agreement", a)
+    assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
+    assert iv_pv.device_status() == 0
+
+
+def test_per_interval_bitwise_batch_invariant_and_chunked(lib, iv_pv, weights, ev16):
+    r1 = run_full(iv_pv, ev16)
+    r2 = run_full(iv_pv, ev16)
+    rs = run_full(iv_pv, ev16.subset(6, 10))
+    chunked = lib(weights, precision="fp32", max_events=16, chunk_events=5, max_pv_per_event=MAX_PV,
+                  per_interval=True)
+    rc = run_full(chunked, ev16)
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(r1[k], r2[k])
+        np.testing.assert_array_equal(rs[k], r1[k][6:10])
+        np.testing.assert_array_equal(rc[k], r1[k])
+
+
+def test_per_interval_with_boundary_tracks_matches_oracle(lib, weights, ev16):
+    """§3's combination: intervals processed on their own, boundary tracks in two."""
+    ref = oracle.infer(weights, ev16.features, ev16.offsets, max_pv=MAX_PV, want_hist=True,
+                       want_logit=True, nthreads=NTHREADS, per_interval=True, edge_mm=0.5)
+    pv = lib(weights, precision="fp32", max_events=16, max_pv_per_event=MAX_PV, per_interval=True,
+             boundary_mm=0.5)
+    r = run_full(pv, ev16)
+    assert_per_bin(r["hist"], ref["hist"])
+    assert_per_bin(r["logit"], ref["logit"])
+    eps = max(4 * float(np.max(np.abs(r["logit"] - ref["logit"]))), 1e-6)
+    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"], r["count"], ref["logit"], eps)
+    assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_per_interval_tensor_core_forms_unsupported(lib, weights, precision):
+    from paper_2602_19959_gb300.pvf import PvfError, PVF_ERR_UNSUPPORTED
+    with pytest.raises(PvfError) as ei:
+        lib(weights, precision=precision, max_events=4, per_interval=True)
+    assert ei.value.code == PVF_ERR_UNSUPPORTED

@@ -62,13 +62,21 @@ def test_pool_bytes_required_and_config_validation(lib):
     assert 1.9 * fp32 < fp32w < 2.1 * fp32
     assert P.pool_bytes_required(precision="fp32", max_events=1000, unet_width=16) == fp32
     for prec in ("bf16", "fp16", "fp8"):
-        cfg, _ = P.make_config(precision=prec, max_events=10, unet_width=32)
-        out = ctypes.c_size_t(0)
-        assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
+        for kw in (dict(unet_width=32), dict(per_interval=True)):
+            cfg, _ = P.make_config(precision=prec, max_events=10, **kw)
+            out = ctypes.c_size_t(0)
+            assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
+    cfg, _ = P.make_config(precision="fp32", max_events=10, unet_width=32, per_interval=True)
+    out = ctypes.c_size_t(0)
+    assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
+    # the per-interval layout: 40 sequences of 104 bins per event (e4: 17 rows x 128 channels)
+    iv = P.pool_bytes_required(precision="fp32", max_events=1000, per_interval=True)
+    assert 1.25 * fp32 < iv < 1.45 * fp32
     for bad in (dict(max_events=0), dict(max_tracks_per_event=0), dict(max_tracks_per_event=9000),
                 dict(max_pv_per_event=0), dict(chunk_events=-1), dict(precision=7),
                 dict(boundary_mm=-0.1), dict(boundary_mm=5.0), dict(boundary_mm=float("nan")),
-                dict(unet_width=24), dict(unet_width=64), dict(unet_width=-16)):
+                dict(unet_width=24), dict(unet_width=64), dict(unet_width=-16),
+                dict(per_interval=2), dict(per_interval=-1)):
         kw = dict(precision="fp32", max_events=10)
         kw.update(bad)
         cfg, _ = P.make_config(**kw)
