@@ -53,45 +53,52 @@ def convT_io(L, cin, cout):
     return L * 2 * cout * cin, cin * (L + 4), cout * (2 * L + 4)
 
 
-def kernel_table(form, c0=16):
+def kernel_table(form, c0=16, iv=False):
     """Algorithmic work per event of each kernel family: (MAC, bytes, compute unit), for
-    UNet base width c0 (levels c0, 2 c0, 4 c0, 8 c0). MACs of the FC depend on the track
-    count and are added by the caller."""
+    UNet base width c0 (levels c0, 2 c0, 4 c0, 8 c0); iv: the per-interval layout (40
+    sequences of 104 bins per event instead of one of 4000). MACs of the FC depend on the
+    track count and are added by the caller."""
     es = {"fp32": 4, "bf16": 2, "fp16": 2, "fp8": 1}[form]
     c1, c2, c3, c4 = c0, 2 * c0, 4 * c0, 8 * c0
+    L0, q = (104, 40) if iv else (4000, 1)             # sequence length, sequences per event
+    L1, L2, L3 = L0 // 2, L0 // 4, L0 // 8
+
+    def scaled(mrw):
+        return tuple(q * x for x in mrw)
+
     t = {}
-    e1 = c1 * 4004 + c1 * 2004               # e1 and p1 written by the front kernel
-    t["front"] = (4000 * c1 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
-    m, r, w = conv_io(2000, c1, c2, pool=True); t["enc2"] = (m, 0, (r + w) * es, None)
-    m, r, w = conv_io(1000, c2, c3, pool=True); t["enc3"] = (m, 0, (r + w) * es, None)
+    e1 = q * (c1 * (L0 + 4) + c1 * (L1 + 4))            # e1 and p1 written by the front kernel
+    t["front"] = (q * L0 * c1 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
+    m, r, w = scaled(conv_io(L1, c1, c2, pool=True)); t["enc2"] = (m, 0, (r + w) * es, None)
+    m, r, w = scaled(conv_io(L2, c2, c3, pool=True)); t["enc3"] = (m, 0, (r + w) * es, None)
     if form == "fp32":
-        m, r, w = conv_io(500, c3, c4); t["enc4"] = (m, 0, (r + w) * es, None)
-        m, r, w = convT_io(500, c4, c3); t["up3"] = (m, 0, (r + w) * es, None)
-        m, r, w = conv_io(1000, 2 * c3, c3); t["dec3"] = (m, 0, (r + w) * es, None)
-        m, r, w = convT_io(1000, c3, c2); t["up2"] = (m, 0, (r + w) * es, None)
-        m, r, w = conv_io(2000, 2 * c2, c2); t["dec2"] = (m, 0, (r + w) * es, None)
-        m, r, w = convT_io(2000, c2, c1); t["up1"] = (m, 0, (r + w) * es, None)
-        m, r, w = conv_io(4000, 2 * c1, c1); t["dec1"] = (m, 0, (r + w) * es, None)
-        t["tail"] = (4000 * c1 * 5, 0, c1 * 4004 * es + 16000, "alu")
+        m, r, w = scaled(conv_io(L3, c3, c4)); t["enc4"] = (m, 0, (r + w) * es, None)
+        m, r, w = scaled(convT_io(L3, c4, c3)); t["up3"] = (m, 0, (r + w) * es, None)
+        m, r, w = scaled(conv_io(L2, 2 * c3, c3)); t["dec3"] = (m, 0, (r + w) * es, None)
+        m, r, w = scaled(convT_io(L2, c3, c2)); t["up2"] = (m, 0, (r + w) * es, None)
+        m, r, w = scaled(conv_io(L1, 2 * c2, c2)); t["dec2"] = (m, 0, (r + w) * es, None)
+        m, r, w = scaled(convT_io(L1, c2, c1)); t["up1"] = (m, 0, (r + w) * es, None)
+        m, r, w = scaled(conv_io(L0, 2 * c1, c1)); t["dec1"] = (m, 0, (r + w) * es, None)
+        t["tail"] = (4000 * c1 * 5, 0, q * c1 * (L0 + 4) * es + 16000, "alu")
     else:
-        m1, r1, _ = conv_io(500, c3, c4); m2, _, w2 = convT_io(500, c4, c3)
+        m1, r1, _ = conv_io(L3, c3, c4); m2, _, w2 = convT_io(L3, c4, c3)
         t["enc4_up3"] = (m1 + m2, 0, (r1 + w2) * es, None)
-        m1, r1, _ = conv_io(1000, 2 * c3, c3); m2, _, w2 = convT_io(1000, c3, c2)
+        m1, r1, _ = conv_io(L2, 2 * c3, c3); m2, _, w2 = convT_io(L2, c3, c2)
         t["dec3_up2"] = (m1 + m2, 0, (r1 + w2) * es, None)
-        m1, r1, _ = conv_io(2000, 2 * c2, c2); m2, _, w2 = convT_io(2000, c2, c1)
+        m1, r1, _ = conv_io(L1, 2 * c2, c2); m2, _, w2 = convT_io(L1, c2, c1)
         t["dec2_up1"] = (m1 + m2, 0, (r1 + w2) * es, None)
-        m1, r1, _ = conv_io(4000, 2 * c1, c1)
-        t["dec1_final"] = (m1 + 4000 * c1 * 5, 0, r1 * es + 16000, None)
+        m1, r1, _ = conv_io(L0, 2 * c1, c1)
+        t["dec1_final"] = (m1 + L0 * c1 * 5, 0, r1 * es + 16000, None)
         t["tail"] = (0, 0, 16000, "hbm")
     return t
 
 
 def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_launch, peaks,
-                fc_evals=None, c0=16):
+                fc_evals=None, c0=16, iv=False):
     """Roofline of one kernel family from its algorithmic FLOPs and bytes per launch:
     the bound is whichever of compute and memory needs more time at its peak. fc_evals:
     FC evaluations per launch (tracks plus second slices of boundary tracks)."""
-    mac, per_track_b, bytes_ev, unit = kernel_table(form, c0)[name]
+    mac, per_track_b, bytes_ev, unit = kernel_table(form, c0, iv)[name]
     flops = 2.0 * mac * events_per_launch
     nbytes = bytes_ev * events_per_launch + per_track_b * tracks_per_launch
     if name == "front":
@@ -213,14 +220,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None):
-    """Times the FP64 oracle (as it stands) on a bounded sample of the workload, all cores."""
+def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None, **variant):
+    """Times the FP64 oracle (as it stands) on a bounded sample of the workload, all cores.
+    variant: the oracle's edge_mm / per_interval, matching the GPU run."""
     import oracle
     cores = os.cpu_count() or 1
     n0 = min(batch.n_events, cores)
     sub = batch.subset(0, n0)
     t0 = time.perf_counter()
-    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores)
+    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores, **variant)
     dt0 = time.perf_counter() - t0
     n = int(min(batch.n_events, max(n0, n0 * target_s / max(dt0, 1e-3))))
     if max_events:
@@ -228,11 +236,16 @@ def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None):
     n = max(n0, n // cores * cores)
     sub = batch.subset(0, n)
     t0 = time.perf_counter()
-    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores)
+    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores, **variant)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "events/s", "cores": min(cores, n), "kind": "oracle",
             "sample": f"first {n} of the {batch.n_events}-event workload, FP64 C oracle, "
                       f"one event per thread, {dt:.1f} s wall"}
+
+
+def oracle_variant(args):
+    """The oracle's options for the workload variant the GPU run uses."""
+    return {"edge_mm": args.boundary_mm, "per_interval": args.per_interval}
 
 
 def run_reference(args, weights, batch, rank, world):
@@ -249,7 +262,8 @@ def run_reference(args, weights, batch, rank, world):
         b = min(n, a + per_step)
         sub = batch.subset(a, b)
         t0 = time.perf_counter()
-        oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores)
+        oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores,
+                     **oracle_variant(args))
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append((b - a, dt))
@@ -295,7 +309,8 @@ def workload_config(args, dtype):
             "events_per_gpu": args.events, "bins": 4000, "max_pv_per_event": args.max_pv,
             "l2": f"flushed between steps ({args.flush_mb} MB write)" if args.flush_mb >= 256
                   else "not flushed (profiling run)", "form": args.precision,
-            "boundary_mm": args.boundary_mm, "unet_width": args.unet_width}
+            "boundary_mm": args.boundary_mm, "unet_width": args.unet_width,
+            "per_interval": args.per_interval}
 
 
 def make_finder(args, weights, precision, events, **kw):
@@ -312,7 +327,7 @@ def make_finder(args, weights, precision, events, **kw):
                                 torch.from_numpy(cal.offsets).cuda())
         pcal.close()
     return PVFinder(weights, precision=precision, max_events=events, fp8_act_scales=scales,
-                    boundary_mm=args.boundary_mm, **kw)
+                    boundary_mm=args.boundary_mm, per_interval=args.per_interval, **kw)
 
 
 def time_steps(pv, step, flush, steps, world, profile):
@@ -470,12 +485,12 @@ def run_step(args, weights, batch, rank, world, local):
     total_ms = max(sum(v[1] for v in prof.values()), 1e-9)
     for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
         rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks, fc_evals,
-                         args.unet_width)
+                         args.unet_width, args.per_interval)
         kernels[k] = {"launches": n, "avg_us": 1000.0 * ms / max(n, 1), "share": ms / total_ms,
                       "bound": rf["bound"], "frac": rf["frac"]}
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
     roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks, fc_evals,
-                       args.unet_width)
+                       args.unet_width, args.per_interval)
     traffic = NCU_TRAFFIC.get((args.precision, name, args.events))
     roof.update({"kernel": name, "traffic": traffic,
                  "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
@@ -526,7 +541,7 @@ def run_step(args, weights, batch, rank, world, local):
         line["serving"]["workload"] = "uneven events (N_PV ~ U{1..12}, heavy-tailed background)"
         ps.close()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_cpu_baseline(weights, batch)
+        line["cpu_baseline"] = oracle_cpu_baseline(weights, batch, **oracle_variant(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -580,6 +595,8 @@ def main():
     ap.add_argument("--max-pv", type=int, default=672)
     ap.add_argument("--unet-width", type=int, default=16, choices=[16, 32],
                     help="UNet base width (32: the wide variant, float32 form only)")
+    ap.add_argument("--per-interval", action="store_true",
+                    help="each interval runs the UNet as its own 104-bin sequence (fp32 form only)")
     ap.add_argument("--boundary-mm", type=float, default=0.0,
                     help="boundary tracks fill a second slice within this width (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -601,6 +618,8 @@ def main():
     rank, world, local = dist_env()
     if args.unet_width != 16 and args.precision != "fp32":
         ap.error("--unet-width 32 exists in the fp32 form only")
+    if args.per_interval and (args.precision != "fp32" or args.unet_width != 16):
+        ap.error("--per-interval exists in the fp32 form at width 16 only")
     weights = synth.he_weights(0, c0=args.unet_width)
     if args.impl == "reference":
         batch = synth.generate_standard(args.events, rank_workload_seed(rank))
