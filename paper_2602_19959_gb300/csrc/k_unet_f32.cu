@@ -125,14 +125,17 @@ k_conv5_f32(const float *__restrict__ inA, const float *__restrict__ inB,
         }
     }
     // pad rows of this event: written by the first and the last tile
+    // (a single tile is both: it writes both sides)
     const bool first = blockIdx.x == 0, last = blockIdx.x == gridDim.x - 1;
-    if (first || last) {
-        const int base = first ? 0 : L + kPad;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        if (!(side == 0 ? first : last)) continue;
+        const int base = side == 0 ? 0 : L + kPad;
         for (int i = tid; i < 2 * COUT; i += NT) ob[(size_t)base * COUT + i] = 0.0f;
         if constexpr (POOL) {
             const int Lp = L / 2;
             float *pb = outp + (size_t)e * padded_rows(Lp) * COUT;
-            const int pbase = first ? 0 : Lp + kPad;
+            const int pbase = side == 0 ? 0 : Lp + kPad;
             for (int i = tid; i < 2 * COUT; i += NT) pb[(size_t)pbase * COUT + i] = 0.0f;
         }
     }
@@ -211,8 +214,10 @@ k_convT_f32(const float *__restrict__ in, const float *__restrict__ W,
         }
     }
     const bool first = blockIdx.x == 0, last = blockIdx.x == gridDim.x - 1;
-    if (first || last) {
-        const int base = first ? 0 : Lout + kPad;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {   // a single tile is both first and last
+        if (!(side == 0 ? first : last)) continue;
+        const int base = side == 0 ? 0 : Lout + kPad;
         for (int i = tid; i < 2 * COUT; i += NT) ob[(size_t)base * COUT + i] = 0.0f;
     }
 }
