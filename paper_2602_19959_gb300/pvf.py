@@ -215,7 +215,16 @@ class Graph:
 
 
 class PVFinder:
-    """Owns a pool tensor and a pvf_handle; every method maps to one C entry point."""
+    """Owns a pool tensor and a pvf_handle; every method maps to one C entry point.
+
+    weights: {layer: (W, b)} in PyTorch layouts (the UNet base width, 16 or 32, is taken
+    from enc1). precision: "fp32", "bf16", "fp16" or "fp8" (fp8 needs fp8_act_scales,
+    e.g. from calibrate() of a bf16 instance). max_events / max_tracks_per_event /
+    max_pv_per_event / chunk_events: the frozen plan of pvf_config. boundary_mm: width of
+    the band in which a track also fills the neighbouring slice (0: none).
+    per_interval: each interval runs the UNet as its own 104-bin sequence (float32 form,
+    width 16). Width 32 and per_interval are float32 only; other forms raise PvfError
+    with PVF_ERR_UNSUPPORTED."""
 
     def __init__(self, weights: dict, precision="fp32", max_events=1024,
                  max_tracks_per_event=2048, max_pv_per_event=64, chunk_events=0,
