@@ -13,11 +13,12 @@
  *   3. heuristic peak finding by local-maximum detection.
  * The paper does not print the layer shapes, activations, padding or peak-finder
  * constants; the readings used here (architecture 9-32-32-32-32-32-100 with
- * LeakyReLU(0.01) and softplus; UNet with 4 levels of 16/32/64/128 channels, k5 zero
- * "same" padding, maxpool 2, ConvTranspose k2 s2, skip concat [upsampled, skip];
- * threshold 0.01, strict-left / non-strict-right local max over +-5 bins, centroid
- * over +-3 bins; slice-relative z as the third feature) are stated next to the code
- * that uses them and listed in the design notes.
+ * LeakyReLU(0.01) and softplus; UNet with 4 levels of c0/2c0/4c0/8c0 channels, c0 = 16
+ * or 32, k5 zero "same" padding, maxpool 2, ConvTranspose k2 s2, skip concat
+ * [upsampled, skip]; threshold 0.01, strict-left / non-strict-right local max over
+ * +-5 bins, centroid over +-3 bins; slice-relative z as the third feature; optional
+ * boundary tracks in a second interval and the per-interval UNet layout of §3) are
+ * stated next to the code that uses them and listed in the design notes.
  *
  * Everything is a direct loop in double precision, in the order of the definition;
  * no blocking, fusion or reordering. Features arrive as float32 and are widened.
