@@ -131,3 +131,38 @@ def test_blob_layout():
     w = np.frombuffer(blob, dtype="<f4", count=64 * 128 * 5, offset=wo).reshape(64, 128, 5)
     np.testing.assert_array_equal(w, synth.he_weights(0)["dec3"][0])
     assert wo % 16 == 0 and bo % 16 == 0
+
+
+def _serve_bytes(lib, max_pv=64, **kw):
+    cfg = P.PvfServeConfig()
+    cfg.max_batch, cfg.max_tracks_per_batch, cfg.max_inflight, cfg.min_batch = 32, 8000, 2, 1
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    out = ctypes.c_size_t(0)
+    return lib.pvf_serve_bytes_required(ctypes.byref(cfg), max_pv, ctypes.byref(out)), out.value
+
+
+def test_serve_slot_sizing_and_validation(lib):
+    """A serving slot holds one batch: 9 feature rows of max_tracks_per_batch floats and
+    max_batch + 1 offsets, then the counts, then max_batch x max_pv z values, each part
+    256-byte aligned; max_inflight slots in all."""
+    align = lambda x: (x + 255) // 256 * 256
+    slot = align(align(align(4 * 9 * 8000 + 4 * 33) + 4 * 32) + 4 * 32 * 64)
+    st, n2 = _serve_bytes(lib)
+    assert st == 0 and n2 == 2 * slot
+    st, n5 = _serve_bytes(lib, max_inflight=5)
+    assert st == 0 and n5 == 5 * slot
+    for bad in (dict(max_batch=0), dict(max_inflight=0), dict(max_inflight=17),
+                dict(max_tracks_per_batch=0)):
+        assert _serve_bytes(lib, **bad)[0] == P.PVF_ERR_INVALID_ARG
+    assert _serve_bytes(lib, max_pv=0)[0] == P.PVF_ERR_INVALID_ARG
+    out = ctypes.c_size_t(0)
+    assert lib.pvf_serve_bytes_required(None, 64, ctypes.byref(out)) == P.PVF_ERR_INVALID_ARG
+
+
+def test_config_struct_layout():
+    """The ctypes mirrors of the C structs keep the header's sizes and offsets."""
+    assert ctypes.sizeof(P.PvfConfig) == 40
+    assert P.PvfConfig.boundary_mm.offset == 20 and P.PvfConfig.unet_width.offset == 24
+    assert P.PvfConfig.per_interval.offset == 28 and P.PvfConfig.fp8_act_scales.offset == 32
+    assert ctypes.sizeof(P.PvfServeConfig) == 32 and P.PvfServeConfig.flags.offset == 20
