@@ -58,3 +58,23 @@ def test_fc_evaluations_follow_the_oracle_second_slice_rule():
                 want += 1
         assert bench.fc_evaluations(b, edge) == want
     assert bench.fc_evaluations(b, 0.5) > b.n_tracks
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host cores (no GPU needed)
+    and prints one JSON line with the same metric as the GPU arm."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--events", "16"], cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "events/s" and line["value"] > 0
+    assert line["higher_is_better"] is True and line["dtype"] == "f64"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
