@@ -403,3 +403,33 @@ def test_per_interval_tensor_core_forms_unsupported(lib, weights, precision):
     with pytest.raises(PvfError) as ei:
         lib(weights, precision=precision, max_events=4, per_interval=True)
     assert ei.value.code == PVF_ERR_UNSUPPORTED
+
+
+def test_end_to_end_closed_form(lib):
+    """All four steps against hand-derived values (the oracle pin of the same name): zero
+    FC weights and the identity UNet, so each populated slice s gives one vertex at
+    z = -100 + (100 s + 50.5) * 0.1."""
+    from tests.test_oracle_pins import identity_unet_weights
+    a, c = 0.5, -6.0
+    w = identity_unet_weights(a, c)
+    j = np.arange(100)
+    b6 = (3.0 - (j - 50.0) ** 2 / 20.0).astype(np.float32)
+    w["fc6"] = (w["fc6"][0], b6)
+    counts = {3: 1, 7: 2, 20: 5, 39: 3}
+    z = [np.float32(-100 + 10 * s + 4.2) for s, n in counts.items() for _ in range(n)]
+    f = np.random.default_rng(30).normal(0, 1, (9, len(z))).astype(np.float32)
+    f[2] = z
+    b = synth.EventBatch(features=f, offsets=np.array([0, len(z)], np.int32),
+                         n_pv=np.zeros(1, np.int32), pv_z=np.zeros(0))
+    pv = lib(w, precision="fp32", max_events=1, max_pv_per_event=64)
+    r = run_full(pv, b)
+    sp = np.logaddexp(0.0, b6.astype(np.float64))
+    want_hist = np.zeros(4000)
+    for s, n in counts.items():
+        want_hist[100 * s:100 * s + 100] = n * sp
+    assert_per_bin(r["hist"], want_hist[None])
+    assert_per_bin(r["logit"], (a * want_hist + c)[None])
+    assert r["count"][0] == len(counts)
+    want_z = [-100.0 + (100 * s + 50 + 0.5) * 0.1 for s in sorted(counts)]
+    np.testing.assert_allclose(r["z"][0, :len(counts)], want_z, rtol=0, atol=1e-3)
+    assert pv.device_status() == 0

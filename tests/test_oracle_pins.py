@@ -539,3 +539,32 @@ def test_per_interval_infer_uses_the_assembled_logits():
         n, z, _ = oracle.peaks(f, max_pv=672)    # weights via numpy's exp: z to the last ulp
         assert r["pv_count"][e] == n
         np.testing.assert_allclose(r["pv_z"][e, :n], z, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------- all four steps at once
+
+def test_end_to_end_closed_form():
+    """FC weights zero: each track adds softplus(b6[j]) to bin j of its slice. Identity
+    UNet: logit = a * hist + c (hist >= 0). b6 peaks at j = 50 and is symmetric about it,
+    so each populated slice s gives exactly one vertex, at bin 100 s + 50 with a zero
+    centroid offset; empty bins stay below the threshold (sigmoid(-6) < 0.01)."""
+    a, c = 0.5, -6.0
+    w = identity_unet_weights(a, c)
+    j = np.arange(100)
+    b6 = (3.0 - (j - 50.0) ** 2 / 20.0).astype(np.float32)
+    w["fc6"] = (w["fc6"][0], b6)
+    counts = {3: 1, 7: 2, 20: 5, 39: 3}
+    z = [np.float32(-100 + 10 * s + 4.2) for s, n in counts.items() for _ in range(n)]
+    f = np.random.default_rng(30).normal(0, 1, (9, len(z))).astype(np.float32)
+    f[2] = z
+    r = oracle.infer(w, f, np.array([0, len(z)], np.int32), max_pv=64, want_hist=True,
+                     want_logit=True)
+    sp = np.logaddexp(0.0, b6.astype(np.float64))
+    want_hist = np.zeros(4000)
+    for s, n in counts.items():
+        want_hist[100 * s:100 * s + 100] = n * sp
+    np.testing.assert_allclose(r["hist"][0], want_hist, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(r["logit"][0], a * want_hist + c, rtol=1e-14, atol=1e-14)
+    assert r["pv_count"][0] == len(counts)
+    want_z = [-100.0 + (100 * s + 50 + 0.5) * 0.1 for s in sorted(counts)]
+    np.testing.assert_allclose(r["pv_z"][0, :len(counts)], want_z, rtol=0, atol=1e-12)
