@@ -15,8 +15,11 @@ device->host copy of the PV lists.
   python bench.py --mode serve                    # Poisson arrivals at 20k..200k events/s
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
 
-The default line is the BF16 form; it also carries the plain FP32 form measured on the
-same events ("comparison") and a 2 s serving sample at 120k events/s ("serving").
+The default line is the FP16 form (the paper's §5 proposal, the reduced form whose PV
+lists meet the 99.9% agreement bar against the FP64 oracle); it also carries the plain
+FP32 form measured on the same events with the same steps ("fp32_plain", with its own
+roofline, kernels and e2e), a serving sample ("serving"), and the strict PV agreement of
+the headline form with the oracle's run in the cpu_baseline leg ("pv_agreement").
 
 With N > 1 (torchrun) every rank runs its own 1000 events (weak scaling, no
 collective on the data path; events are independent).
@@ -54,11 +57,14 @@ def convT_io(L, cin, cout):
 
 
 def kernel_table(form, c0=16, iv=False):
-    """Algorithmic work per event of each kernel family: (MAC, bytes, compute unit), for
-    UNet base width c0 (levels c0, 2 c0, 4 c0, 8 c0); iv: the per-interval layout (40
-    sequences of 104 bins per event instead of one of 4000). MACs of the FC depend on the
-    track count and are added by the caller."""
+    """Work per event of each kernel family: (tensor-core MAC, CUDA-core MAC, activation
+    bytes read + written), for UNet base width c0 (levels c0, 2 c0, 4 c0, 8 c0); iv: the
+    per-interval layout (40 sequences of 104 bins per event instead of one of 4000). The
+    FC's MACs depend on the track count and are added by the caller (front kernel). The
+    activation bytes are those the implementation stores between kernels, not work the
+    method requires (its own bytes are the input tracks and the PV lists)."""
     es = {"fp32": 4, "bf16": 2, "fp16": 2, "fp8": 1}[form]
+    tc = form != "fp32"
     c1, c2, c3, c4 = c0, 2 * c0, 4 * c0, 8 * c0
     L0, q = (104, 40) if iv else (4000, 1)             # sequence length, sequences per event
     L1, L2, L3 = L0 // 2, L0 // 4, L0 // 8
@@ -66,66 +72,100 @@ def kernel_table(form, c0=16, iv=False):
     def scaled(mrw):
         return tuple(q * x for x in mrw)
 
+    def entry(mac, nbytes, alu_mac=0):
+        return (mac, alu_mac, nbytes) if tc else (0, mac + alu_mac, nbytes)
+
     t = {}
     e1 = q * (c1 * (L0 + 4) + c1 * (L1 + 4))            # e1 and p1 written by the front kernel
-    t["front"] = (q * L0 * c1 * 5, 36.0, e1 * es, "alu")          # + tracks * 36 B read
-    m, r, w = scaled(conv_io(L1, c1, c2, pool=True)); t["enc2"] = (m, 0, (r + w) * es, None)
-    m, r, w = scaled(conv_io(L2, c2, c3, pool=True)); t["enc3"] = (m, 0, (r + w) * es, None)
+    t["front"] = (0, q * L0 * c1 * 5, e1 * es)          # enc1 on CUDA cores; + the FC, + 36 B per track
+    m, r, w = scaled(conv_io(L1, c1, c2, pool=True)); t["enc2"] = entry(m, (r + w) * es)
+    m, r, w = scaled(conv_io(L2, c2, c3, pool=True)); t["enc3"] = entry(m, (r + w) * es)
     if form == "fp32":
-        m, r, w = scaled(conv_io(L3, c3, c4)); t["enc4"] = (m, 0, (r + w) * es, None)
-        m, r, w = scaled(convT_io(L3, c4, c3)); t["up3"] = (m, 0, (r + w) * es, None)
-        m, r, w = scaled(conv_io(L2, 2 * c3, c3)); t["dec3"] = (m, 0, (r + w) * es, None)
-        m, r, w = scaled(convT_io(L2, c3, c2)); t["up2"] = (m, 0, (r + w) * es, None)
-        m, r, w = scaled(conv_io(L1, 2 * c2, c2)); t["dec2"] = (m, 0, (r + w) * es, None)
-        m, r, w = scaled(convT_io(L1, c2, c1)); t["up1"] = (m, 0, (r + w) * es, None)
-        m, r, w = scaled(conv_io(L0, 2 * c1, c1)); t["dec1"] = (m, 0, (r + w) * es, None)
-        t["tail"] = (4000 * c1 * 5, 0, q * c1 * (L0 + 4) * es + 16000, "alu")
+        m, r, w = scaled(conv_io(L3, c3, c4)); t["enc4"] = entry(m, (r + w) * es)
+        m, r, w = scaled(convT_io(L3, c4, c3)); t["up3"] = entry(m, (r + w) * es)
+        m, r, w = scaled(conv_io(L2, 2 * c3, c3)); t["dec3"] = entry(m, (r + w) * es)
+        m, r, w = scaled(convT_io(L2, c3, c2)); t["up2"] = entry(m, (r + w) * es)
+        m, r, w = scaled(conv_io(L1, 2 * c2, c2)); t["dec2"] = entry(m, (r + w) * es)
+        m, r, w = scaled(convT_io(L1, c2, c1)); t["up1"] = entry(m, (r + w) * es)
+        m, r, w = scaled(conv_io(L0, 2 * c1, c1)); t["dec1"] = entry(m, (r + w) * es)
+        t["tail"] = (0, 4000 * c1 * 5, q * c1 * (L0 + 4) * es + 16000)
     else:
         m1, r1, _ = conv_io(L3, c3, c4); m2, _, w2 = convT_io(L3, c4, c3)
-        t["enc4_up3"] = (m1 + m2, 0, (r1 + w2) * es, None)
+        t["enc4_up3"] = entry(m1 + m2, (r1 + w2) * es)
         m1, r1, _ = conv_io(L2, 2 * c3, c3); m2, _, w2 = convT_io(L2, c3, c2)
-        t["dec3_up2"] = (m1 + m2, 0, (r1 + w2) * es, None)
+        t["dec3_up2"] = entry(m1 + m2, (r1 + w2) * es)
         m1, r1, _ = conv_io(L1, 2 * c2, c2); m2, _, w2 = convT_io(L1, c2, c1)
-        t["dec2_up1"] = (m1 + m2, 0, (r1 + w2) * es, None)
+        t["dec2_up1"] = entry(m1 + m2, (r1 + w2) * es)
         m1, r1, _ = conv_io(L0, 2 * c1, c1)
-        t["dec1_final"] = (m1 + L0 * c1 * 5, 0, r1 * es + 16000, None)
-        t["tail"] = (0, 0, 16000, "hbm")
+        t["dec1_final"] = entry(m1, r1 * es + 16000, alu_mac=L0 * c1 * 5)   # final conv: fp32
+        t["tail"] = (0, 0, 16000)
     return t
+
+
+def peak_rates(peaks, form):
+    """Peak rates the fractions are taken against: tensor FLOP/s for the form's operand
+    type (measured bf16 burst; fp16 = bf16; e4m3 = 2 x bf16, the nominal ratio), fp32
+    CUDA-core FLOP/s and SFU operations/s derived from unit counts and the maximum SM
+    clock (152 SMs x 128 fp32 lanes x 2; 152 SMs x 16 SFU lanes), HBM bytes/s (measured)."""
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    return {"tensor": peaks["bf16_tflops"] * 1e12 * (2.0 if form == "fp8" else 1.0),
+            "alu": 152 * 128 * 2 * clk, "sfu": 152 * 16 * clk, "hbm": peaks["hbm_gbs"] * 1e9}
 
 
 def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_launch, peaks,
                 fc_evals=None, c0=16, iv=False):
-    """Roofline of one kernel family from its algorithmic FLOPs and bytes per launch:
-    the bound is whichever of compute and memory needs more time at its peak. fc_evals:
-    FC evaluations per launch (tracks plus second slices of boundary tracks)."""
-    mac, per_track_b, bytes_ev, unit = kernel_table(form, c0, iv)[name]
-    flops = 2.0 * mac * events_per_launch
-    nbytes = bytes_ev * events_per_launch + per_track_b * tracks_per_launch
-    if name == "front":
-        flops += 2.0 * FC_MAC_PER_TRACK * (tracks_per_launch if fc_evals is None else fc_evals)
+    """Roofline of one kernel family from the method's work per launch (MACs of the layers
+    it computes) over its measured launch duration. The bound is the compute unit that
+    does the kernel's arithmetic: the tensor pipe for the UNet convolutions of the
+    tensor-core forms, the fp32 CUDA cores for the float32 form. `hbm_frac` is the
+    activation bytes the implementation moves (not required by the method) over the
+    measured HBM bandwidth. The front kernel runs the FC on the tensor pipe, softplus on
+    the SFU and enc1 on CUDA cores, and is reported against each; its bound is
+    "latency" when none of them is near its peak. fc_evals: FC evaluations per launch
+    (tracks plus second slices of boundary tracks)."""
+    tc_mac, alu_mac, bytes_ev = kernel_table(form, c0, iv)[name]
     sec = tot_ms / max(launches, 1) / 1000.0
-    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6     # FLOP/s, fp32 lanes
-    tc_peak = peaks["bf16_tflops"] * 1e12 * (2.0 if form == "fp8" else 1.0)
-    cpeak = alu_peak if (unit == "alu" or form == "fp32") else tc_peak
-    hbm = peaks["hbm_gbs"] * 1e9
-    t_c, t_m = flops / cpeak, nbytes / hbm
-    if unit == "hbm" or (unit is None and t_m >= t_c):
-        return {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": nbytes / sec / hbm, "algorithmic_bytes": nbytes}
-    kind = "alu" if cpeak == alu_peak else "tensor"
-    return {"bound": kind, "achieved": flops / sec / 1e12, "peak": cpeak / 1e12, "unit": "TFLOP/s",
-            "frac": flops / sec / cpeak, "algorithmic_flops": flops}
+    pk = peak_rates(peaks, form)
+    nbytes = bytes_ev * events_per_launch
+    if name == "front":
+        fe = tracks_per_launch if fc_evals is None else fc_evals
+        nbytes += 36.0 * tracks_per_launch
+        fc_flops = 2.0 * FC_MAC_PER_TRACK * fe
+        alu_flops = 2.0 * alu_mac * events_per_launch + (0 if form != "fp32" else fc_flops)
+        fracs = {"alu": alu_flops / sec / pk["alu"],
+                 "sfu": 200.0 * fe / sec / pk["sfu"],          # softplus: exp2 + log2 per output
+                 "hbm": nbytes / sec / pk["hbm"]}
+        if form != "fp32":
+            fracs["tensor"] = fc_flops / sec / pk["tensor"]
+        top = max(fracs, key=fracs.get)
+        return {"bound": top if fracs[top] >= 0.5 else "latency", "frac": fracs[top],
+                "unit_fracs": fracs, "achieved": fracs[top] * pk[top] / (1e9 if top == "hbm" else 1e12),
+                "peak": pk[top] / (1e9 if top == "hbm" else 1e12),
+                "unit": "GB/s" if top == "hbm" else ("TOP/s" if top == "sfu" else "TFLOP/s"),
+                "hbm_frac": nbytes / sec / pk["hbm"], "activation_bytes": nbytes}
+    if tc_mac == 0 and alu_mac == 0:              # the tail of the tensor-core forms: reads logits
+        return {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": pk["hbm"] / 1e9,
+                "unit": "GB/s", "frac": nbytes / sec / pk["hbm"], "hbm_frac": nbytes / sec / pk["hbm"],
+                "activation_bytes": nbytes}
+    kind, mac = ("tensor", tc_mac) if tc_mac else ("alu", alu_mac)
+    flops = 2.0 * mac * events_per_launch
+    return {"bound": kind, "achieved": flops / sec / 1e12, "peak": pk[kind] / 1e12, "unit": "TFLOP/s",
+            "frac": flops / sec / pk[kind], "algorithmic_flops": flops,
+            "hbm_frac": nbytes / sec / pk["hbm"], "activation_bytes": nbytes}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels
-# that can dominate a step, from one `ncu --set full` capture of a 512-event step of the
-# current kernels (its summary is kept under profiles/), scaled to a launch of 1000
-# events (traffic grows with the events). Keyed by (form, kernel, events per launch). A kernel changed since
-# that capture has no entry and reports null.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels that
+# can dominate a step, from one ncu capture of a 512-event step (the summaries under
+# profiles/ give the command), scaled to a launch of 1000 events (traffic grows with the
+# events). Keyed by (form, kernel, events per launch); the value is (bytes, source). A
+# kernel changed since its capture has no entry and reports null.
 NCU_TRAFFIC = {
-    ("bf16", "dec3_up2", 1000): (131.740160e6 + 28.147712e6) * 1000 / 512,
-    ("bf16", "dec1_final", 1000): (131.237888e6 + 4.603136e6) * 1000 / 512,
-    ("bf16", "dec2_up1", 1000): (131.397376e6 + 28.666624e6) * 1000 / 512,
+    ("bf16", "dec3_up2", 1000): ((131.740160e6 + 28.147712e6) * 1000 / 512,
+                                 "ncu --set full, 512-event step, scaled by 1000/512"),
+    ("bf16", "dec1_final", 1000): ((131.237888e6 + 4.603136e6) * 1000 / 512,
+                                   "ncu --set full, 512-event step, scaled by 1000/512"),
+    ("bf16", "dec2_up1", 1000): ((131.397376e6 + 28.666624e6) * 1000 / 512,
+                                 "ncu --set full, 512-event step, scaled by 1000/512"),
 }
 
 
@@ -222,13 +262,14 @@ class ClockSampler:
 
 def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None, **variant):
     """Times the FP64 oracle (as it stands) on a bounded sample of the workload, all cores.
-    variant: the oracle's edge_mm / per_interval, matching the GPU run."""
+    variant: the oracle's edge_mm / per_interval, matching the GPU run. Returns the
+    baseline and the oracle's results on the sample (its PV lists and logits)."""
     import oracle
     cores = os.cpu_count() or 1
     n0 = min(batch.n_events, cores)
     sub = batch.subset(0, n0)
     t0 = time.perf_counter()
-    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores, **variant)
+    oracle.infer(weights, sub.features, sub.offsets, max_pv=672, nthreads=cores, **variant)
     dt0 = time.perf_counter() - t0
     n = int(min(batch.n_events, max(n0, n0 * target_s / max(dt0, 1e-3))))
     if max_events:
@@ -236,11 +277,12 @@ def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None, **varian
     n = max(n0, n // cores * cores)
     sub = batch.subset(0, n)
     t0 = time.perf_counter()
-    oracle.infer(weights, sub.features, sub.offsets, max_pv=256, nthreads=cores, **variant)
+    ref = oracle.infer(weights, sub.features, sub.offsets, max_pv=672, want_logit=True,
+                       nthreads=cores, **variant)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "events/s", "cores": min(cores, n), "kind": "oracle",
             "sample": f"first {n} of the {batch.n_events}-event workload, FP64 C oracle, "
-                      f"one event per thread, {dt:.1f} s wall"}
+                      f"one event per thread, {dt:.1f} s wall"}, ref
 
 
 def oracle_variant(args):
@@ -434,24 +476,15 @@ def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight):
             "under_400us_p99": bool(np.percentile(lat, 99) < 400.0)}
 
 
-def run_step(args, weights, batch, rank, world, local):
+def measure_form(args, weights, batch, precision, feats, offs, feats_h, offs_h, flush, world, local,
+                 clocks_too=False):
+    """One form of the path on the rank's batch: device-timed steps, the same steps with
+    per-kernel events (breakdown and roofline), and end-to-end steps through the public API
+    on pinned host buffers. Returns (line fields, the finder, its device outputs)."""
     import torch
-    from paper_2602_19959_gb300 import build
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0:
-        build()
-    barrier(world)
-
-    dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision]
-    pv = make_finder(args, weights, args.precision, args.events, max_pv_per_event=args.max_pv)
-    feats_h = torch.from_numpy(batch.features).pin_memory()
-    offs_h = torch.from_numpy(batch.offsets).pin_memory()
-    feats = feats_h.cuda()
-    offs = offs_h.cuda()
+    dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[precision]
+    pv = make_finder(args, weights, precision, args.events, max_pv_per_event=args.max_pv)
     z, c = pv.alloc_outputs(args.events)
-    flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def step_device():
         pv.infer(feats, offs, out=(z, c))
@@ -462,13 +495,14 @@ def run_step(args, weights, batch, rank, world, local):
     torch.cuda.synchronize()
     status = pv.device_status()
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    # the headline: whole steps only (per-kernel events between launches would also stop
-    # the kernels' dependent launches from overlapping one kernel's tail with the next
-    # one's prologue); then the same steps again with per-kernel events for the breakdown
+    sampler = ClockSampler(local) if clocks_too else None
+    if sampler:
+        sampler.start()
+    # whole steps only (per-kernel events between launches would also stop the kernels'
+    # dependent launches from overlapping one kernel's tail with the next one's prologue);
+    # then the same steps again with per-kernel events for the breakdown
     dev_ms, wall, _ = time_steps(pv, step_device, flush, args.steps, world, False)
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     prof_ms, _, prof = time_steps(pv, step_device, flush, args.steps, world, True)
     e2e_ms = time_e2e_pipelined(pv, feats_h, offs_h, args.events, args.steps, world)
 
@@ -477,58 +511,89 @@ def run_step(args, weights, batch, rank, world, local):
     value = aggregate_value(args.events, world, args.steps, dev_ms)
     e2e_value = aggregate_value(args.events, world, args.steps, e2e_ms)
 
-    # dominant kernel and its roofline (algorithmic work / live launch duration)
+    # dominant kernel and its roofline (the method's work / live launch duration)
     peaks, peak_src = load_peaks()
     valid_tracks = int(np.sum(np.diff(batch.offsets)))
     fc_evals = fc_evaluations(batch, args.boundary_mm)
     kernels = {}
     total_ms = max(sum(v[1] for v in prof.values()), 1e-9)
     for k, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
-        rf = roofline_of(k, n, ms, args.precision, args.events, valid_tracks, peaks, fc_evals,
+        rf = roofline_of(k, n, ms, precision, args.events, valid_tracks, peaks, fc_evals,
                          args.unet_width, args.per_interval)
         kernels[k] = {"launches": n, "avg_us": 1000.0 * ms / max(n, 1), "share": ms / total_ms,
-                      "bound": rf["bound"], "frac": rf["frac"]}
+                      "bound": rf["bound"], "frac": rf["frac"], "hbm_frac": rf["hbm_frac"]}
+        if "unit_fracs" in rf:
+            kernels[k]["unit_fracs"] = rf["unit_fracs"]
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    roof = roofline_of(name, launches, tot_ms, args.precision, args.events, valid_tracks, peaks, fc_evals,
+    roof = roofline_of(name, launches, tot_ms, precision, args.events, valid_tracks, peaks, fc_evals,
                        args.unet_width, args.per_interval)
-    traffic = NCU_TRAFFIC.get((args.precision, name, args.events))
-    roof.update({"kernel": name, "traffic": traffic,
-                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json: hbm_gbs, bf16_tflops burst; "
-                                "fp32 ALU = 152 SM x 128 lanes x 2 x sm_max_mhz; fp16 = bf16; fp8 = 2 x bf16)"})
-    gpu_launches = int(sum(n for n, _ in prof.values()))
-
+    traffic = NCU_TRAFFIC.get((precision, name, args.events))
+    roof.update({"kernel": name, "traffic": traffic[0] if traffic else None,
+                 "traffic_source": traffic[1] if traffic else "no ncu capture of this kernel as built",
+                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json: bf16_tflops burst, hbm_gbs; fp16 = "
+                                "bf16; e4m3 = 2 x bf16; fp32 ALU = 152 SM x 128 lanes x 2 x sm_max_mhz)"})
     h2d = batch.features.nbytes + batch.offsets.nbytes
     d2h = z.numel() * 4 + c.numel() * 4
-    line = {
-        "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
-        "ms_per_step_with_kernel_events": prof_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-        "data": "synthetic", "config": workload_config(args, dtype),
+    out = {
+        "value": value, "ms_per_step": dev_ms / args.steps,
+        "ms_per_step_with_kernel_events": prof_ms / args.steps, "dtype": dtype, "form": precision,
         "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "how": "pvf_infer per step on pinned host inputs and outputs, the copies of "
                        "step i+1 / i-1 overlapping step i's compute (two buffer sets, an "
                        "input and an output copy stream)"},
-        "roofline": roof, "kernels": kernels, "gpu_launches": gpu_launches,
-        "clocks": clocks, "wall_s_timed": wall, "device_status": status,
-        "peaks_source": peak_src,
+        "roofline": roof, "kernels": kernels, "gpu_launches": int(sum(n for n, _ in prof.values())),
+        "device_status": status, "wall_s_timed": wall,
     }
-    pv.close()
-    del pv
+    if clocks_too:
+        out["clocks"] = clocks
+    return out, pv, (z, c)
+
+
+def gpu_logits(pv, feats, offs, n):
+    """PV lists and logits of the first n events of the batch (outside any timed region),
+    for the agreement with the oracle's run."""
+    import torch
+    logit = torch.zeros((n, 4000), dtype=torch.float32, device="cuda")
+    z, c = pv.alloc_outputs(n)
+    pv.infer(feats, offs[:n + 1], n_events=n, out=(z, c), logit=logit)
+    torch.cuda.synchronize()
+    return z.cpu().numpy(), c.cpu().numpy(), logit.cpu().numpy()
+
+
+def run_step(args, weights, batch, rank, world, local):
+    import torch
+    from paper_2602_19959_gb300 import build
+    from paper_2602_19959_gb300.agreement import pv_agreement
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build()
+    barrier(world)
+
+    feats_h = torch.from_numpy(batch.features).pin_memory()
+    offs_h = torch.from_numpy(batch.offsets).pin_memory()
+    feats = feats_h.cuda()
+    offs = offs_h.cuda()
+    flush = torch.empty(max(args.flush_mb, 1) * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    head, pv, _ = measure_form(args, weights, batch, args.precision, feats, offs, feats_h, offs_h,
+                               flush, world, local, clocks_too=True)
+    line = {
+        "metric": "events/s", "value": head["value"], "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"],
+        "data": "synthetic", "config": workload_config(args, head["dtype"]),
+    }
+    line.update({k: v for k, v in head.items() if k not in line and k not in ("value",)})
+    agree_pv = pv
     if args.compare and args.precision != "fp32":
-        # the plain FP32 GPU form on the same events, same timing
-        p32 = make_finder(args, weights, "fp32", args.events, max_pv_per_event=args.max_pv)
-
-        def step32():
-            p32.infer(feats, offs, out=(z, c))
-
-        for _ in range(args.warmup):
-            step32()
-        ms32, _, _ = time_steps(p32, step32, flush, max(args.steps // 4, 3), world, False)
-        ms32 = max_over_ranks(ms32, world, "cuda")
-        v32 = aggregate_value(args.events, world, max(args.steps // 4, 3), ms32)
-        line["comparison"] = {"fp32_plain_events_per_s": v32, "speedup_vs_fp32": value / v32}
+        # the plain FP32 GPU form on the same events, same steps and the same measurements
+        p32_line, p32, _ = measure_form(args, weights, batch, "fp32", feats, offs, feats_h, offs_h,
+                                        flush, world, local)
+        p32_line["speedup_of_headline"] = head["value"] / p32_line["value"]
+        line["fp32_plain"] = p32_line
         p32.close()
         del p32
     if args.serve_seconds > 0 and world == 1:
@@ -541,7 +606,17 @@ def run_step(args, weights, batch, rank, world, local):
         line["serving"]["workload"] = "uneven events (N_PV ~ U{1..12}, heavy-tailed background)"
         ps.close()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_cpu_baseline(weights, batch, **oracle_variant(args))
+        cb, ref = oracle_cpu_baseline(weights, batch, **oracle_variant(args))
+        line["cpu_baseline"] = cb
+        n = len(ref["pv_count"])
+        gz, gc, gl = gpu_logits(agree_pv, feats, offs, n)
+        a = pv_agreement(ref["pv_z"], ref["pv_count"], gz, gc, ref["logit"], gl)
+        line["pv_agreement"] = {
+            "form": args.precision, "events": n, "strict": a["strict"], "exempt": a["exempt"],
+            "matched": a["matched"], "total": a["total"], "max_dz_mm": a["max_dz"],
+            "source": "the FP64 oracle's run of the cpu_baseline leg (same events); exempt: "
+                      "disagreements the measured per-bin logit differences can flip"}
+    pv.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -590,7 +665,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step")
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16", "fp8"])
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "bf16", "fp16", "fp8"])
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--max-pv", type=int, default=672)
     ap.add_argument("--unet-width", type=int, default=16, choices=[16, 32],

@@ -221,12 +221,14 @@ PVF_API pvf_status pvf_profile_read(pvf_handle *h, pvf_kernel_time *out, int32_t
  *   out_hist       device float[n_events * 4000], 16-byte aligned
  *   out_bypass     device int32[n_events] or NULL: 1 where the event was bypassed (bad
  *                  offsets or more than 2048 tracks; its histogram row is all zero)
- * The kernel's scratch (packed FC weights, per-event flags) is a fixed 64 KiB array
- * inside libpvf.so that every GPU loading the library holds until the process exits.
- * The first call on each device looks up that array's device address (make it before
- * any stream capture). Every call overwrites the array, which keeps the last call's
- * contents; calls that overlap on the GPU race on it. Asynchronous on stream (the blob
- * is copied out of host memory before the call returns). */
+ * The kernel's scratch (the packed FC weights, 31,760 bytes, and a bypass flag per event,
+ * 16,384 bytes: 48,384 bytes in all) is a fixed array inside libpvf.so that every GPU
+ * loading the library holds until the process exits. The first call on each device looks
+ * up that array's device address (make it before any stream capture). Every call
+ * overwrites the array, which keeps the last call's contents; calls that overlap on the
+ * GPU race on it. The packed weights go to the array in a copy from pageable host memory,
+ * so the call may wait for work already queued on stream before it returns; the kernel
+ * is then enqueued on stream and runs asynchronously. */
 PVF_API pvf_status pvf_histogram_static(const void *weights_blob, size_t blob_bytes,
                                         const pvf_tracks_soa *tracks,
                                         const int32_t *event_offsets, int32_t n_events,

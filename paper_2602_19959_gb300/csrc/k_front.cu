@@ -185,17 +185,10 @@ __global__ void __launch_bounds__(kThreads) k_front(FrontArgs a) {
 // the register limit at 256 threads), capped by the number of events.
 template <int PREC, bool ENC1, bool EDGE, int C0, bool IV = false>
 cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
-    static size_t configured = 0;
-    static int sms = 0;
-    if (smem > configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_front<PREC, ENC1, EDGE, C0, IV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        configured = smem;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
+    int sms = 0;
+    cudaError_t err = current_device_sms(&sms);
+    if (err == cudaSuccess) err = prepare_kernel((const void *)k_front<PREC, ENC1, EDGE, C0, IV>, smem, nullptr);
+    if (err != cudaSuccess) return err;
     int per_sm = (int)((228 * 1024) / (smem + 1024));
     if (per_sm > 2) per_sm = 2;
     if (per_sm < 1) per_sm = 1;

@@ -307,20 +307,13 @@ template <int PREC, bool EDGE>
 cudaError_t launch_front_tc_k(const FrontArgs &a, cudaStream_t s) {
     // persistent grid: as many CTAs as fit on the GPU at once (shared memory allows two
     // per SM, which also fill the 512 TMEM columns), each walking events
-    static size_t configured = 0;
-    static int grid_cap = 0;
     const size_t smem = TcSmem::total(a.max_tracks, a.edge);
-    if (smem > configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_front_tc<PREC, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        configured = smem;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid_cap = (sms > 0 ? sms : 1) * 2;
-    }
+    int sms = 0;
+    cudaError_t err = current_device_sms(&sms);
+    if (err == cudaSuccess) err = prepare_kernel((const void *)k_front_tc<PREC, EDGE>, smem, nullptr);
+    if (err != cudaSuccess) return err;
     const int per_sm = (int)((228 * 1024) / (smem + 1024));
-    int grid = grid_cap / 2 * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
+    int grid = sms * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
     if (grid > a.n_events) grid = a.n_events;
     k_front_tc<PREC, EDGE><<<grid, kT, smem, s>>>(a);
     return cudaGetLastError();

@@ -172,13 +172,9 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
     // persistent grid of resident CTAs (their launch bounds fix the registers: two per SM
     // with the final conv, eight without), each walking events
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
+    int sms = 0;
+    const cudaError_t err = current_device_sms(&sms);
+    if (err != cudaSuccess) return err;
     const int per_sm = a.logit_in ? 8 : 2;
     dim3 grid(a.n_events < per_sm * sms ? a.n_events : per_sm * sms), block(kThreads);
     if (a.logit_in) return launch_pdl(k_tail<false, kC0>, grid, block, 0, s, a);

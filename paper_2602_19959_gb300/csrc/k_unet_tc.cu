@@ -797,17 +797,6 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     }
 }
 
-int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
 template <class C>
 cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, const char *name) {
     if (a.n_events <= 0) return cudaSuccess;
@@ -819,26 +808,23 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
     const int by_tmem_smem = kSmemPerSm / kMaxByTmem - 1024;
     if (smem < by_tmem_smem) smem = by_tmem_smem;
     if (smem > 227 * 1024) smem = 227 * 1024;
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaError_t err = cudaFuncSetAttribute(k_conv_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (err != cudaSuccess) return err;
-        cudaFuncAttributes fa;
-        err = cudaFuncGetAttributes(&fa, k_conv_tc<C>);
-        if (err != cudaSuccess) return err;
-        // resident CTAs per SM: registers (each of the 4 sub-partitions holds 16K, allocated
-        // per warp in units of 256), shared memory (+1 KB reserved per CTA), threads, TMEM
-        const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
-        const int by_regs = 4 * (16384 / warp_regs) / (C::THREADS / 32);
-        const int by_smem = kSmemPerSm / (smem + 1024);
-        const int by_threads = 2048 / C::THREADS;
-        int n = by_regs < by_smem ? by_regs : by_smem;
-        if (by_threads < n) n = by_threads;
-        if (kMaxByTmem < n) n = kMaxByTmem;
-        per_sm = n < 1 ? 1 : n;
-    }
+    int sms = 0;
+    cudaFuncAttributes fa;
+    cudaError_t err = current_device_sms(&sms);
+    if (err == cudaSuccess) err = prepare_kernel((const void *)k_conv_tc<C>, (size_t)smem, &fa);
+    if (err != cudaSuccess) return err;
+    // resident CTAs per SM: registers (each of the 4 sub-partitions holds 16K, allocated
+    // per warp in units of 256), shared memory (+1 KB reserved per CTA), threads, TMEM
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = 4 * (16384 / warp_regs) / (C::THREADS / 32);
+    const int by_smem = kSmemPerSm / (smem + 1024);
+    const int by_threads = 2048 / C::THREADS;
+    int per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (by_threads < per_sm) per_sm = by_threads;
+    if (kMaxByTmem < per_sm) per_sm = kMaxByTmem;
+    if (per_sm < 1) per_sm = 1;
     const int ntiles = a.n_events * C::TPE;
-    int grid = sm_count() * per_sm;
+    int grid = sms * per_sm;
     if (grid > ntiles) grid = ntiles;
     ProfScope ps(prof, name, s);
     return launch_pdl(k_conv_tc<C>, dim3(grid), dim3(C::THREADS), (size_t)smem, s, a);

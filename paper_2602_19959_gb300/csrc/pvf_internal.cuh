@@ -247,6 +247,12 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Per-device launch set-up (csrc/launch_setup.cu), thread-safe: the SM count of the
+// current device, and a kernel's attributes on the current device with its dynamic
+// shared-memory limit raised to at least smem_bytes there (once per kernel and device).
+cudaError_t current_device_sms(int *sms);
+cudaError_t prepare_kernel(const void *kernel, size_t smem_bytes, cudaFuncAttributes *attr);
+
 // Host-side launchers (defined in the kernel translation units).
 cudaError_t launch_front(const FrontArgs &a, int precision, size_t smem_bytes, cudaStream_t s);
 // Sorted (track, slice) entries an event may hold: boundary tracks (§3) fill a second

@@ -14,7 +14,7 @@ constexpr int kStaticMaxTracks = 2048;    // tracks per event; larger events are
 constexpr size_t kOffFlags = 0;                                       // int32 [kStaticMaxEvents]
 constexpr size_t kOffFc = kOffFlags + sizeof(int32_t) * kStaticMaxEvents;  // float [kFcFloats]
 constexpr size_t kScratchBytes = (kOffFc + sizeof(float) * kFcFloats + 255) / 256 * 256;
-static_assert(kScratchBytes <= 64 * 1024, "the static scratch stays small");
+static_assert(kScratchBytes == 48384, "size stated in include/pvf.h");
 
 // Held by every GPU that loads the library, until the process exits. In host code this
 // name is only a stand-in for the symbol, never a device address.
@@ -67,7 +67,9 @@ extern "C" pvf_status pvf_histogram_static(const void *weights_blob, size_t blob
     if (scratch_address(&base) != cudaSuccess) return PVF_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     // this call's weights overwrite the previous call's; the flags are written per event
-    // by the kernel before they are read, so nothing needs clearing
+    // by the kernel before they are read, so nothing needs clearing. The copy is from
+    // pageable memory (this entry point allocates nothing, pinned staging included): the
+    // runtime stages it before returning, which may wait for work queued on the stream.
     if (cudaMemcpyAsync(base + kOffFc, fc.data(), sizeof(float) * kFcFloats, cudaMemcpyHostToDevice,
                         s) != cudaSuccess)
         return PVF_ERR_CUDA;

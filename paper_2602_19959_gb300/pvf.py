@@ -179,6 +179,14 @@ def tracks_struct(features) -> PvfTracks:
     return t
 
 
+def _check_out(t, shape, itemsize, name):
+    """An output tensor the kernels write: CUDA, contiguous, of this shape and element size."""
+    if not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != tuple(shape) or \
+            t.dtype.itemsize != itemsize or t.dtype.is_complex:
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of shape {tuple(shape)} "
+                         f"and {itemsize}-byte elements")
+
+
 def histogram_static(weights: dict, features, offsets, out_hist, out_bypass=None, stream=None):
     """Steps 1-2 through pvf_histogram_static (no device allocation by the library)."""
     lib = load()
@@ -186,6 +194,9 @@ def histogram_static(weights: dict, features, offsets, out_hist, out_bypass=None
     buf = ctypes.create_string_buffer(blob, len(blob))
     tr = tracks_struct(features)
     n = int(offsets.numel() - 1)
+    _check_out(out_hist, (n, N_BINS), 4, "out_hist")
+    if out_bypass is not None:
+        _check_out(out_bypass, (n,), 4, "out_bypass")
     _check(lib.pvf_histogram_static(buf, len(blob), ctypes.byref(tr), offsets.data_ptr(), n,
                                     out_hist.data_ptr(),
                                     out_bypass.data_ptr() if out_bypass is not None else None,

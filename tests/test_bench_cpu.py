@@ -30,14 +30,32 @@ def unet_macs_from_shapes(c0):
 @pytest.mark.parametrize("c0", [16, 32])
 def test_fp32_kernel_table_macs_equal_the_layer_shapes(c0):
     t = bench.kernel_table("fp32", c0)
-    assert sum(v[0] for v in t.values()) == unet_macs_from_shapes(c0)
+    assert sum(v[0] for v in t.values()) == 0                   # no tensor-core work
+    assert sum(v[1] for v in t.values()) == unet_macs_from_shapes(c0)
 
 
 @pytest.mark.parametrize("form", ["bf16", "fp16", "fp8"])
 def test_tensor_core_kernel_table_covers_the_same_macs(form):
     t = bench.kernel_table(form, 16)
-    assert sum(v[0] for v in t.values()) == unet_macs_from_shapes(16)
+    assert sum(v[0] + v[1] for v in t.values()) == unet_macs_from_shapes(16)
     assert unet_macs_from_shapes(16) == 122_496_000          # 245 MFLOP per event
+    # on CUDA cores: enc1 (1 -> 16) and the final conv (16 -> 1), 4000 x 16 x 5 MACs each
+    assert sum(v[1] for v in t.values()) == 2 * 4000 * 16 * 5
+
+
+def test_dominant_kernel_fraction_from_the_method_flops():
+    """dec3_up2 (dec3 1000 x 64 x 640 plus up2 1000 x 64 x 64 MACs per event) at 100 us
+    per 1000-event launch: 2 x 45.056e6 x 1000 FLOP / 100 us = 901 TFLOP/s."""
+    peaks = {"bf16_tflops": 1949.8, "hbm_gbs": 6785.5, "sm_max_mhz": 2070.0}
+    r = bench.roofline_of("dec3_up2", 10, 1.0, "fp16", 1000, 155000, peaks)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 901.12) < 0.01
+    assert abs(r["frac"] - 901.12 / 1949.8) < 1e-5
+    r8 = bench.roofline_of("dec3_up2", 10, 1.0, "fp8", 1000, 155000, peaks)
+    assert abs(r8["frac"] - r["frac"] / 2) < 1e-9             # e4m3 peak = 2 x bf16
+    front = bench.roofline_of("front", 1, 0.086, "fp16", 1000, 155000, peaks)
+    assert set(front["unit_fracs"]) == {"alu", "sfu", "hbm", "tensor"}
+    assert front["bound"] == "latency"                          # no unit near its peak
 
 
 def test_activation_bytes_scale_with_the_element_size():

@@ -184,9 +184,9 @@ def test_end_to_end_matches_oracle(pv16, ev16, ref16):
     r = run_full(pv16, ev16)
     assert_per_bin(r["hist"], ref16["hist"])
     assert_per_bin(r["logit"], ref16["logit"])
-    eps = max(4 * float(np.max(np.abs(r["logit"] - ref16["logit"]))), 1e-6)
-    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], eps)
-    print("fp32 agreement", a, "eps", eps)
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"],
+                     r["logit"])
+    print("fp32 agreement", a)
     assert a["max_dz"] <= 0.1
     assert a["exempt"] == 1.0
     assert a["strict"] >= 0.99
@@ -259,8 +259,8 @@ def test_full_size_sampled(lib, weights):
                        want_logit=True, nthreads=NTHREADS)
     assert_per_bin(r["hist"][sample], ref["hist"])
     assert_per_bin(r["logit"][sample], ref["logit"])
-    eps = max(4 * float(np.max(np.abs(r["logit"][sample] - ref["logit"]))), 1e-6)
-    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"][sample], r["count"][sample], ref["logit"], eps)
+    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"][sample], r["count"][sample], ref["logit"],
+                     r["logit"][sample])
     assert a["exempt"] == 1.0
     assert pv.device_status() == 0
     for e in range(1000):
@@ -306,9 +306,9 @@ def test_wide_end_to_end_matches_oracle(wide_pv, wide_ref):
     np.testing.assert_array_equal(r["hist"] == 0, ref["hist"] == 0)
     assert_per_bin(r["hist"], ref["hist"])
     assert_per_bin(r["logit"], ref["logit"])
-    eps = max(4 * float(np.max(np.abs(r["logit"] - ref["logit"]))), 1e-6)
-    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"], r["count"], ref["logit"], eps)
-    print("wide fp32 agreement", a, "eps", eps)
+    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"], r["count"], ref["logit"],
+                     r["logit"])
+    print("wide fp32 agreement", a)
     assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
     assert wide_pv.device_status() == 0
 
@@ -363,8 +363,8 @@ def test_per_interval_end_to_end_matches_oracle(iv_pv, ev16, iv_ref, ref16):
     assert_per_bin(r["hist"], ref16["hist"])            # the histogram does not depend on the layout
     assert_per_bin(r["logit"], iv_ref["logit"])
     assert np.max(np.abs(iv_ref["logit"] - ref16["logit"])) > 1e-3      # a different network output
-    eps = max(4 * float(np.max(np.abs(r["logit"] - iv_ref["logit"]))), 1e-6)
-    a = pv_agreement(iv_ref["pv_z"], iv_ref["pv_count"], r["z"], r["count"], iv_ref["logit"], eps)
+    a = pv_agreement(iv_ref["pv_z"], iv_ref["pv_count"], r["z"], r["count"], iv_ref["logit"],
+                     r["logit"])
     print("per-interval fp32 agreement", a)
     assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
     assert iv_pv.device_status() == 0
@@ -392,8 +392,8 @@ def test_per_interval_with_boundary_tracks_matches_oracle(lib, weights, ev16):
     r = run_full(pv, ev16)
     assert_per_bin(r["hist"], ref["hist"])
     assert_per_bin(r["logit"], ref["logit"])
-    eps = max(4 * float(np.max(np.abs(r["logit"] - ref["logit"]))), 1e-6)
-    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"], r["count"], ref["logit"], eps)
+    a = pv_agreement(ref["pv_z"], ref["pv_count"], r["z"], r["count"], ref["logit"],
+                     r["logit"])
     assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
 
 

@@ -4,7 +4,8 @@
    exactly the points where the kernels store bf16 (tests/ref_torch64.unet_quantized):
    only float32-accumulation differences and the occasional one-ulp rounding flip remain.
 2. Against the FP64 oracle: per-bin error of the logits (reported and bounded) and the
-   PV-list agreement, strict and with the near-tie exemption at the measured error.
+   PV-list agreement, strict and with the near-tie exemption computed from the measured
+   per-bin logit differences (paper_2602_19959_gb300.agreement).
 3. Determinism and batch invariance, as for the FP32 form.
 """
 
@@ -112,12 +113,15 @@ def test_bf16_against_oracle(bf16, ev16, ref16):
            for e in range(16)]
     prob_err = np.max(np.abs(1 / (1 + np.exp(-r["logit"].astype(np.float64))) -
                              1 / (1 + np.exp(-ref16["logit"]))))
-    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
-    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"],
+                     r["logit"])
     print("bf16 per-bin logit err / max:", max(rel), "prob err:", prob_err, "agreement:", a)
     assert max(rel) <= 0.05
     assert a["max_dz"] <= 0.1
-    assert a["exempt"] >= 0.999
+    # every disagreement is a decision the measured per-bin differences can flip; BF16 misses
+    # the 99.9% strict bar (measured 99.15% on these events), the guard below catches a drop
+    assert a["exempt"] == 1.0
+    assert a["strict"] >= 0.985
 
 
 def test_bf16_deterministic_and_batch_invariant(bf16, ev16):
@@ -228,12 +232,15 @@ def test_fp8_against_oracle(fp8, ev16, ref16):
     r = run_full(fp8, ev16)
     rel = [np.max(np.abs(r["logit"][e] - ref16["logit"][e])) / np.max(np.abs(ref16["logit"][e]))
            for e in range(16)]
-    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
-    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"],
+                     r["logit"])
     print("fp8 per-bin logit err / max:", max(rel), "agreement:", a)
     assert max(rel) <= 0.2
     assert a["max_dz"] <= 0.1
-    assert a["exempt"] >= 0.999
+    # FP8 misses the 99.9% strict bar (measured 93.7%); every disagreement is explained by
+    # the measured per-bin differences
+    assert a["exempt"] == 1.0
+    assert a["strict"] >= 0.9
 
 
 def test_fp8_deterministic_and_batch_invariant(fp8, ev16):
@@ -292,13 +299,16 @@ def test_fp16_against_oracle(fp16, ev16, ref16):
                for e in range(16))
     rel = max(np.max(np.abs(r["logit"][e] - ref16["logit"][e])) / np.max(np.abs(ref16["logit"][e]))
               for e in range(16))
-    eps = float(np.max(np.abs(r["logit"] - ref16["logit"])))
-    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"], 2 * eps)
+    a = pv_agreement(ref16["pv_z"], ref16["pv_count"], r["z"], r["count"], ref16["logit"],
+                     r["logit"])
     print("fp16 histogram err / max:", hist, "per-bin logit err / max:", rel, "agreement:", a)
     assert hist <= 4e-3
     assert rel <= 1e-2
     assert a["max_dz"] <= 0.1
-    assert a["exempt"] >= 0.999
+    # the headline form: strict agreement at the 99.9% bar, and every disagreement a decision
+    # the measured per-bin differences can flip
+    assert a["strict"] >= 0.999
+    assert a["exempt"] == 1.0
 
 
 def test_fp16_deterministic_and_batch_invariant(fp16, ev16):
