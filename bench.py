@@ -12,7 +12,7 @@ device->host copy of the PV lists.
 
   python bench.py [--gpus N --steps K --warmup W] [--precision fp32|bf16|fp16|fp8]
   python bench.py --mode batch --events 50000     # one autotuned graph launch, uneven events
-  python bench.py --mode serve                    # Poisson arrivals at 20k..200k events/s
+  python bench.py --mode serve                    # Poisson arrivals at 20k..1.5M events/s
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
 
 The default line is the FP16 form (the paper's §5 proposal, the reduced form whose PV
@@ -457,15 +457,16 @@ def barrier(world):
     torch.cuda.synchronize()
 
 
-def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight):
-    """Poisson arrivals at `rate` events/s for `seconds` through pvf_serve_replay."""
+def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight, copy=False):
+    """Poisson arrivals at `rate` events/s for `seconds` through pvf_serve_replay; latency is
+    arrival -> the host seeing its batch complete (results readable on the host)."""
     rng = np.random.default_rng(seed)
     n = int(rate * seconds)
     arrivals = np.cumsum(rng.exponential(1e9 / rate, n)).astype(np.int64)
     req = (np.arange(n) % store.n_events).astype(np.int32)
     t0 = time.perf_counter()
     done, cnt, batches, _ = pv.serve_replay(store, arrivals, req, max_batch=max_batch,
-                                            max_inflight=max_inflight)
+                                            max_inflight=max_inflight, copy=copy)
     wall = time.perf_counter() - t0
     lat = (done - arrivals) / 1000.0
     return {"rate_offered": rate, "events": n, "seconds": seconds,
@@ -473,6 +474,7 @@ def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight):
             "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
             "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()),
             "batches": batches, "mean_batch": n / max(batches, 1), "wall_s": wall,
+            "form": "copy" if copy else "gather (zero-copy)",
             "under_400us_p99": bool(np.percentile(lat, 99) < 400.0)}
 
 
@@ -602,7 +604,7 @@ def run_step(args, weights, batch, rank, world, local):
         ps = make_finder(args, weights, args.precision, args.serve_batch,
                          max_pv_per_event=args.max_pv)
         line["serving"] = serve_sample(ps, store, args.serve_rate, args.serve_seconds, 7,
-                                       args.serve_batch, args.serve_inflight)
+                                       args.serve_batch, args.serve_inflight, copy=args.serve_copy)
         line["serving"]["workload"] = "uneven events (N_PV ~ U{1..12}, heavy-tailed background)"
         ps.close()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -643,19 +645,22 @@ def run_batch(args, weights):
 
 
 def run_serve(args, weights):
+    """Serving: Poisson arrivals at each offered rate for serve_seconds_full, through the
+    continuous-batching loop; one JSON line per rate."""
     import synth
     from paper_2602_19959_gb300 import build
     build()
     store = synth.generate_uneven(20000, 55)
+    pv = make_finder(args, weights, args.precision, args.serve_batch, max_pv_per_event=args.max_pv)
     for rate in args.rates:
-        pv = make_finder(args, weights, args.precision, args.serve_batch, max_pv_per_event=args.max_pv)
         r = serve_sample(pv, store, rate, args.serve_seconds_full, 100 + int(rate // 1000),
-                         args.serve_batch, args.serve_inflight)
+                         args.serve_batch, args.serve_inflight, copy=args.serve_copy)
         r.update({"metric": "serving latency", "dtype": args.precision,
                   "workload": "Poisson arrivals over 20000 stored uneven events (cycled)",
-                  "max_batch": args.serve_batch, "max_inflight": args.serve_inflight})
+                  "max_batch": args.serve_batch, "max_inflight": args.serve_inflight,
+                  "pool_bytes": pv.pool_bytes})
         print(json.dumps(r), flush=True)
-        pv.close()
+    pv.close()
 
 
 def main():
@@ -681,11 +686,15 @@ def main():
                     help="L2 flush buffer written between steps (0: none, for small profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="serving sample folded into the step line (0: none)")
-    ap.add_argument("--serve-rate", type=float, default=120000.0)
-    ap.add_argument("--serve-batch", type=int, default=128)
+    ap.add_argument("--serve-rate", type=float, default=870000.0,
+                    help="offered rate of that sample (5x the plain FP32 form's throughput)")
+    ap.add_argument("--serve-batch", type=int, default=512)
     ap.add_argument("--serve-inflight", type=int, default=2)
+    ap.add_argument("--serve-copy", action="store_true",
+                    help="serving: the copy form (device slots, per-bucket graphs)")
     ap.add_argument("--serve-seconds-full", type=float, default=10.0)
-    ap.add_argument("--rates", type=float, nargs="+", default=[20000, 60000, 120000, 200000])
+    ap.add_argument("--rates", type=float, nargs="+",
+                    default=[20000, 60000, 120000, 200000, 500000, 870000, 1200000, 1500000])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

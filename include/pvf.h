@@ -246,6 +246,21 @@ typedef struct pvf_graph pvf_graph;
 PVF_API pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks,
                                     const int32_t *event_offsets, int32_t n_events,
                                     float *out_pv_z, int32_t *out_pv_count, pvf_graph **out);
+/* The same with the event count read on the device at every launch: the graph covers up
+ * to max_n_events events and each launch processes the first *n_events of them (clamped
+ * to [0, max_n_events]), so one captured graph serves batches of any size without padding
+ * them with empty events. Only the first *n_events entries of out_pv_count (and their z
+ * lists) are written.
+ *   n_events  int32 the device reads (device memory, or pinned host memory mapped into
+ *             the device's address space), written before each launch; its value is
+ *             read by the first kernel of the launch, so it may change between launches
+ * Tensor-core forms (PVF_BF16, PVF_FP16, PVF_FP8_E4M3) only; PVF_FP32: UNSUPPORTED.
+ * This is the batching interface of §3's fixed-shape execution with a run-time batch
+ * size, as the serving loop below uses it. */
+PVF_API pvf_status pvf_graph_create_dynamic(pvf_handle *h, const pvf_tracks_soa *tracks,
+                                            const int32_t *event_offsets, const int32_t *n_events,
+                                            int32_t max_n_events, float *out_pv_z,
+                                            int32_t *out_pv_count, pvf_graph **out);
 PVF_API pvf_status pvf_graph_launch(pvf_graph *g, pvf_stream_t stream);
 PVF_API pvf_status pvf_graph_destroy(pvf_graph *g);
 
@@ -253,16 +268,24 @@ PVF_API pvf_status pvf_graph_destroy(pvf_graph *g);
  * Requests are events of a host-side event store, arriving at given times. Whenever
  * fewer than max_inflight batches are enqueued on the stream, the loop admits the queued
  * events that fit one in-flight slot (at most max_batch events and max_tracks_per_batch
- * tracks: the slot's memory), packs their tracks into pinned staging, and enqueues on
- * `stream` the host->device copies, the path, and the copies of PV counts and z lists
- * back. A batch is launched as soon as a slot is free and min_batch events are queued, or
- * the oldest queued event has waited max_wait_us, or no more arrivals remain.
- * By default the path runs as a CUDA graph: before the first arrival the loop captures,
- * for every slot, one graph per bucket of 1, 2, 4, ... events up to max_batch (tracks at
- * a fixed stride of max_tracks_per_batch), and a batch of k events launches the graph of
- * the smallest bucket >= k with the missing events empty. PVF_SERVE_STREAM_LAUNCH
- * enqueues pvf_infer instead. */
+ * tracks: the slot's memory), packs their tracks into the slot's pinned staging and
+ * enqueues the path on `stream`. A batch is launched as soon as a slot is free and
+ * min_batch events are queued, or the oldest queued event has waited max_wait_us, or no
+ * more arrivals remain.
+ * Gather form (default for the tensor-core forms on a device that can map host memory):
+ * before the first arrival the event store is copied into pinned host memory mapped into
+ * the device's address space (events as they would land in pinned receive buffers), and
+ * each slot gets one graph, captured then, that takes the batch's store indices and event
+ * count from a mapped record, reads the indexed events' tracks straight from the store
+ * and writes the PV counts and z lists into the record: a batch is k index writes and one
+ * graph launch, with no copies and no padding.
+ * Copy form (PVF_SERVE_COPY, and always for PVF_FP32): the staging is copied into the
+ * caller's device_slots and the results back, around the graph of the smallest bucket of
+ * 1, 2, 4, ... max_batch events that holds the batch (tracks at a fixed stride of
+ * max_tracks_per_batch, missing events empty). PVF_SERVE_STREAM_LAUNCH (copy form)
+ * enqueues pvf_infer instead of a graph. */
 #define PVF_SERVE_STREAM_LAUNCH 1
+#define PVF_SERVE_COPY 2
 typedef struct {
     int32_t max_batch;            /* events per launch, 1..max_events of the handle      */
     int32_t max_tracks_per_batch; /* tracks per launch; every stored event must fit       */
@@ -273,7 +296,8 @@ typedef struct {
     int32_t reserved[2];
 } pvf_serve_config;
 
-/* Device bytes the in-flight slots need (inputs and outputs of max_inflight batches). */
+/* Device bytes the in-flight slots of the copy form need (inputs and outputs of
+ * max_inflight batches); pvf_serve_replay requires them in every form. */
 PVF_API pvf_status pvf_serve_bytes_required(const pvf_serve_config *cfg, int32_t max_pv_per_event,
                                             size_t *out_bytes);
 
@@ -288,7 +312,8 @@ PVF_API pvf_status pvf_serve_bytes_required(const pvf_serve_config *cfg, int32_t
  *   out_batches                number of launches, or NULL
  * Pinned host staging (one slot's size per in-flight batch) and the graphs are created
  * for the call and freed before it returns; no device memory is allocated. The graphs use
- * the handle's pool like pvf_infer, so the handle serves one call at a time. */
+ * the handle's pool like pvf_infer, so the handle serves one call at a time. Synchronises
+ * stream before returning. */
 PVF_API pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg,
                                     const float *const *store_f, const int32_t *store_offsets,
                                     int32_t n_store, const int64_t *arrival_ns,

@@ -80,7 +80,8 @@ template <int NT, bool EDGE>
 __device__ __forceinline__ void validate_sort(const FrontArgs &a, int ge, int tid, int *scnt, int *sseg,
                                               int *srun, uint16_t *ssorted, uint8_t *sslice,
                                               int64_t &t0_out, int &nvalid_out) {
-    const int64_t t0 = a.offsets[ge], t1 = a.offsets[ge + 1];
+    const int src = a.ev_index ? a.ev_index[ge] : ge;      // gathered events: store index
+    const int64_t t0 = a.offsets[src], t1 = a.offsets[src + 1];
     const bool bypass = t0 < 0 || t1 < t0 || t1 > a.n_tracks || (t1 - t0) > a.max_tracks;
     const int n = bypass ? 0 : (int)(t1 - t0);
     if (tid == 0) {

@@ -133,8 +133,14 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     bool failed = false;
     uint32_t phase = 0;
 
+    // a device-side count is read here (features and offsets come from the caller, in
+    // stream order) and copied to device memory for the kernels after this one
+    const int n_ev = launch_events(a.n_dyn, a.ev_base, a.n_events);
+    if (a.n_dyn_copy && blockIdx.x == 0 && tid == 0)
+        *a.n_dyn_copy = *reinterpret_cast<const volatile int32_t *>(a.n_dyn);
+
     // persistent: the CTA walks the launch's events
-    for (int e = blockIdx.x; e < a.n_events; e += gridDim.x) {
+    for (int e = blockIdx.x; e < n_ev; e += gridDim.x) {
         const int ge = a.ev_base + e;
         if (a.hist_in) {
             const float *src = a.hist_in + (size_t)ge * kBins;

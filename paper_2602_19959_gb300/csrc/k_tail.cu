@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kThreads, CONV ? 2 : 8) k_tail(TailArgs a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // persistent: the CTA walks the launch's events
-    for (int e = blockIdx.x; e < a.n_events; e += gridDim.x) {
+    const int n_ev = launch_events(a.n_dyn, a.ev_base, a.n_events);
+    for (int e = blockIdx.x; e < n_ev; e += gridDim.x) {
         const int ge = a.ev_base + e;
         if constexpr (!CONV) {
             const float *src = a.logit_in + (size_t)(ge - a.logit_in_base) * kBins;

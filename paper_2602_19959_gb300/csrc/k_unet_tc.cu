@@ -163,9 +163,11 @@ struct TcArgs {
     float out_inv, mid_inv;             // fp8: 1 / scale of the stored output and of A2
     float *amax;                        // calibration: running max |x| per scale slot, or null
     int amax_out, amax_mid;             // slots of the stored output and of A2 (kScale*)
-    int n_events;
+    int n_events;                       // events of the launch (its capacity with n_dyn)
     int32_t *status;
     int32_t *sched;                     // [2]: next tile, finished CTAs (zero between launches)
+    const int32_t *n_dyn;               // nullable: device-side event count of the call
+    int dyn_base;                       // index of the launch's first event in the call
 };
 
 // Calibration: folds max |v| of 16 values (rows with valid = false count as 0) into the
@@ -771,14 +773,17 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     // previous kernel's output
     grid_dep_wait();
     grid_dep_launch();
+    // with a device-side count, the events of this launch are known from here on
+    TcArgs r = a;
+    r.n_events = launch_events(a.n_dyn, a.dyn_base, a.n_events);
 
     bool ok = true;
     if (warp == 0) {
-        if (lane == 0) ok = producer<C>(a, smem, bar, ring, abort);
+        if (lane == 0) ok = producer<C>(r, smem, bar, ring, abort);
     } else if (warp == 1) {
-        if (lane == 0) ok = mma_issuer<C>(a, smem, bar, tmem, ring, abort);
+        if (lane == 0) ok = mma_issuer<C>(r, smem, bar, tmem, ring, abort);
     } else {
-        ok = epilogue<C>(a, smem, bar, tmem, ring, abort, warp, lane);
+        ok = epilogue<C>(r, smem, bar, tmem, ring, abort, warp, lane);
     }
     if (!ok) {
         *abort = 1;
@@ -1006,8 +1011,8 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
 }
 
 template <int PREC>
-static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStream_t s,
-                          const ProfHook *prof) {
+static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, const int32_t *n_dyn, int dyn_base,
+                          cudaStream_t s, const ProfHook *prof) {
     using N = Net<PREC>;
     const float *sc = n.act_scale;
     auto inv = [&](int i) { return is16(PREC) ? 1.0f : 1.0f / sc[i]; };
@@ -1017,6 +1022,8 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStre
     cudaError_t err;
     TcArgs a{};
     a.n_events = ne;
+    a.n_dyn = n_dyn;
+    a.dyn_base = dyn_base;
     a.status = n.status;
     a.amax = n.amax;
     // one scheduler counter pair per kernel family (each launch leaves it at zero)
@@ -1052,13 +1059,13 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, cudaStre
     return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final");
 }
 
-cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, cudaStream_t s,
-                           const ProfHook *prof) {
+cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, const int32_t *n_dyn, int dyn_base,
+                           cudaStream_t s, const ProfHook *prof) {
     if (n <= 0) return cudaSuccess;
     switch (net.precision) {
-    case PVF_BF16: return run_tc<PVF_BF16>(net, b, n, s, prof);
-    case PVF_FP16: return run_tc<PVF_FP16>(net, b, n, s, prof);
-    case PVF_FP8_E4M3: return run_tc<PVF_FP8_E4M3>(net, b, n, s, prof);
+    case PVF_BF16: return run_tc<PVF_BF16>(net, b, n, n_dyn, dyn_base, s, prof);
+    case PVF_FP16: return run_tc<PVF_FP16>(net, b, n, n_dyn, dyn_base, s, prof);
+    case PVF_FP8_E4M3: return run_tc<PVF_FP8_E4M3>(net, b, n, n_dyn, dyn_base, s, prof);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -220,6 +220,9 @@ void slot_elems(int L0, int c0, int seqs, size_t *big, size_t *small) {
 }
 
 constexpr int kMaxIvChunk = 65535 / kSlices;
+// Byte offset, inside the 256-byte status block, of the device copy of a dynamic event
+// count (status word at 0, calibration maxima at 64, tile schedulers at 128..176).
+constexpr size_t kDynCountOff = 192;
 
 Plan make_plan(const pvf_config *c) {
     Plan p{};
@@ -306,6 +309,7 @@ struct pvf_handle {
 
 int pvf_handle_max_pv(const pvf_handle *h) { return h->cfg.max_pv_per_event; }
 int pvf_handle_max_events(const pvf_handle *h) { return h->cfg.max_events; }
+int pvf_handle_precision(const pvf_handle *h) { return h->cfg.precision; }
 
 extern "C" {
 
@@ -476,12 +480,16 @@ static bool aligned4(const void *p) { return reinterpret_cast<uintptr_t>(p) % 4 
 static bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
 // One chunk: front (steps 1-2 + enc1), UNet, tail (final conv + peaks).
+// n_dyn (tensor-core forms, whole path only): device-side event count of the call, read
+// by the front kernel and copied to a pool word for the kernels after it.
 static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
                              const float *hist_in, const float *logit_in, int ev_base, int n,
                              float *pv_z, int32_t *pv_count, float *hist_out, float *logit_out,
-                             bool run_front, bool run_unet, bool run_tail, cudaStream_t s) {
+                             bool run_front, bool run_unet, bool run_tail, cudaStream_t s,
+                             const int32_t *n_dyn = nullptr, const int32_t *ev_index = nullptr) {
     int32_t *status = reinterpret_cast<int32_t *>(h->pool + h->plan.status);
     int32_t *flags = reinterpret_cast<int32_t *>(h->pool + h->plan.ev_flag);
+    int32_t *n_copy = n_dyn ? reinterpret_cast<int32_t *>(h->pool + h->plan.status + kDynCountOff) : nullptr;
     const int prec = h->cfg.precision;
     cudaError_t err = cudaSuccess;
     const ProfHook *prof = h->prof.on ? &h->hook : nullptr;
@@ -510,6 +518,9 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.ev_flag = flags;
         a.status = status;
         a.amax = h->tc.amax;
+        a.n_dyn = n_dyn;
+        a.n_dyn_copy = n_copy;
+        a.ev_index = ev_index;
         if (prec == PVF_FP32) {
             err = launch_front(a, prec, h->front_smem, s);
         } else {
@@ -520,7 +531,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
     }
     if (run_unet) {
         if (prec == PVF_FP32) err = launch_unet_f32(h->cw, h->buf, n, h->cfg.per_interval != 0, s, prof);
-        else err = launch_unet_tc(h->tc, h->buf, n, s, prof);
+        else err = launch_unet_tc(h->tc, h->buf, n, n_copy, ev_base, s, prof);
         if (err != cudaSuccess) return err;
     }
     if (run_tail) {
@@ -546,6 +557,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         t.pv_count = pv_count;
         t.max_pv = h->cfg.max_pv_per_event;
         t.status = status;
+        t.n_dyn = n_copy;
         err = launch_tail(t, prec, s);
     }
     return err;
@@ -657,14 +669,17 @@ struct pvf_graph {
 
 extern "C" {
 
-pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
-                            int32_t n, float *pv_z, int32_t *pv_count, pvf_graph **out) {
+static pvf_status graph_create(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
+                               const int32_t *n_dyn, int32_t n, float *pv_z, int32_t *pv_count,
+                               pvf_graph **out, const int32_t *ev_index = nullptr) {
     if (!out) return PVF_ERR_INVALID_ARG;
     *out = nullptr;
     if (!h || n < 1 || n > h->cfg.max_events) return PVF_ERR_INVALID_ARG;
     if (!tracks_ok(tracks) || !offsets || !aligned4(offsets) || !pv_z || !aligned4(pv_z) ||
-        !pv_count || !aligned4(pv_count))
+        !pv_count || !aligned4(pv_count) || (n_dyn && !aligned4(n_dyn)))
         return PVF_ERR_INVALID_ARG;
+    if ((n_dyn || ev_index) && h->cfg.precision == PVF_FP32) return PVF_ERR_UNSUPPORTED;
+    if (ev_index && !aligned4(ev_index)) return PVF_ERR_INVALID_ARG;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PVF_ERR_CUDA;
     const bool prof = h->prof.on;
@@ -678,7 +693,7 @@ pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks, const i
         for (int c0 = 0; c0 < n && err == cudaSuccess; c0 += h->plan.chunk) {
             const int nc = n - c0 < h->plan.chunk ? n - c0 : h->plan.chunk;
             err = run_chunk(h, tracks, offsets, nullptr, nullptr, c0, nc, pv_z, pv_count, nullptr,
-                            nullptr, true, true, true, cs);
+                            nullptr, true, true, true, cs, n_dyn, ev_index);
         }
         cudaGraph_t graph = nullptr;
         const cudaError_t end = cudaStreamEndCapture(cs, &graph);
@@ -702,6 +717,31 @@ pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks, const i
     }
     *out = g;
     return PVF_OK;
+}
+
+pvf_status pvf_graph_create(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
+                            int32_t n, float *pv_z, int32_t *pv_count, pvf_graph **out) {
+    return graph_create(h, tracks, offsets, nullptr, n, pv_z, pv_count, out);
+}
+
+pvf_status graph_create_gather(pvf_handle *h, const pvf_tracks_soa *store, const int32_t *store_offsets,
+                               const int32_t *ev_index, const int32_t *n_events, int32_t max_n_events,
+                               float *pv_z, int32_t *pv_count, pvf_graph **out) {
+    if (!ev_index || !n_events) {
+        if (out) *out = nullptr;
+        return PVF_ERR_INVALID_ARG;
+    }
+    return graph_create(h, store, store_offsets, n_events, max_n_events, pv_z, pv_count, out, ev_index);
+}
+
+pvf_status pvf_graph_create_dynamic(pvf_handle *h, const pvf_tracks_soa *tracks, const int32_t *offsets,
+                                    const int32_t *n_events, int32_t max_n_events, float *pv_z,
+                                    int32_t *pv_count, pvf_graph **out) {
+    if (!n_events) {
+        if (out) *out = nullptr;
+        return PVF_ERR_INVALID_ARG;
+    }
+    return graph_create(h, tracks, offsets, n_events, max_n_events, pv_z, pv_count, out);
 }
 
 pvf_status pvf_graph_launch(pvf_graph *g, pvf_stream_t stream) {

@@ -141,6 +141,18 @@ template <> __device__ __forceinline__ float from_elem<__nv_fp8_e4m3>(__nv_fp8_e
     return float(v) * s;
 }
 
+// Events one launch processes. Without a device-side count (n_dyn null) that is the
+// launch's n_events. With one, *n_dyn is the event count of the whole call, read at run
+// time (so a captured graph serves any count up to its capacity), and the launch, which
+// covers events [base, base + n_events) of the call, processes the part below that count.
+// The word is written before the launch (by the host or by an earlier kernel of the
+// stream), so a volatile load sees the current value.
+__device__ __forceinline__ int launch_events(const int32_t *n_dyn, int base, int n_events) {
+    if (!n_dyn) return n_events;
+    const int n = *reinterpret_cast<const volatile int32_t *>(n_dyn) - base;
+    return n < 0 ? 0 : (n > n_events ? n_events : n);
+}
+
 // Rows per event of a padded activation tensor with L positions.
 __host__ __device__ __forceinline__ int64_t padded_rows(int L) { return (int64_t)L + 2 * kPad; }
 
@@ -192,6 +204,12 @@ struct FrontArgs {
     float *amax;                 // calibration: max |e1| into amax[0], or null
     int32_t *ev_flag;            // global [max_events]: 1 = bypassed
     int32_t *status;
+    const int32_t *ev_index;     // nullable: event e of the call is event ev_index[e] of the
+                                 // offsets array (a gather from a larger event store)
+    const int32_t *n_dyn;        // nullable: device-side event count of the call (any memory
+                                 // the device reads; see launch_events)
+    int32_t *n_dyn_copy;         // with n_dyn: pool word that receives *n_dyn, which the
+                                 // later kernels of the call read from device memory
 };
 
 struct TailArgs {
@@ -210,6 +228,7 @@ struct TailArgs {
     int32_t *pv_count;           // global [n_total]
     int32_t max_pv;
     int32_t *status;
+    const int32_t *n_dyn;        // nullable: device-side event count of the call
 };
 
 // Optional per-launch timing hook: begin/end bracket one kernel launch on stream s.
@@ -296,3 +315,12 @@ cudaError_t launch_unet_f32(const ConvF32Weights &w, const UnetBuffers &b, int n
 // Plan values of a handle, for the host runtime in other translation units.
 int pvf_handle_max_pv(const pvf_handle *h);
 int pvf_handle_max_events(const pvf_handle *h);
+int pvf_handle_precision(const pvf_handle *h);
+// A dynamic-count graph (pvf_graph_create_dynamic) whose event e is event ev_index[e] of a
+// larger store (tracks and store_offsets index the store; ev_index and n_events are read
+// on the device at each launch). For the serving loop.
+// (C linkage, not exported: the library is built with hidden visibility.)
+extern "C" pvf_status graph_create_gather(pvf_handle *h, const pvf_tracks_soa *store,
+                                          const int32_t *store_offsets, const int32_t *ev_index,
+                                          const int32_t *n_events, int32_t max_n_events, float *pv_z,
+                                          int32_t *pv_count, pvf_graph **out);

@@ -47,7 +47,9 @@ bool tc_supported(int precision);
 // computed for that device address) and fills net with the device pointers.
 bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const float *act_scale,
                      std::vector<unsigned char> &out, TcNet *net, unsigned char *dev_base);
-cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n_events, cudaStream_t s,
-                           const ProfHook *prof);
+// n_dyn (nullable): device-side event count of the call, of which this launch covers
+// events [dyn_base, dyn_base + n_events) (see launch_events).
+cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n_events, const int32_t *n_dyn,
+                           int dyn_base, cudaStream_t s, const ProfHook *prof);
 
 }  // namespace pvf

@@ -36,7 +36,8 @@ N_ACT_SCALES = 16
 EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex",
             "pvf_stage_histogram", "pvf_stage_unet", "pvf_stage_peaks",
             "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_calibrate",
-            "pvf_histogram_static", "pvf_graph_create", "pvf_graph_launch", "pvf_graph_destroy",
+            "pvf_histogram_static", "pvf_graph_create", "pvf_graph_create_dynamic",
+            "pvf_graph_launch", "pvf_graph_destroy",
             "pvf_serve_bytes_required", "pvf_serve_replay", "pvf_destroy", "pvf_status_str",
             "pvf_version")
 
@@ -64,6 +65,7 @@ class PvfServeConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 SERVE_STREAM_LAUNCH = 1
+SERVE_COPY = 2
 
 
 class PvfError(RuntimeError):
@@ -103,6 +105,8 @@ def load(path: str = None):
             "pvf_calibrate": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P]),
             "pvf_histogram_static": (S, [P, SZ, ctypes.POINTER(PvfTracks), P, I32, P, P, P]),
             "pvf_graph_create": (S, [P, ctypes.POINTER(PvfTracks), P, I32, P, P, ctypes.POINTER(P)]),
+            "pvf_graph_create_dynamic": (S, [P, ctypes.POINTER(PvfTracks), P, P, I32, P, P,
+                                             ctypes.POINTER(P)]),
             "pvf_graph_launch": (S, [P, P]),
             "pvf_graph_destroy": (S, [P]),
             "pvf_serve_bytes_required": (S, [ctypes.POINTER(PvfServeConfig), I32, ctypes.POINTER(SZ)]),
@@ -345,11 +349,25 @@ class PVFinder:
                                          z.data_ptr(), c.data_ptr(), ctypes.byref(g)), "pvf_graph_create")
         return Graph(self.lib, g, (features, offsets, out))
 
+    def capture_graph_dynamic(self, features, offsets, n_events, out):
+        """A CUDA graph of the whole launch sequence for these fixed buffers that reads
+        its event count from n_events (CUDA int32 tensor of one element) at each launch;
+        out covers its capacity, offsets.numel() - 1 events."""
+        tr = tracks_struct(features)
+        n = int(offsets.numel() - 1)
+        z, c = out
+        g = ctypes.c_void_p()
+        _check(self.lib.pvf_graph_create_dynamic(self.handle, ctypes.byref(tr), offsets.data_ptr(),
+                                                 n_events.data_ptr(), n, z.data_ptr(), c.data_ptr(),
+                                                 ctypes.byref(g)), "pvf_graph_create_dynamic")
+        return Graph(self.lib, g, (features, offsets, n_events, out))
+
     def serve_replay(self, store, arrival_ns, request_event, max_batch=128,
                      max_tracks_per_batch=None, max_inflight=2, min_batch=1, max_wait_us=0.0,
-                     want_z=False, graphs=True, stream=None):
+                     want_z=False, graphs=True, copy=False, stream=None):
         """Continuous-batching replay (pvf_serve_replay). store: an EventBatch (host SoA).
-        graphs=False enqueues pvf_infer per batch instead of the per-bucket CUDA graphs.
+        copy=True: the copy form (device slots and per-bucket graphs) instead of the
+        zero-copy form; graphs=False (copy form) enqueues pvf_infer per batch.
         Returns (done_ns int64 [n], pv_count int32 [n], batches, z [n, max_pv] or None)."""
         import torch
         feats = np.ascontiguousarray(store.features, dtype=np.float32)
@@ -360,7 +378,8 @@ class PVFinder:
         if max_tracks_per_batch is None:
             max_tracks_per_batch = int(max(np.diff(offs).max(), 1) * max_batch)
         cfg = PvfServeConfig(max_batch, max_tracks_per_batch, max_inflight, min_batch,
-                             float(max_wait_us), 0 if graphs else SERVE_STREAM_LAUNCH)
+                             float(max_wait_us),
+                             (0 if graphs else SERVE_STREAM_LAUNCH) | (SERVE_COPY if copy else 0))
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_serve_bytes_required(ctypes.byref(cfg), self.max_pv, ctypes.byref(need)),
                "pvf_serve_bytes_required")

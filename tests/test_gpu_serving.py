@@ -65,23 +65,79 @@ def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, pr
     g.close()
 
 
-@pytest.mark.parametrize("graphs,max_batch,inflight,precision",
-                         [(True, 32, 3, "bf16"), (True, 24, 1, "bf16"), (False, 32, 2, "bf16"),
-                          (True, 32, 2, "fp16")])
-def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, max_batch, inflight,
-                                                    precision):
-    """Per-bucket graphs (a batch of k events runs the graph of the next bucket with the
-    missing events empty; 24 is a bucket of its own) and stream launches give every
-    request the result it has alone."""
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
+def test_dynamic_graph_follows_the_device_side_count(PVFinder, weights, precision, request):
+    """One graph captured for 48 events, launched with 48, 17, 1, 0 and 30 events as its
+    device-side count: each launch gives pvf_infer's results on the first n events and
+    writes no count past them."""
+    kw = {}
+    if precision == "fp8":
+        cal = synth.generate_standard(512, 1)
+        pc = PVFinder(weights, precision="bf16", max_events=512, max_pv_per_event=8)
+        kw["fp8_act_scales"] = pc.calibrate(*to_cuda(cal))
+        pc.close()
+    b = synth.generate_uneven(48, 13)
+    pv = PVFinder(weights, precision=precision, max_events=48, chunk_events=16, max_pv_per_event=96, **kw)
+    feats, offs = to_cuda(b)
+    n_dev = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = pv.alloc_outputs(48)
+    g = pv.capture_graph_dynamic(feats, offs, n_dev, out)
+    zz, cc = pv.infer(feats, offs)
+    torch.cuda.synchronize()
+    ref_c, ref_z = cc.cpu().numpy(), zz.cpu().numpy()
+    for n in (48, 17, 1, 0, 30):
+        out[1].fill_(-7)
+        n_dev.fill_(n)
+        g.launch()
+        torch.cuda.synchronize()
+        gc, gz = out[1].cpu().numpy(), out[0].cpu().numpy()
+        np.testing.assert_array_equal(gc[:n], ref_c[:n])
+        assert np.all(gc[n:] == -7)
+        for e in range(n):
+            k = min(int(gc[e]), 96)
+            np.testing.assert_array_equal(gz[e, :k], ref_z[e, :k])
+    assert pv.device_status() == 0
+    g.close()
+
+
+def test_dynamic_graph_is_refused_by_the_float32_form(PVFinder, weights):
+    from paper_2602_19959_gb300.pvf import PvfError, PVF_ERR_UNSUPPORTED
+    pv = PVFinder(weights, precision="fp32", max_events=8)
+    b = synth.generate_uneven(8, 2)
+    feats, offs = to_cuda(b)
+    n_dev = torch.full((1,), 8, dtype=torch.int32, device="cuda")
+    with pytest.raises(PvfError) as ei:
+        pv.capture_graph_dynamic(feats, offs, n_dev, pv.alloc_outputs(8))
+    assert ei.value.code == PVF_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("graphs,copy,max_batch,inflight,precision",
+                         [(True, False, 32, 3, "bf16"), (True, False, 24, 1, "fp16"),
+                          (True, True, 32, 3, "bf16"), (True, True, 24, 1, "bf16"),
+                          (False, True, 32, 2, "bf16"), (True, False, 32, 2, "fp8"),
+                          (True, True, 16, 2, "fp32")])
+def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, copy, max_batch, inflight,
+                                                    precision, request):
+    """Zero-copy slots (mapped staging, one graph per slot with the count read on the
+    device), the copy form's per-bucket graphs (a batch of k events runs the graph of the
+    next bucket with the missing events empty; 24 is a bucket of its own) and stream
+    launches give every request the result it has alone."""
     store = synth.generate_uneven(40, 21)
     max_pv = 96
-    pv = PVFinder(weights, precision=precision, max_events=32, max_pv_per_event=max_pv)
+    kw = {}
+    if precision == "fp8":
+        cal = synth.generate_standard(512, 1)
+        pc = PVFinder(weights, precision="bf16", max_events=512, max_pv_per_event=8)
+        kw["fp8_act_scales"] = pc.calibrate(*to_cuda(cal))
+        pc.close()
+    pv = PVFinder(weights, precision=precision, max_events=32, max_pv_per_event=max_pv, **kw)
     rng = np.random.default_rng(5)
     n = 300
     arrivals = np.cumsum(rng.exponential(1e9 / 60000.0, n)).astype(np.int64)   # 60k events/s
     req = rng.integers(0, store.n_events, n).astype(np.int32)
     done, cnt, batches, z = pv.serve_replay(store, arrivals, req, max_batch=max_batch,
-                                            max_inflight=inflight, want_z=True, graphs=graphs)
+                                            max_inflight=inflight, want_z=True, graphs=graphs,
+                                            copy=copy)
     assert batches >= n // max_batch and np.all(done >= arrivals)
     ref_cnt, ref_z = alone(pv, store, max_pv)
     np.testing.assert_array_equal(cnt, ref_cnt[req])

@@ -143,9 +143,9 @@ def _serve_bytes(lib, max_pv=64, **kw):
 
 
 def test_serve_slot_sizing_and_validation(lib):
-    """A serving slot holds one batch: 9 feature rows of max_tracks_per_batch floats and
-    max_batch + 1 offsets, then the counts, then max_batch x max_pv z values, each part
-    256-byte aligned; max_inflight slots in all."""
+    """A serving slot of the copy form holds one batch: 9 feature rows of
+    max_tracks_per_batch floats and max_batch + 1 offsets, then the counts, then
+    max_batch x max_pv z values, each part 256-byte aligned; max_inflight slots in all."""
     align = lambda x: (x + 255) // 256 * 256
     slot = align(align(align(4 * 9 * 8000 + 4 * 33) + 4 * 32) + 4 * 32 * 64)
     st, n2 = _serve_bytes(lib)
