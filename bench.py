@@ -457,7 +457,7 @@ def barrier(world):
     torch.cuda.synchronize()
 
 
-def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight, copy=False):
+def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight, copy=False, lead_us=0.0):
     """Poisson arrivals at `rate` events/s for `seconds` through pvf_serve_replay; latency is
     arrival -> the host seeing its batch complete (results readable on the host)."""
     rng = np.random.default_rng(seed)
@@ -466,7 +466,8 @@ def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight, copy=F
     req = (np.arange(n) % store.n_events).astype(np.int32)
     t0 = time.perf_counter()
     done, cnt, batches, _ = pv.serve_replay(store, arrivals, req, max_batch=max_batch,
-                                            max_inflight=max_inflight, copy=copy)
+                                            max_inflight=max_inflight, copy=copy,
+                                            launch_lead_us=lead_us)
     wall = time.perf_counter() - t0
     lat = (done - arrivals) / 1000.0
     return {"rate_offered": rate, "events": n, "seconds": seconds,
@@ -474,7 +475,8 @@ def serve_sample(pv, store, rate, seconds, seed, max_batch, max_inflight, copy=F
             "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
             "p999_us": float(np.percentile(lat, 99.9)), "max_us": float(lat.max()),
             "batches": batches, "mean_batch": n / max(batches, 1), "wall_s": wall,
-            "form": "copy" if copy else "gather (zero-copy)",
+            "form": "copy" if copy else "gather (zero-copy)", "launch_lead_us": lead_us,
+            "max_batch": max_batch, "max_inflight": max_inflight,
             "under_400us_p99": bool(np.percentile(lat, 99) < 400.0)}
 
 
@@ -604,7 +606,8 @@ def run_step(args, weights, batch, rank, world, local):
         ps = make_finder(args, weights, args.precision, args.serve_batch,
                          max_pv_per_event=args.max_pv)
         line["serving"] = serve_sample(ps, store, args.serve_rate, args.serve_seconds, 7,
-                                       args.serve_batch, args.serve_inflight, copy=args.serve_copy)
+                                       args.serve_batch, args.serve_inflight, copy=args.serve_copy,
+                                       lead_us=args.serve_lead_us)
         line["serving"]["workload"] = "uneven events (N_PV ~ U{1..12}, heavy-tailed background)"
         ps.close()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -654,10 +657,10 @@ def run_serve(args, weights):
     pv = make_finder(args, weights, args.precision, args.serve_batch, max_pv_per_event=args.max_pv)
     for rate in args.rates:
         r = serve_sample(pv, store, rate, args.serve_seconds_full, 100 + int(rate // 1000),
-                         args.serve_batch, args.serve_inflight, copy=args.serve_copy)
+                         args.serve_batch, args.serve_inflight, copy=args.serve_copy,
+                         lead_us=args.serve_lead_us)
         r.update({"metric": "serving latency", "dtype": args.precision,
                   "workload": "Poisson arrivals over 20000 stored uneven events (cycled)",
-                  "max_batch": args.serve_batch, "max_inflight": args.serve_inflight,
                   "pool_bytes": pv.pool_bytes})
         print(json.dumps(r), flush=True)
     pv.close()
@@ -692,6 +695,9 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=2)
     ap.add_argument("--serve-copy", action="store_true",
                     help="serving: the copy form (device slots, per-bucket graphs)")
+    ap.add_argument("--serve-lead-us", type=float, default=0.0,
+                    help="serving: admit the next batch only when the running one is predicted "
+                         "to end within this many us (0: whenever a slot is free)")
     ap.add_argument("--serve-seconds-full", type=float, default=10.0)
     ap.add_argument("--rates", type=float, nargs="+",
                     default=[20000, 60000, 120000, 200000, 500000, 870000, 1200000, 1500000])

@@ -292,8 +292,14 @@ typedef struct {
     int32_t max_inflight;         /* batches enqueued at once, 1..16                      */
     int32_t min_batch;            /* >= 1                                                 */
     float max_wait_us;            /* batching window for the oldest queued event          */
-    int32_t flags;                /* 0 or PVF_SERVE_STREAM_LAUNCH                         */
-    int32_t reserved[2];
+    int32_t flags;                /* 0, PVF_SERVE_COPY, PVF_SERVE_COPY | STREAM_LAUNCH     */
+    float launch_lead_us;         /* > 0: while a batch runs, the next one is admitted only
+                                     once the running one is predicted to end within this
+                                     many us (its duration from a line through the graph's
+                                     times at 1 and max_batch events, measured before the
+                                     first arrival), so that it takes every request that
+                                     arrives meanwhile; 0: admit whenever a slot is free   */
+    int32_t reserved;
 } pvf_serve_config;
 
 /* Device bytes the in-flight slots of the copy form need (inputs and outputs of

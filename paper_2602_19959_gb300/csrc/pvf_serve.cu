@@ -188,6 +188,39 @@ pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg, const fl
         for (size_t b = 0; b < buckets.size() && st == PVF_OK; ++b)
             st = pvf_graph_create(h, &tr, doff, buckets[b], dz, dcnt, &sl.graph[b]);
     }
+    // launch timing (gather form): the device time of a batch of k events, on a line
+    // through the times measured here at 1 and MB events (store events 0, 1, ...)
+    double t_one_ns = 0.0, t_mb_ns = 0.0;
+    const bool lead = gather && cfg->launch_lead_us > 0.0f && st == PVF_OK;
+    if (lead) {
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) st = PVF_ERR_CUDA;
+        for (int rep = 0; rep < 4 && st == PVF_OK; ++rep)
+            for (int which = 0; which < 2 && st == PVF_OK; ++which) {
+                const int k = which ? MB : 1;
+                Slot &sl = slots[0];
+                int32_t *idx = reinterpret_cast<int32_t *>(sl.host + gl.index);
+                for (int i = 0; i < k; ++i) idx[i] = i % n_store;
+                *reinterpret_cast<volatile int32_t *>(sl.host + gl.count) = k;
+                float ms = 0.0f;
+                if (cudaEventRecord(ea, s) != cudaSuccess || pvf_graph_launch(sl.graph[0], stream_) != PVF_OK ||
+                    cudaEventRecord(eb, s) != cudaSuccess || cudaEventSynchronize(eb) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, ea, eb) != cudaSuccess) {
+                    st = PVF_ERR_CUDA;
+                    break;
+                }
+                if (rep == 0) continue;                      // the first launch warms up
+                double &t = which ? t_mb_ns : t_one_ns;
+                if (t == 0.0 || ms * 1e6 < t) t = ms * 1e6;   // fastest of three
+            }
+        if (ea) cudaEventDestroy(ea);
+        if (eb) cudaEventDestroy(eb);
+    }
+    auto predict_ns = [&](int k) {
+        return t_one_ns + (t_mb_ns - t_one_ns) * (double)(k - 1) / (double)(MB > 1 ? MB - 1 : 1);
+    };
+    const double lead_ns = 1000.0 * cfg->launch_lead_us;
+    double end_est = 0.0;              // predicted end (host ns) of the last enqueued batch
     std::vector<int32_t> batch_offsets(MB + 1);
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
@@ -221,9 +254,11 @@ pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg, const fl
             --ring_n;
         }
         if (st != PVF_OK) break;
-        // admission: a free slot and queued requests
+        // admission: a free slot and queued requests (and, with a launch lead, the running
+        // batch about to end, so that the next one takes everything that arrives before)
         const int queued = next_arr - q_head;
-        if (ring_n < nslots && queued > 0) {
+        const bool due = !lead || ring_n == 0 || end_est - (double)now <= lead_ns;
+        if (ring_n < nslots && queued > 0 && due) {
             const bool all_arrived = next_arr == n_requests;
             const bool waited = (double)(now - arrival_ns[q_head]) >= 1000.0 * cfg->max_wait_us;
             if (queued >= cfg->min_batch || waited || all_arrived) {
@@ -288,6 +323,7 @@ pvf_status pvf_serve_replay(pvf_handle *h, const pvf_serve_config *cfg, const fl
                 }
                 sl.r0 = q_head;
                 sl.r1 = q_head + k;
+                if (lead) end_est = (ring_n == 0 || end_est < (double)now ? (double)now : end_est) + predict_ns(k);
                 ++ring_n;
                 ++batches;
                 q_head += k;

@@ -62,7 +62,7 @@ class PvfServeConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("max_tracks_per_batch", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("min_batch", ctypes.c_int32),
                 ("max_wait_us", ctypes.c_float), ("flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("launch_lead_us", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 SERVE_STREAM_LAUNCH = 1
 SERVE_COPY = 2
@@ -364,10 +364,12 @@ class PVFinder:
 
     def serve_replay(self, store, arrival_ns, request_event, max_batch=128,
                      max_tracks_per_batch=None, max_inflight=2, min_batch=1, max_wait_us=0.0,
-                     want_z=False, graphs=True, copy=False, stream=None):
+                     want_z=False, graphs=True, copy=False, launch_lead_us=0.0, stream=None):
         """Continuous-batching replay (pvf_serve_replay). store: an EventBatch (host SoA).
         copy=True: the copy form (device slots and per-bucket graphs) instead of the
-        zero-copy form; graphs=False (copy form) enqueues pvf_infer per batch.
+        gather form; graphs=False (copy form) enqueues pvf_infer per batch.
+        launch_lead_us > 0: the next batch is admitted only once the running one is
+        predicted to end within that many microseconds.
         Returns (done_ns int64 [n], pv_count int32 [n], batches, z [n, max_pv] or None)."""
         import torch
         feats = np.ascontiguousarray(store.features, dtype=np.float32)
@@ -379,7 +381,8 @@ class PVFinder:
             max_tracks_per_batch = int(max(np.diff(offs).max(), 1) * max_batch)
         cfg = PvfServeConfig(max_batch, max_tracks_per_batch, max_inflight, min_batch,
                              float(max_wait_us),
-                             (0 if graphs else SERVE_STREAM_LAUNCH) | (SERVE_COPY if copy else 0))
+                             (0 if graphs else SERVE_STREAM_LAUNCH) | (SERVE_COPY if copy else 0),
+                             float(launch_lead_us))
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_serve_bytes_required(ctypes.byref(cfg), self.max_pv, ctypes.byref(need)),
                "pvf_serve_bytes_required")

@@ -96,7 +96,8 @@ def test_dynamic_graph_follows_the_device_side_count(PVFinder, weights, precisio
         for e in range(n):
             k = min(int(gc[e]), 96)
             np.testing.assert_array_equal(gz[e, :k], ref_z[e, :k])
-    assert pv.device_status() == 0
+    from paper_2602_19959_gb300.pvf import PVF_WARN_TRUNCATED
+    assert pv.device_status() in (0, PVF_WARN_TRUNCATED)        # 96 slots: some lists truncated
     g.close()
 
 
@@ -111,13 +112,14 @@ def test_dynamic_graph_is_refused_by_the_float32_form(PVFinder, weights):
     assert ei.value.code == PVF_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("graphs,copy,max_batch,inflight,precision",
-                         [(True, False, 32, 3, "bf16"), (True, False, 24, 1, "fp16"),
-                          (True, True, 32, 3, "bf16"), (True, True, 24, 1, "bf16"),
-                          (False, True, 32, 2, "bf16"), (True, False, 32, 2, "fp8"),
-                          (True, True, 16, 2, "fp32")])
+@pytest.mark.parametrize("graphs,copy,max_batch,inflight,precision,lead",
+                         [(True, False, 32, 3, "bf16", 0.0), (True, False, 24, 1, "fp16", 0.0),
+                          (True, False, 32, 2, "fp16", 20.0),
+                          (True, True, 32, 3, "bf16", 0.0), (True, True, 24, 1, "bf16", 0.0),
+                          (False, True, 32, 2, "bf16", 0.0), (True, False, 32, 2, "fp8", 0.0),
+                          (True, True, 16, 2, "fp32", 0.0)])
 def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, copy, max_batch, inflight,
-                                                    precision, request):
+                                                    precision, lead, request):
     """Zero-copy slots (mapped staging, one graph per slot with the count read on the
     device), the copy form's per-bucket graphs (a batch of k events runs the graph of the
     next bucket with the missing events empty; 24 is a bucket of its own) and stream
@@ -137,7 +139,7 @@ def test_serving_results_equal_alone_and_in_the_mix(PVFinder, weights, graphs, c
     req = rng.integers(0, store.n_events, n).astype(np.int32)
     done, cnt, batches, z = pv.serve_replay(store, arrivals, req, max_batch=max_batch,
                                             max_inflight=inflight, want_z=True, graphs=graphs,
-                                            copy=copy)
+                                            copy=copy, launch_lead_us=lead)
     assert batches >= n // max_batch and np.all(done >= arrivals)
     ref_cnt, ref_z = alone(pv, store, max_pv)
     np.testing.assert_array_equal(cnt, ref_cnt[req])

@@ -166,3 +166,4 @@ def test_config_struct_layout():
     assert P.PvfConfig.boundary_mm.offset == 20 and P.PvfConfig.unet_width.offset == 24
     assert P.PvfConfig.per_interval.offset == 28 and P.PvfConfig.fp8_act_scales.offset == 32
     assert ctypes.sizeof(P.PvfServeConfig) == 32 and P.PvfServeConfig.flags.offset == 20
+    assert P.PvfServeConfig.launch_lead_us.offset == 24
