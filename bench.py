@@ -692,7 +692,9 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=870000.0,
                     help="offered rate of that sample (5x the plain FP32 form's throughput)")
     ap.add_argument("--serve-batch", type=int, default=512)
-    ap.add_argument("--serve-inflight", type=int, default=2)
+    ap.add_argument("--serve-inflight", type=int, default=1,
+                    help="batches enqueued at once (1 measured lowest p99: the next batch takes "
+                         "every request that arrives while one runs)")
     ap.add_argument("--serve-copy", action="store_true",
                     help="serving: the copy form (device slots, per-bucket graphs)")
     ap.add_argument("--serve-lead-us", type=float, default=0.0,
