@@ -71,7 +71,7 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_, int EWG_ = 1,
-          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false>
+          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false, bool A2T_ = false>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = is16(PREC) ? 2 : 1;            // bytes per element
@@ -106,13 +106,19 @@ struct Cfg {
     static constexpr int N2 = EPI == EPI_UP ? 2 * CUP : 0;   // fused ConvT: n = r * CUP + co
     static constexpr int P2 = COUT / PW;                     // K-planes of the fused GEMM
     static constexpr int W2_BYTES = EPI == EPI_UP ? P2 * N2 * 16 : 0;
-    static constexpr int A2_BYTES = EPI == EPI_UP ? P2 * kTileM * 16 : 0;
+    // the fused ConvT's A operand (the conv output of the tile, quantised): in shared memory,
+    // or (A2T) in tensor memory, written by the epilogue with tcgen05.st and read by the
+    // MMA directly, which takes its traffic off the shared-memory pipe
+    static constexpr bool A2T = A2T_ && EPI == EPI_UP;
+    static constexpr int A2_BYTES = EPI == EPI_UP && !A2T ? P2 * kTileM * 16 : 0;
+    static constexpr int A2_COLS = A2T ? P2 * 4 : 0;         // a 16-byte plane row = 4 columns
     // accumulator buffer: the fused ConvT writes its result over the conv columns, which
     // the epilogue has read before the ConvT's operand is complete
     static constexpr int CONV_COLS = PAIRED ? 2 * COUT : COUT;      // E | O when paired
     static constexpr int COLS_BUF = CONV_COLS > N2 ? CONV_COLS : N2;
     static constexpr int UP_OFF = 0;
-    static constexpr int TMEM_COLS = pow2ceil(NB * COLS_BUF);
+    static constexpr int A2_COL0 = NB * COLS_BUF;            // A2 buffers after the accumulators
+    static constexpr int TMEM_COLS = pow2ceil(NB * COLS_BUF + 2 * A2_COLS);
     // float parameters kept in shared memory: bias, bias2, column scales, final conv
     static constexpr int NPAR = 2 * (COUT + N2) + (EPI == EPI_FINAL ? kFinalFloats : 0);
     static constexpr int OFF_W = 0;
@@ -140,7 +146,7 @@ struct Cfg {
     static_assert(OFF_PAR % 16 == 0 && COUT % 4 == 0 && N2 % 4 == 0, "parameters read as float4");
     static_assert(OFF_X % 16 == 0, "paired exchange in float4");
     static_assert(STAGES >= 2 && STAGES <= 6, "stages");
-    static_assert(NB == 2 || NB == 4, "accumulator buffers");
+    static_assert(NB >= 2 && NB <= 4, "accumulator buffers");
     static_assert(!PAIRED || (!PAIR && PIN % 2 == 0 && 2 * COUT <= 256 && EPI != EPI_POOL &&
                               (EWG <= 2 || EPI == EPI_UP)),
                   "tap pairing");
@@ -343,6 +349,26 @@ __device__ __forceinline__ void issue_up(uint32_t d2, uint32_t a2, uint32_t w2_b
     }
 }
 
+// The fused ConvT with its A operand in tensor memory (A2T): the K step kb reads the 8
+// columns holding channels [16 kb, 16 kb + 16) (16-bit; 32 e4m3 channels per step).
+template <class C>
+__device__ __forceinline__ void issue_up_ts(uint32_t d2, uint32_t a2_tmem, uint32_t w2_base) {
+#pragma unroll
+    for (int kb = 0; kb < C::P2 / 2; ++kb) {
+        const uint64_t bd = smem_desc(w2_base + 2 * kb * C::N2 * 16, C::N2 * 16, 128);
+        if constexpr (is16(C::PREC)) mma_f16_ts(d2, a2_tmem + 8 * kb, bd, C::IDESC2, kb != 0);
+        else mma_fp8_ts(d2, a2_tmem + 8 * kb, bd, C::IDESC2, kb != 0);
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void issue_up_any(uint32_t tmem, int bp, int ap, uint32_t a2_base, uint32_t w2_base) {
+    if constexpr (C::A2T)
+        issue_up_ts<C>(tmem + bp * C::COLS_BUF + C::UP_OFF, tmem + C::A2_COL0 + ap * C::A2_COLS, w2_base);
+    else
+        issue_up<C>(tmem + bp * C::COLS_BUF + C::UP_OFF, a2_base + ap * C::A2_BYTES, w2_base);
+}
+
 // One thread issues all MMAs. With a fused ConvT, the conv of tile i is issued before the
 // ConvT of tile i - 1, so the tensor core works while the epilogue turns tile i - 1's
 // conv accumulator into the shared-memory operand of its ConvT.
@@ -383,7 +409,7 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
                 const int bp = (i - 1) % C::NB, ap = (i - 1) & 1;
                 if (!mbar_wait(&a2full[ap], ((i - 1) >> 1) & 1, abort)) { ok = false; break; }
                 tc_fence_after();
-                issue_up<C>(tmem + bp * C::COLS_BUF + C::UP_OFF, a2_base + ap * C::A2_BYTES, w2_base);
+                issue_up_any<C>(tmem, bp, ap, a2_base, w2_base);
                 mma_commit(&t2full[bp]);
             }
         }
@@ -393,7 +419,7 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
             const int bp = (i - 1) % C::NB, ap = (i - 1) & 1;
             if (mbar_wait(&a2full[ap], ((i - 1) >> 1) & 1, abort)) {
                 tc_fence_after();
-                issue_up<C>(tmem + bp * C::COLS_BUF + C::UP_OFF, a2_base + ap * C::A2_BYTES, w2_base);
+                issue_up_any<C>(tmem, bp, ap, a2_base, w2_base);
                 mma_commit(&t2full[bp]);
             } else {
                 ok = false;
@@ -475,7 +501,8 @@ __device__ __forceinline__ bool paired_publish(uint32_t dcol, int c_beg, float *
 template <class C, int NC>
 __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
                                          const float *scs, uint32_t dcol, int c_beg, int ab, int e,
-                                         int p, int m, bool valid, const float *sx = nullptr) {
+                                         int p, int m, bool valid, const float *sx = nullptr,
+                                         uint32_t a2t = 0) {
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad;
     constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
 #pragma unroll 1
@@ -502,7 +529,22 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = leaky(fmaf(vv[16 * h + j], sc[j], bj[j]));
             }
-            if constexpr (C::EPI == EPI_UP) {
+            if constexpr (C::EPI == EPI_UP && C::A2T) {
+                // this row's 16 channels into its TMEM lane: 16-bit pairs (8 columns) or
+                // e4m3 quads (4 columns), the K order the MMA reads
+                if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
+                if constexpr (is16(C::PREC)) {
+                    using T = typename Elem<C::PREC>::T;
+                    uint32_t r[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) r[j] = pack2<T>(v[2 * j], v[2 * j + 1]);
+                    tmem_st<8>(a2t + c0 / 2, r);
+                } else {
+                    uint32_t r[4];
+                    pack_e4m3<16>(v, a.mid_inv, reinterpret_cast<unsigned char *>(r));
+                    tmem_st<4>(a2t + c0 / 4, r);
+                }
+            } else if constexpr (C::EPI == EPI_UP) {
                 if (a.amax) amax_fold(a.amax, a.amax_mid, v, valid);
                 unsigned char *a2 = smem + C::OFF_A2 + ab * C::A2_BYTES;
                 put16<C::PREC>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
@@ -586,6 +628,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
     const int m = q * 32 + lane;                    // tile row
     const int wg = (warp - 2) >> 2;                 // epilogue warpgroup
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
+    const uint32_t a2_lane = tmem + lane_field + C::A2_COL0;    // A2T: this warp's lanes of the A2 buffers
     constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
     constexpr bool ROLES = C::EPI == EPI_UP && C::EWG >= 2;
     const int ntiles = a.n_events * C::TPE;
@@ -622,8 +665,9 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                         return false;
                 }
                 epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
-                                           valid, sx);
-                fence_proxy_async_smem();           // A2 writes -> visible to the tensor core
+                                           valid, sx, a2_lane + ab * C::A2_COLS);
+                if constexpr (C::A2T) tmem_st_wait();   // A2 in TMEM complete before the MMA reads it
+                else fence_proxy_async_smem();          // A2 writes -> visible to the tensor core
                 tc_fence_before();
                 mbar_arrive(&a2full[ab]);
             } else {            // ConvT accumulator -> output; frees the buffer
@@ -690,8 +734,10 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             if constexpr (C::PAIRED) {
                 if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
             }
-            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx);
-            fence_proxy_async_smem();
+            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx, a2_lane + ab * C::A2_COLS);
+            if constexpr (C::A2T) tmem_st_wait();
+            else fence_proxy_async_smem();
+            tc_fence_before();
             mbar_arrive(&a2full[ab]);
             if (!mbar_wait(&t2full[b], ph_b, abort)) return false;
             tc_fence_after();
@@ -846,10 +892,14 @@ constexpr bool conv_paired(int li, int prec) { return (li == 3 || li == 4) && is
 template <int PREC> struct Net {
     using Enc2 = Cfg<PREC, 16, 0, 32, 2000, EPI_POOL, 0, 4, 1, 56, 2, false, true>;    // 6 CTAs per SM
     using Enc3 = Cfg<PREC, 32, 0, 64, 1000, EPI_POOL, 0, 4, 1, 80, 2, false, true>;    // 4
+    // the fused-ConvT kernels keep the ConvT operand in TMEM (three accumulator buffers
+    // leave room for its two buffers): 59 -> 55, 99 -> 96 and 77 -> 75 us (16-bit forms)
     using Enc4Up3 = Cfg<PREC, 64, 0, 128, 500, EPI_UP, 64, is16(PREC) ? 2 : 4,
-                        is16(PREC) ? 2 : 4, 96, 4>;                                  // 1
-    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 4, conv_paired(3, PREC)>; // 1 CTA/SM
-    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 4, conv_paired(4, PREC)>; // 2
+                        is16(PREC) ? 2 : 4, 96, 3, false, false, true>;              // 1
+    using Dec3Up2 = Cfg<PREC, 64, 64, 64, 1000, EPI_UP, 32, 3, 2, 128, 3, conv_paired(3, PREC), false,
+                        true>;                                                         // 1 CTA/SM
+    using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 3, conv_paired(4, PREC), false,
+                        true>;                                                         // 2
     using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 3, 1, 64, 4, conv_paired(5, PREC)>; // 5
 };
 
