@@ -155,17 +155,12 @@ def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_laun
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels that
-# can dominate a step, from one ncu capture of a 512-event step (the summaries under
-# profiles/ give the command), scaled to a launch of 1000 events (traffic grows with the
-# events). Keyed by (form, kernel, events per launch); the value is (bytes, source). A
+# can dominate a step, from ncu captures of the kernels as built (profiles/ gives the
+# commands). Keyed by (form, kernel, events per launch); the value is (bytes, source). A
 # kernel changed since its capture has no entry and reports null.
 NCU_TRAFFIC = {
-    ("bf16", "dec3_up2", 1000): ((131.740160e6 + 28.147712e6) * 1000 / 512,
-                                 "ncu --set full, 512-event step, scaled by 1000/512"),
-    ("bf16", "dec1_final", 1000): ((131.237888e6 + 4.603136e6) * 1000 / 512,
-                                   "ncu --set full, 512-event step, scaled by 1000/512"),
-    ("bf16", "dec2_up1", 1000): ((131.397376e6 + 28.666624e6) * 1000 / 512,
-                                 "ncu --set full, 512-event step, scaled by 1000/512"),
+    ("fp16", "dec3_up2", 1000): ((257.178880e6 + 90.632448e6),
+                                 "ncu --set full of one 1000-event launch (profiles/dec3_up2_fp16_1000ev.md)"),
 }
 
 

@@ -451,13 +451,8 @@ template <class C, int W>
 __device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *sx, int q, int lane,
                                             float (&v)[W]) {
     float o[W];
-    if constexpr (W == 32) {
-        tmem_ld32(dcol + c0, v);
-        tmem_ld32(dcol + C::COUT + c0, o);
-    } else {
-        tmem_ld16(dcol + c0, v);
-        tmem_ld16(dcol + C::COUT + c0, o);
-    }
+    if constexpr (W == 32) tmem_ld32x2(dcol + c0, dcol + C::COUT + c0, v, o);
+    else tmem_ld16x2(dcol + c0, dcol + C::COUT + c0, v, o);
 #pragma unroll
     for (int j = 0; j < W; ++j) o[j] = __shfl_down_sync(0xffffffffu, o[j], 1);
     if (lane == 31) {     // row 32 q + 31: its O[m + 1] is the next quarter's first row
