@@ -73,6 +73,18 @@ typedef enum {
                           the f16 range saturate to +-65504 (NaN stays NaN).           */
 } pvf_precision;
 
+/* Launch schedule: how many CTAs per SM each persistent kernel family launches (its grid
+ * is that times the SM count, capped by its work). 0 = as many as fit at once (the
+ * default); values above what fits are clamped to it. These are the autotuner's
+ * parameters (the events per CTA of the front follow from its grid); results do not
+ * depend on them. */
+typedef struct {
+    int32_t front_ctas_per_sm;     /* front kernel (steps 1-2 + enc1): 1..2                    */
+    int32_t conv_ctas_per_sm[6];   /* tensor-core forms: enc2, enc3, enc4_up3, dec3_up2,
+                                      dec2_up1, dec1_final                                    */
+    int32_t tail_ctas_per_sm;      /* peak finder: 1..8                                         */
+} pvf_schedule;
+
 /* Creation-time plan (§3: TensorSpec freezing batch dimensions, channels, length and
  * data type at initialisation). Everything is frozen at pvf_create. */
 typedef struct {
@@ -103,6 +115,9 @@ typedef struct {
     const float *fp8_act_scales;   /* host, PVF_FP8_E4M3 only: PVF_N_ACT_SCALES per-tensor
                                       input scales (amax / 448), or NULL to use
                                       pvf_calibrate before the first pvf_infer              */
+    const pvf_schedule *schedule;  /* host, copied at pvf_create, or NULL: the defaults (a
+                                      table written by the autotuner goes here); negative
+                                      entries: INVALID_ARG                                   */
 } pvf_config;
 
 #define PVF_N_FEATURES 9

@@ -191,6 +191,7 @@ cudaError_t launch_front_t(const FrontArgs &a, size_t smem, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     int per_sm = (int)((228 * 1024) / (smem + 1024));
     if (per_sm > 2) per_sm = 2;
+    if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;

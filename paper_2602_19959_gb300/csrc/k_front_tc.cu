@@ -318,8 +318,11 @@ cudaError_t launch_front_tc_k(const FrontArgs &a, cudaStream_t s) {
     cudaError_t err = current_device_sms(&sms);
     if (err == cudaSuccess) err = prepare_kernel((const void *)k_front_tc<PREC, EDGE>, smem, nullptr);
     if (err != cudaSuccess) return err;
-    const int per_sm = (int)((228 * 1024) / (smem + 1024));
-    int grid = sms * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
+    int per_sm = (int)((228 * 1024) / (smem + 1024));
+    if (per_sm > 2) per_sm = 2;
+    if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;
     k_front_tc<PREC, EDGE><<<grid, kT, smem, s>>>(a);
     return cudaGetLastError();

@@ -176,7 +176,8 @@ cudaError_t launch_tail(const TailArgs &a, int precision, cudaStream_t s) {
     int sms = 0;
     const cudaError_t err = current_device_sms(&sms);
     if (err != cudaSuccess) return err;
-    const int per_sm = a.logit_in ? 8 : 2;
+    int per_sm = a.logit_in ? 8 : 2;
+    if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
     dim3 grid(a.n_events < per_sm * sms ? a.n_events : per_sm * sms), block(kThreads);
     if (a.logit_in) return launch_pdl(k_tail<false, kC0>, grid, block, 0, s, a);
     // the final conv runs here in the FP32 form only (the tensor-core forms run it in

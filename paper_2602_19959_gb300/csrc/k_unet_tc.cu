@@ -843,8 +843,9 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     }
 }
 
+// cap: the launch schedule's CTAs per SM (0 = as many as fit)
 template <class C>
-cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, const char *name) {
+cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, const char *name, int cap) {
     if (a.n_events <= 0) return cudaSuccess;
     // shared memory request padded so that the CTAs resident on one SM never ask for more
     // than the 512 TMEM columns: tcgen05.alloc would otherwise wait for a neighbour
@@ -868,6 +869,7 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
     int per_sm = by_regs < by_smem ? by_regs : by_smem;
     if (by_threads < per_sm) per_sm = by_threads;
     if (kMaxByTmem < per_sm) per_sm = kMaxByTmem;
+    if (cap > 0 && cap < per_sm) per_sm = cap;
     if (per_sm < 1) per_sm = 1;
     const int ntiles = a.n_events * C::TPE;
     int grid = sms * per_sm;
@@ -1077,31 +1079,31 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, const in
     // enc2: p1 (s0) -> e2, p2 (s1)
     a.inA = U(b.s0); a.inB = nullptr; a.out = U(b.e2); a.outp = U(b.s1);
     a.w = W(0); a.bias = n.b[0]; a.cs = cs(0); a.out_inv = inv(kScaleL2); a.amax_out = kScaleL2;
-    if ((err = launch_conv<typename N::Enc2>(a, s, prof, "enc2")) != cudaSuccess) return err;
+    if ((err = launch_conv<typename N::Enc2>(a, s, prof, "enc2", n.ctas_per_sm[0])) != cudaSuccess) return err;
     // enc3: p2 (s1) -> e3, p3 (s0)
     a.inA = U(b.s1); a.out = U(b.e3); a.outp = U(b.s0); a.sched = sched(1);
     a.w = W(1); a.bias = n.b[1]; a.cs = cs(1); a.out_inv = inv(kScaleL3); a.amax_out = kScaleL3;
-    if ((err = launch_conv<typename N::Enc3>(a, s, prof, "enc3")) != cudaSuccess) return err;
+    if ((err = launch_conv<typename N::Enc3>(a, s, prof, "enc3", n.ctas_per_sm[1])) != cudaSuccess) return err;
     // enc4 + up3: p3 (s0) -> u3 (up)
     a.inA = U(b.s0); a.out = U(b.up); a.outp = nullptr; a.sched = sched(2);
     a.w = W(2); a.bias = n.b[2]; a.cs = cs(2); a.w2 = W(6); a.bias2 = n.b[6]; a.cs2 = cs(6);
     a.mid_inv = inv(kScaleE4); a.out_inv = inv(kScaleL3); a.amax_mid = kScaleE4; a.amax_out = kScaleL3;
-    if ((err = launch_conv<typename N::Enc4Up3>(a, s, prof, "enc4_up3")) != cudaSuccess) return err;
+    if ((err = launch_conv<typename N::Enc4Up3>(a, s, prof, "enc4_up3", n.ctas_per_sm[2])) != cudaSuccess) return err;
     // dec3 + up2: [u3 (up), e3] -> u2 (deep)
     a.inA = U(b.up); a.inB = U(b.e3); a.out = U(b.deep); a.sched = sched(3);
     a.w = W(3); a.bias = n.b[3]; a.cs = cs(3); a.w2 = W(7); a.bias2 = n.b[7]; a.cs2 = cs(7);
     a.mid_inv = inv(kScaleD3); a.out_inv = inv(kScaleL2); a.amax_mid = kScaleD3; a.amax_out = kScaleL2;
-    if ((err = launch_conv<typename N::Dec3Up2>(a, s, prof, "dec3_up2")) != cudaSuccess) return err;
+    if ((err = launch_conv<typename N::Dec3Up2>(a, s, prof, "dec3_up2", n.ctas_per_sm[3])) != cudaSuccess) return err;
     // dec2 + up1: [u2 (deep), e2] -> u1 (up)
     a.inA = U(b.deep); a.inB = U(b.e2); a.out = U(b.up); a.sched = sched(4);
     a.w = W(4); a.bias = n.b[4]; a.cs = cs(4); a.w2 = W(8); a.bias2 = n.b[8]; a.cs2 = cs(8);
     a.mid_inv = inv(kScaleD2); a.out_inv = inv(kScaleL1); a.amax_mid = kScaleD2; a.amax_out = kScaleL1;
-    if ((err = launch_conv<typename N::Dec2Up1>(a, s, prof, "dec2_up1")) != cudaSuccess) return err;
+    if ((err = launch_conv<typename N::Dec2Up1>(a, s, prof, "dec2_up1", n.ctas_per_sm[4])) != cudaSuccess) return err;
     // dec1 + final conv: [u1 (up), e1] -> logits (float32)
     a.inA = U(b.up); a.inB = U(b.e1); a.out = nullptr; a.w2 = nullptr; a.bias2 = nullptr; a.sched = sched(5);
     a.cs2 = nullptr; a.logits = b.logits; a.final_w = n.final_w; a.amax_out = kScaleD1;
     a.w = W(5); a.bias = n.b[5]; a.cs = cs(5);
-    return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final");
+    return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final", n.ctas_per_sm[5]);
 }
 
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, const int32_t *n_dyn, int dyn_base,

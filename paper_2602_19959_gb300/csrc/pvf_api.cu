@@ -203,6 +203,11 @@ pvf_status check_config(const pvf_config *c) {
     if (c->unet_width == kC0Max && c->precision != PVF_FP32) return PVF_ERR_UNSUPPORTED;
     if (c->per_interval != 0 && c->per_interval != 1) return PVF_ERR_INVALID_ARG;
     if (c->per_interval && (c->precision != PVF_FP32 || c->unet_width == kC0Max)) return PVF_ERR_UNSUPPORTED;
+    if (c->schedule) {
+        const pvf_schedule &q = *c->schedule;
+        if (q.front_ctas_per_sm < 0 || q.tail_ctas_per_sm < 0) return PVF_ERR_INVALID_ARG;
+        for (int k = 0; k < 6; ++k) if (q.conv_ctas_per_sm[k] < 0) return PVF_ERR_INVALID_ARG;
+    }
     return PVF_OK;
 }
 
@@ -305,6 +310,7 @@ struct pvf_handle {
     UnetBuffers buf;
     TcNet tc;
     float act_scale[PVF_N_ACT_SCALES];
+    pvf_schedule sched;                     // launch schedule (zeros: the defaults)
 };
 
 int pvf_handle_max_pv(const pvf_handle *h) { return h->cfg.max_pv_per_event; }
@@ -357,6 +363,9 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
     if (!h) return PVF_ERR_INVALID_ARG;
     h->cfg = *cfg;
     h->cfg.fp8_act_scales = nullptr;
+    h->cfg.schedule = nullptr;
+    h->sched = cfg->schedule ? *cfg->schedule : pvf_schedule{};
+    for (int k = 0; k < 6; ++k) h->tc.ctas_per_sm[k] = h->sched.conv_ctas_per_sm[k];
     h->plan = plan;
     h->pool = static_cast<unsigned char *>(pool);
     h->front_smem = front_smem_bytes(cfg->max_tracks_per_event, cfg->boundary_mm);
@@ -521,6 +530,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         a.n_dyn = n_dyn;
         a.n_dyn_copy = n_copy;
         a.ev_index = ev_index;
+        a.ctas_per_sm = h->sched.front_ctas_per_sm;
         if (prec == PVF_FP32) {
             err = launch_front(a, prec, h->front_smem, s);
         } else {
@@ -558,6 +568,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
         t.max_pv = h->cfg.max_pv_per_event;
         t.status = status;
         t.n_dyn = n_copy;
+        t.ctas_per_sm = h->sched.tail_ctas_per_sm;
         err = launch_tail(t, prec, s);
     }
     return err;

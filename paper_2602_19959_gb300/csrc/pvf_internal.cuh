@@ -210,6 +210,7 @@ struct FrontArgs {
                                  // the device reads; see launch_events)
     int32_t *n_dyn_copy;         // with n_dyn: pool word that receives *n_dyn, which the
                                  // later kernels of the call read from device memory
+    int32_t ctas_per_sm;         // launch schedule: 0 = as many as fit
 };
 
 struct TailArgs {
@@ -229,6 +230,7 @@ struct TailArgs {
     int32_t max_pv;
     int32_t *status;
     const int32_t *n_dyn;        // nullable: device-side event count of the call
+    int32_t ctas_per_sm;         // launch schedule: 0 = as many as fit
 };
 
 // Optional per-launch timing hook: begin/end bracket one kernel launch on stream s.

@@ -42,12 +42,29 @@ EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex"
             "pvf_version")
 
 
+class PvfSchedule(ctypes.Structure):
+    _fields_ = [("front_ctas_per_sm", ctypes.c_int32), ("conv_ctas_per_sm", ctypes.c_int32 * 6),
+                ("tail_ctas_per_sm", ctypes.c_int32)]
+
+    CONV = ("enc2", "enc3", "enc4_up3", "dec3_up2", "dec2_up1", "dec1_final")
+
+    @classmethod
+    def from_dict(cls, d: dict):
+        """{"front": n, "enc2": n, ..., "dec1_final": n, "tail": n} (missing keys: 0 = default)."""
+        q = cls()
+        q.front_ctas_per_sm = int(d.get("front", 0))
+        q.tail_ctas_per_sm = int(d.get("tail", 0))
+        for i, k in enumerate(cls.CONV):
+            q.conv_ctas_per_sm[i] = int(d.get(k, 0))
+        return q
+
+
 class PvfConfig(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_events", ctypes.c_int32),
                 ("max_tracks_per_event", ctypes.c_int32), ("max_pv_per_event", ctypes.c_int32),
                 ("chunk_events", ctypes.c_int32), ("boundary_mm", ctypes.c_float),
                 ("unet_width", ctypes.c_int32), ("per_interval", ctypes.c_int32),
-                ("fp8_act_scales", ctypes.c_void_p)]
+                ("fp8_act_scales", ctypes.c_void_p), ("schedule", ctypes.c_void_p)]
 
 
 class PvfTracks(ctypes.Structure):
@@ -139,7 +156,7 @@ def _check(code: int, where: str, allow_warn: bool = False):
 
 def make_config(precision="fp32", max_events=1, max_tracks_per_event=2048, max_pv_per_event=64,
                 chunk_events=0, fp8_act_scales=None, boundary_mm=0.0, unet_width=0,
-                per_interval=False):
+                per_interval=False, schedule=None):
     cfg = PvfConfig()
     cfg.boundary_mm = boundary_mm
     cfg.unet_width = unet_width
@@ -149,10 +166,15 @@ def make_config(precision="fp32", max_events=1, max_tracks_per_event=2048, max_p
     cfg.max_tracks_per_event = max_tracks_per_event
     cfg.max_pv_per_event = max_pv_per_event
     cfg.chunk_events = chunk_events
-    keep = None
+    keep = []
     if fp8_act_scales is not None:
-        keep = np.ascontiguousarray(fp8_act_scales, dtype=np.float32)
-        cfg.fp8_act_scales = keep.ctypes.data
+        scales = np.ascontiguousarray(fp8_act_scales, dtype=np.float32)
+        keep.append(scales)
+        cfg.fp8_act_scales = scales.ctypes.data
+    if schedule is not None:
+        q = schedule if isinstance(schedule, PvfSchedule) else PvfSchedule.from_dict(schedule)
+        keep.append(q)
+        cfg.schedule = ctypes.addressof(q)
     return cfg, keep
 
 
@@ -239,19 +261,21 @@ class PVFinder:
     the band in which a track also fills the neighbouring slice (0: none).
     per_interval: each interval runs the UNet as its own 104-bin sequence (float32 form,
     width 16). Width 32 and per_interval are float32 only; other forms raise PvfError
-    with PVF_ERR_UNSUPPORTED."""
+    with PVF_ERR_UNSUPPORTED. schedule: launch schedule (a dict of CTAs per SM per kernel
+    family, e.g. the autotuner's table; None: the defaults)."""
 
     def __init__(self, weights: dict, precision="fp32", max_events=1024,
                  max_tracks_per_event=2048, max_pv_per_event=64, chunk_events=0,
                  fp8_act_scales=None, device=None, stream=None, boundary_mm=0.0,
-                 per_interval=False):
+                 per_interval=False, schedule=None):
         import torch
         self.lib = load()
         self.device = torch.device(device or "cuda")
         # the UNet base width follows the weights (the blob records it too)
         self.cfg, self._keep = make_config(precision, max_events, max_tracks_per_event,
                                            max_pv_per_event, chunk_events, fp8_act_scales,
-                                           boundary_mm, unet_width(weights), per_interval)
+                                           boundary_mm, unet_width(weights), per_interval,
+                                           schedule)
         need = ctypes.c_size_t(0)
         _check(self.lib.pvf_pool_bytes_required(ctypes.byref(self.cfg), ctypes.byref(need)),
                "pvf_pool_bytes_required")

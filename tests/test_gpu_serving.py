@@ -65,6 +65,27 @@ def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, pr
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_launch_schedule_changes_nothing_but_the_grids(PVFinder, weights, precision):
+    """Every kernel walks its work whatever its grid, and no sum depends on which CTA takes
+    which event or tile: results are bit for bit the same under any launch schedule."""
+    b = synth.generate_uneven(96, 17)
+    feats, offs = to_cuda(b)
+    outs = []
+    for sched in (None, {"front": 1, "enc2": 2, "enc3": 1, "dec2_up1": 1, "dec1_final": 2, "tail": 1},
+                  {"front": 2, "enc2": 99, "dec1_final": 3, "tail": 4}):
+        pv = PVFinder(weights, precision=precision, max_events=96, max_pv_per_event=96, schedule=sched)
+        hist = torch.zeros((96, 4000), device="cuda")
+        logit = torch.zeros((96, 4000), device="cuda")
+        z, c = pv.infer(feats, offs, hist=hist, logit=logit)
+        torch.cuda.synchronize()
+        outs.append((hist.cpu().numpy(), logit.cpu().numpy(), c.cpu().numpy()))
+        pv.close()
+    for o in outs[1:]:
+        for x, y in zip(o, outs[0]):
+            np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
 def test_dynamic_graph_follows_the_device_side_count(PVFinder, weights, precision, request):
     """One graph captured for 48 events, launched with 48, 17, 1, 0 and 30 events as its

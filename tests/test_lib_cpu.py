@@ -69,6 +69,9 @@ def test_pool_bytes_required_and_config_validation(lib):
     cfg, _ = P.make_config(precision="fp32", max_events=10, unet_width=32, per_interval=True)
     out = ctypes.c_size_t(0)
     assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
+    # a launch schedule changes grids only: the plan is the same
+    sched = {"front": 1, "enc2": 3, "dec3_up2": 1, "tail": 4}
+    assert P.pool_bytes_required(precision="bf16", max_events=1000, schedule=sched) == bf16
     # the per-interval layout: 40 sequences of 104 bins per event (e4: 17 rows x 128 channels)
     iv = P.pool_bytes_required(precision="fp32", max_events=1000, per_interval=True)
     assert 1.25 * fp32 < iv < 1.45 * fp32
@@ -76,7 +79,8 @@ def test_pool_bytes_required_and_config_validation(lib):
                 dict(max_pv_per_event=0), dict(chunk_events=-1), dict(precision=7),
                 dict(boundary_mm=-0.1), dict(boundary_mm=5.0), dict(boundary_mm=float("nan")),
                 dict(unet_width=24), dict(unet_width=64), dict(unet_width=-16),
-                dict(per_interval=2), dict(per_interval=-1)):
+                dict(per_interval=2), dict(per_interval=-1), dict(schedule={"front": -1}),
+                dict(schedule={"dec3_up2": -2}), dict(schedule={"tail": -1})):
         kw = dict(precision="fp32", max_events=10)
         kw.update(bad)
         cfg, _ = P.make_config(**kw)
@@ -162,7 +166,8 @@ def test_serve_slot_sizing_and_validation(lib):
 
 def test_config_struct_layout():
     """The ctypes mirrors of the C structs keep the header's sizes and offsets."""
-    assert ctypes.sizeof(P.PvfConfig) == 40
+    assert ctypes.sizeof(P.PvfConfig) == 48 and P.PvfConfig.schedule.offset == 40
+    assert ctypes.sizeof(P.PvfSchedule) == 32
     assert P.PvfConfig.boundary_mm.offset == 20 and P.PvfConfig.unet_width.offset == 24
     assert P.PvfConfig.per_interval.offset == 28 and P.PvfConfig.fp8_act_scales.offset == 32
     assert ctypes.sizeof(P.PvfServeConfig) == 32 and P.PvfServeConfig.flags.offset == 20
