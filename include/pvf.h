@@ -209,6 +209,19 @@ PVF_API pvf_status pvf_calibrate(pvf_handle *h, const pvf_tracks_soa *tracks,
  * Synchronises stream. */
 PVF_API pvf_status pvf_last_device_status(pvf_handle *h, int32_t *out_status, pvf_stream_t stream);
 
+/* Failure detection (§3 bounds every device-side wait; the paper has no test counterpart):
+ * runs the tensor-core enc2 kernel on the handle's first n_events events with its MMA
+ * thread waiting, for limit_us microseconds, on a barrier that nothing arrives on. The wait
+ * gives up, the kernel raises PVF_ERR_TIMEOUT in the device status word, waits (bounded)
+ * for its own copies in flight, frees its tensor memory and returns; the handle stays
+ * usable. For tests of the bounded-wait path (every production wait gives up after 1 s).
+ *   n_events  1..min(max_events, chunk_events); limit_us 1..100000
+ * Errors: PVF_ERR_INVALID_ARG; PVF_ERR_UNSUPPORTED for PVF_FP32 (no tensor-core waits).
+ * Asynchronous on stream; read the status with pvf_last_device_status. The kernel writes
+ * the handle's activation buffers: run pvf_infer again before reading results. */
+PVF_API pvf_status pvf_test_wait_timeout(pvf_handle *h, int32_t n_events, uint32_t limit_us,
+                                         pvf_stream_t stream);
+
 /* Per-kernel timing (CUDA events recorded around every kernel launch on the launch
  * stream), for profiling only. pvf_profile_enable(h, 1) creates the events (host-side
  * driver objects, no device memory) and starts recording; 0 stops. */

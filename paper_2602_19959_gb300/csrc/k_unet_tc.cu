@@ -174,6 +174,9 @@ struct TcArgs {
     int32_t *sched;                     // [2]: next tile, finished CTAs (zero between launches)
     const int32_t *n_dyn;               // nullable: device-side event count of the call
     int dyn_base;                       // index of the launch's first event in the call
+    uint32_t stall_test_us;             // tests of the bounded waits only (0 otherwise): the
+                                        // MMA thread first waits this long on a barrier that
+                                        // nothing arrives on, then the kernel unwinds
 };
 
 // Calibration: folds max |v| of 16 values (rows with valid = false count as 0) into the
@@ -199,7 +202,7 @@ template <class C> struct Bars {
     static constexpr int W = 0, FULL = 1, EMPTY = 1 + C::STAGES, TFULL = 1 + 2 * C::STAGES,
                          TEMPTY = TFULL + C::NB, T2FULL = TEMPTY + C::NB, A2FULL = T2FULL + C::NB,
                          DRAIN = A2FULL + 2, GREADY = DRAIN + 1, XREADY = GREADY + 2,
-                         TIDF = XREADY + 2, TIDE = TIDF + kRing, N = TIDE + kRing;
+                         TIDF = XREADY + 2, TIDE = TIDF + kRing, NEVER = TIDE + kRing, N = NEVER + 1;
     // after the barriers: TMEM address slot, abort flag, then the ring of tile indices
     static constexpr int RING_OFF = N * 8 + 16;
     static_assert(RING_OFF + 4 * kRing <= 512, "barrier area");
@@ -799,6 +802,7 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
             mbar_init(&bar[B::TIDF + r], 1);                // the producer
             mbar_init(&bar[B::TIDE + r], 1 + 4 * C::EWG);   // the MMA thread and each epilogue warp
         }
+        mbar_init(&bar[B::NEVER], 1);                       // bounded-wait tests: nobody arrives
         *abort = 0;
         fence_mbar_init();
     }
@@ -822,7 +826,10 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
     if (warp == 0) {
         if (lane == 0) ok = producer<C>(r, smem, bar, ring, abort);
     } else if (warp == 1) {
-        if (lane == 0) ok = mma_issuer<C>(r, smem, bar, tmem, ring, abort);
+        // a test of the bounded waits: the wait gives up after stall_test_us, before any MMA
+        if (lane == 0 && a.stall_test_us)
+            ok = mbar_wait(&bar[B::NEVER], 0, abort, 1000ull * a.stall_test_us);
+        if (lane == 0 && ok) ok = mma_issuer<C>(r, smem, bar, tmem, ring, abort);
     } else {
         ok = epilogue<C>(r, smem, bar, tmem, ring, abort, warp, lane);
     }
@@ -1104,6 +1111,36 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, const in
     a.cs2 = nullptr; a.logits = b.logits; a.final_w = n.final_w; a.amax_out = kScaleD1;
     a.w = W(5); a.bias = n.b[5]; a.cs = cs(5);
     return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final", n.ctas_per_sm[5]);
+}
+
+// The enc2 kernel alone with its MMA thread stalled for stall_us (tests of the bounded waits).
+template <int PREC>
+static cudaError_t stall_tc(const TcNet &n, const UnetBuffers &b, int ne, uint32_t stall_us, cudaStream_t s) {
+    using N = Net<PREC>;
+    TcArgs a{};
+    a.n_events = ne;
+    a.status = n.status;
+    a.sched = n.sched;
+    a.inA = static_cast<const unsigned char *>(b.s0);
+    a.out = static_cast<unsigned char *>(b.e2);
+    a.outp = static_cast<unsigned char *>(b.s1);
+    a.w = static_cast<const unsigned char *>(n.w[0]);
+    a.bias = n.b[0];
+    a.cs = is16(PREC) ? nullptr : n.wscale[0];
+    a.out_inv = is16(PREC) ? 1.0f : 1.0f / n.act_scale[kScaleL2];
+    a.stall_test_us = stall_us;
+    return launch_conv<typename N::Enc2>(a, s, nullptr, "enc2", n.ctas_per_sm[0]);
+}
+
+cudaError_t launch_stall_test_tc(const TcNet &net, const UnetBuffers &b, int n, uint32_t stall_us,
+                                 cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    switch (net.precision) {
+    case PVF_BF16: return stall_tc<PVF_BF16>(net, b, n, stall_us, s);
+    case PVF_FP16: return stall_tc<PVF_FP16>(net, b, n, stall_us, s);
+    case PVF_FP8_E4M3: return stall_tc<PVF_FP8_E4M3>(net, b, n, stall_us, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, const int32_t *n_dyn, int dyn_base,

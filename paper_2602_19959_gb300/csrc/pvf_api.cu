@@ -769,6 +769,17 @@ pvf_status pvf_graph_destroy(pvf_graph *g) {
     return PVF_OK;
 }
 
+pvf_status pvf_test_wait_timeout(pvf_handle *h, int32_t n_events, uint32_t limit_us, pvf_stream_t stream_) {
+    if (!h || n_events < 1 || n_events > h->cfg.max_events || n_events > h->plan.chunk || limit_us < 1 ||
+        limit_us > 100000)
+        return PVF_ERR_INVALID_ARG;
+    if (h->cfg.precision == PVF_FP32) return PVF_ERR_UNSUPPORTED;
+    return launch_stall_test_tc(h->tc, h->buf, n_events, limit_us, reinterpret_cast<cudaStream_t>(stream_)) ==
+                   cudaSuccess
+               ? PVF_OK
+               : PVF_ERR_CUDA;
+}
+
 pvf_status pvf_last_device_status(pvf_handle *h, int32_t *out_status, pvf_stream_t stream_) {
     if (!h || !out_status) return PVF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);

@@ -52,5 +52,9 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
 // events [dyn_base, dyn_base + n_events) (see launch_events).
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n_events, const int32_t *n_dyn,
                            int dyn_base, cudaStream_t s, const ProfHook *prof);
+// Tests of the bounded waits: the enc2 kernel with its MMA thread waiting stall_us on a
+// barrier that nothing arrives on (it records PVF_ERR_TIMEOUT and unwinds).
+cudaError_t launch_stall_test_tc(const TcNet &net, const UnetBuffers &b, int n_events, uint32_t stall_us,
+                                 cudaStream_t s);
 
 }  // namespace pvf

@@ -72,16 +72,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 // Waits for the phase of `bar` with the given parity to complete. Returns false after
-// kWaitLimitNs without completion or when *abort is set by another thread; the caller
-// then records PVF_ERR_TIMEOUT and unwinds.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// limit_ns (kWaitLimitNs unless a test asks for less) without completion or when *abort is
+// set by another thread; the caller then records PVF_ERR_TIMEOUT and unwinds.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                          uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255) == 0) {
             if (*abort) return false;
-            if (globaltimer() - t0 > kWaitLimitNs) return false;
+            if (globaltimer() - t0 > limit_ns) return false;
         }
     }
 }

@@ -38,8 +38,8 @@ EXPORTED = ("pvf_pool_bytes_required", "pvf_create", "pvf_infer", "pvf_infer_ex"
             "pvf_last_device_status", "pvf_profile_enable", "pvf_profile_read", "pvf_calibrate",
             "pvf_histogram_static", "pvf_graph_create", "pvf_graph_create_dynamic",
             "pvf_graph_launch", "pvf_graph_destroy",
-            "pvf_serve_bytes_required", "pvf_serve_replay", "pvf_destroy", "pvf_status_str",
-            "pvf_version")
+            "pvf_serve_bytes_required", "pvf_serve_replay", "pvf_test_wait_timeout",
+            "pvf_destroy", "pvf_status_str", "pvf_version")
 
 
 class PvfSchedule(ctypes.Structure):
@@ -129,6 +129,7 @@ def load(path: str = None):
             "pvf_serve_bytes_required": (S, [ctypes.POINTER(PvfServeConfig), I32, ctypes.POINTER(SZ)]),
             "pvf_serve_replay": (S, [P, ctypes.POINTER(PvfServeConfig), ctypes.POINTER(P), P, I32, P, P,
                                      I32, P, SZ, P, P, P, P, P]),
+            "pvf_test_wait_timeout": (S, [P, I32, ctypes.c_uint32, P]),
             "pvf_destroy": (S, [P]),
             "pvf_status_str": (ctypes.c_char_p, [S]),
             "pvf_version": (I32, []),
@@ -423,6 +424,11 @@ class PVFinder:
                                          z.ctypes.data if want_z else None,
                                          ctypes.byref(nb), _stream_ptr(stream)), "pvf_serve_replay")
         return done, cnt, int(nb.value), z
+
+    def test_wait_timeout(self, n_events: int, limit_us: int, stream=None):
+        """pvf_test_wait_timeout: a bounded wait that nothing completes (tests only)."""
+        _check(self.lib.pvf_test_wait_timeout(self.handle, int(n_events), int(limit_us), _stream_ptr(stream)),
+               "pvf_test_wait_timeout")
 
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int32(0)

@@ -164,6 +164,10 @@ def test_serve_slot_sizing_and_validation(lib):
     assert lib.pvf_serve_bytes_required(None, 64, ctypes.byref(out)) == P.PVF_ERR_INVALID_ARG
 
 
+def test_wait_timeout_test_hook_rejects_bad_arguments(lib):
+    assert lib.pvf_test_wait_timeout(None, 1, 1000, None) == P.PVF_ERR_INVALID_ARG
+
+
 def test_config_struct_layout():
     """The ctypes mirrors of the C structs keep the header's sizes and offsets."""
     assert ctypes.sizeof(P.PvfConfig) == 48 and P.PvfConfig.schedule.offset == 40
