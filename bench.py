@@ -700,7 +700,7 @@ def main():
     ap.add_argument("--unet-width", type=int, default=16, choices=[16, 32],
                     help="UNet base width (32: the wide variant, float32 form only)")
     ap.add_argument("--per-interval", action="store_true",
-                    help="each interval runs the UNet as its own 104-bin sequence (fp32 form only)")
+                    help="each interval runs the UNet as its own 104-bin sequence")
     ap.add_argument("--boundary-mm", type=float, default=0.0,
                     help="boundary tracks fill a second slice within this width (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -734,8 +734,8 @@ def main():
     rank, world, local = dist_env()
     if args.unet_width != 16 and args.precision != "fp32":
         ap.error("--unet-width 32 exists in the fp32 form only")
-    if args.per_interval and (args.precision != "fp32" or args.unet_width != 16):
-        ap.error("--per-interval exists in the fp32 form at width 16 only")
+    if args.per_interval and args.unet_width != 16:
+        ap.error("--per-interval exists at width 16 only")
     weights = synth.he_weights(0, c0=args.unet_width)
     if args.impl == "reference":
         batch = synth.generate_standard(args.events, rank_workload_seed(rank))

@@ -188,11 +188,17 @@ __device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_
 // Thread tid owns channels [8 h, 8 h + 8), h = tid & 1, of every position pair it takes,
 // so its 40 weights and 8 biases stay in registers and the loop reads only the histogram
 // from shared memory; the two threads of a pair write the two halves of each row.
-template <class T, int NT, bool AMAX>
+// IV: the per-interval layout of the tensor-core forms: e1 and p1 hold the event's kSlices
+// sequences end to end, each the conv of the interval's kIvLen-bin window (its bins with
+// kIvPad zero bins on each side) with its own two zero rows on each side.
+template <class T, int NT, bool AMAX, bool IV = false>
 __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, const float *shist,
                                             const float *senc) {
     static_assert(NT % 2 == 0, "thread pairs");
-    const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
+    constexpr int S1 = kIvLen + 2 * kPad, S2 = kIvLen / 2 + 2 * kPad;   // rows per sequence
+    const int64_t rows1 = IV ? (int64_t)kSlices * S1 : padded_rows(kBins);
+    const int64_t rows2 = IV ? (int64_t)kSlices * S2 : padded_rows(kBins / 2);
+    constexpr int NQ = IV ? kSlices * (kIvLen / 2) : kBins / 2;         // position pairs
     const float inv = a.e1_inv_scale;
     const int h = tid & 1;
     float w[5][8], bias[8];
@@ -203,12 +209,20 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
         bias[j] = senc[5 * kC0 + 8 * h + j];
     }
     float vmax = 0.0f;
-    for (int q = tid >> 1; q < kBins / 2; q += NT / 2) {
+    for (int qi = tid >> 1; qi < NQ; qi += NT / 2) {
+        // the pair's sequence (IV) and first position; e1 rows r1, r1 + 1, p1 row r2
+        const int sq = IV ? qi / (kIvLen / 2) : 0, q = IV ? qi % (kIvLen / 2) : qi;
+        const int64_t r1 = (int64_t)sq * S1 * IV + 2 * q + kPad, r2 = (int64_t)sq * S2 * IV + q + kPad;
         float hv[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const int p = 2 * q + k - 2;
-            hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
+            if constexpr (IV) {
+                const int b = 2 * q + k - 2 - kIvPad;    // bin of the interval at window position
+                hv[k] = (b >= 0 && b < kSliceBins) ? shist[sq * kSliceBins + b] : 0.0f;
+            } else {
+                const int p = 2 * q + k - 2;
+                hv[k] = (p >= 0 && p < kBins) ? shist[p] : 0.0f;
+            }
         }
         float v0[8], v1[8], vp[8];
 #pragma unroll
@@ -224,16 +238,22 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
             vp[j] = fmaxf(v0[j], v1[j]);
             if constexpr (AMAX) vmax = fmaxf(vmax, fmaxf(fabsf(v0[j]), fabsf(v1[j])));
         }
-        store_half8<T>(a.e1, e, rows1, 2 * q + kPad, h, v0, inv);
-        store_half8<T>(a.e1, e, rows1, 2 * q + 1 + kPad, h, v1, inv);
-        store_half8<T>(a.p1, e, rows2, q + kPad, h, vp, inv);
+        store_half8<T>(a.e1, e, rows1, r1, h, v0, inv);
+        store_half8<T>(a.e1, e, rows1, r1 + 1, h, v1, inv);
+        store_half8<T>(a.p1, e, rows2, r2, h, vp, inv);
     }
     if constexpr (AMAX) {   // calibration: integer max on the float bits (order-independent)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
     }
-    if (tid < 4) {
+    if constexpr (IV) {     // each sequence's rows 0, 1 and L + 2, L + 3
+        for (int idx = tid; idx < kSlices * 4; idx += NT) {
+            const int sq = idx >> 2, k = idx & 3;
+            zero_row16<T>(a.e1, e, rows1, (int64_t)sq * S1 + (k < 2 ? k : S1 - 4 + k));
+            zero_row16<T>(a.p1, e, rows2, (int64_t)sq * S2 + (k < 2 ? k : S2 - 4 + k));
+        }
+    } else if (tid < 4) {
         const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3
         zero_row16<T>(a.e1, e, rows1, r);
         const int rp = tid < 2 ? tid : kBins / 2 + tid;
@@ -377,13 +397,13 @@ __device__ __forceinline__ void enc1_pool_windows_f32(const FrontArgs &a, int e,
 
 // REGW: weights in registers (tensor-core front, width 16) or read from shared memory
 // (float32 front, width C0).
-template <class T, int NT, bool REGW = true, int C0 = kC0>
+template <class T, int NT, bool REGW = true, int C0 = kC0, bool IV = false>
 __device__ __forceinline__ void enc1_pool(const FrontArgs &a, int e, int tid, const float *shist,
                                           const float *senc) {
     if constexpr (REGW) {
         static_assert(C0 == kC0, "register weights for width 16");
-        if (a.amax) enc1_pool_t<T, NT, true>(a, e, tid, shist, senc);
-        else enc1_pool_t<T, NT, false>(a, e, tid, shist, senc);
+        if (a.amax) enc1_pool_t<T, NT, true, IV>(a, e, tid, shist, senc);
+        else enc1_pool_t<T, NT, false, IV>(a, e, tid, shist, senc);
     } else {
         if (a.amax) enc1_pool_shared_t<T, NT, true, C0>(a, e, tid, shist, senc);
         else enc1_pool_shared_t<T, NT, false, C0>(a, e, tid, shist, senc);

@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
             const float4 *src = reinterpret_cast<const float4 *>(shist);
             for (int i = tid; i < kBins / 4; i += kT) dst[i] = src[i];
         }
-        enc1_pool<T, kT>(a, e, tid, shist, senc);
+        if (a.iv) enc1_pool<T, kT, true, kC0, true>(a, e, tid, shist, senc);
+        else enc1_pool<T, kT>(a, e, tid, shist, senc);
         __syncthreads();                   // shist and the sort arrays are reused next event
     }
     if (failed && tid == 0) {
@@ -335,7 +336,7 @@ cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    if (a.c0 != kC0 || a.iv) return cudaErrorInvalidValue;   // tensor-core forms: width 16, whole events
+    if (a.c0 != kC0) return cudaErrorInvalidValue;   // tensor-core forms: width 16
     switch (precision) {
     case PVF_BF16: return launch_front_tc_t<PVF_BF16>(a, s);
     case PVF_FP16: return launch_front_tc_t<PVF_FP16>(a, s);

@@ -71,7 +71,8 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_, int EWG_ = 1,
-          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false, bool A2T_ = false>
+          int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false, bool A2T_ = false,
+          int SEQ_ = 0>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = is16(PREC) ? 2 : 1;            // bytes per element
@@ -95,6 +96,15 @@ struct Cfg {
     static constexpr int ROWS = kTileM + TAPS - 1;           // halo'd tile rows
     static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
     static constexpr bool PAIRED = PAIRED_;                 // taps stacked in pairs along N
+    // per-interval layout: the event is kSlices sequences laid end to end, SEQ storage rows
+    // each (its LSEQ positions and two zero rows on each side), so the event's L = kSlices
+    // SEQ - 4 positions include the zero rows between sequences; 0: one sequence of L
+    static constexpr int SEQ = SEQ_;
+    static constexpr int LSEQ = SEQ ? SEQ - 2 * kPad : L_;
+    static constexpr int SEQP = SEQ ? LSEQ / 2 + 2 * kPad : 0;   // after the 2:1 pool
+    static constexpr int SEQU = SEQ ? 2 * LSEQ + 2 * kPad : 0;   // after the ConvT
+    static constexpr int64_t ROWS_P = SEQ ? (int64_t)kSlices * SEQP : L_ / 2 + 2 * kPad;  // pooled rows per event
+    static constexpr int64_t ROWS_O = SEQ ? (int64_t)kSlices * SEQU : 2 * L_ + 2 * kPad;  // ConvT rows per event
     static constexpr bool DYN = DYN_;                       // tiles from the global counter
     // output rows per tile: row 127 of a paired tile lacks O[128]; the fused final conv
     // also needs two rows on each side
@@ -151,6 +161,10 @@ struct Cfg {
                               (EWG <= 2 || EPI == EPI_UP)),
                   "tap pairing");
     static_assert(SMEM <= 227 * 1024, "shared memory");
+    // the pool pairs lanes m, m + 1 as positions j, j + 1 of one sequence: even SEQ and LSEQ
+    static_assert(!SEQ || (L == kSlices * SEQ - 2 * kPad &&
+                           (EPI != EPI_POOL || (SEQ % 2 == 0 && LSEQ % 2 == 0))),
+                  "per-interval geometry");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
     static_assert(EWG == 1 || (EWG == 2 && EPI != EPI_FINAL && EPI_COLS % 16 == 0) ||
                   (EWG == 4 && EPI == EPI_UP && (COUT / 2) % 16 == 0 && (N2 / 2) % 16 == 0),
@@ -214,6 +228,19 @@ __device__ __forceinline__ void tile_pos(int t, int &e, int &p0) {
     e = t / C::TPE;
     const int k = t % C::TPE;
     p0 = C::EPI == EPI_FINAL ? k * C::STRIDE - kPad : k * C::STRIDE;
+}
+
+// Per-interval layout: position p of the event lies in sequence s at position j of it;
+// j outside [0, LSEQ) is one of the zero rows between sequences. Whole events: s = 0, j = p.
+template <class C>
+__device__ __forceinline__ void seq_pos(int p, int &s, int &j) {
+    if constexpr (C::SEQ != 0) {
+        s = (p + kPad) / C::SEQ;
+        j = (p + kPad) % C::SEQ - kPad;
+    } else {
+        s = 0;
+        j = p;
+    }
 }
 
 // Quantises 16 values to the form's element type and stores them as 16 / PW plane rows.
@@ -496,12 +523,18 @@ __device__ __forceinline__ bool paired_publish(uint32_t dcol, int c_beg, float *
 // Epilogue pieces, one TMEM lane (tile row m, position p) per thread.
 // Conv columns [c_beg, c_beg + NC) of accumulator dcol: bias, LeakyReLU, then either the
 // fused ConvT's shared-memory operand (A2) or the stored output (+ the 2:1 max-pool).
+// inseq: the row is a position of a sequence (false: a zero row between sequences of the
+// per-interval layout, stored as zeros).
 template <class C, int NC>
 __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
                                          const float *scs, uint32_t dcol, int c_beg, int ab, int e,
                                          int p, int m, bool valid, const float *sx = nullptr,
-                                         uint32_t a2t = 0) {
-    constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad;
+                                         uint32_t a2t = 0, bool inseq = true) {
+    constexpr int64_t ROWS_P = C::ROWS_P;
+    int sq, jq;
+    seq_pos<C>(p, sq, jq);
+    // pooled row: position j / 2 of sequence s (whole events: p / 2)
+    const int64_t prow = C::SEQ ? (int64_t)sq * C::SEQP + jq / 2 + kPad : p / 2 + kPad;
     constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
 #pragma unroll 1
     for (int cc = 0; cc < NC; cc += LDW) {
@@ -526,6 +559,12 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
                 lds16(scs + c0, sc);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = leaky(fmaf(vv[16 * h + j], sc[j], bj[j]));
+            }
+            if constexpr (C::SEQ != 0) {
+                if (!inseq) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+                }
             }
             if constexpr (C::EPI == EPI_UP && C::A2T) {
                 // this row's 16 channels into its TMEM lane: 16-bit pairs (8 columns) or
@@ -555,8 +594,8 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
                     float w[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) w[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
-                    if (valid && (m & 1) == 0)
-                        put16<C::PREC>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, p / 2 + kPad),
+                    if (valid && inseq && (m & 1) == 0)
+                        put16<C::PREC>(a.outp + planar_off(e, c0 / C::PW, C::POUT, ROWS_P, prow),
                                   (size_t)ROWS_P * 16, w, a.out_inv);
                 }
             }
@@ -570,7 +609,12 @@ template <class C, int NC>
 __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, const float *scs2,
                                        uint32_t dcol, int n_beg, int e, int p, bool valid, bool pads) {
     constexpr int LO = 2 * C::L;
-    constexpr int64_t ROWS_O = LO + 2 * kPad;
+    constexpr int64_t ROWS_O = C::ROWS_O;
+    int sq, jq;
+    seq_pos<C>(p, sq, jq);
+    const bool inseq = !C::SEQ || (jq >= 0 && jq < C::LSEQ);
+    // output rows 2 j + r of sequence s (whole events: 2 p + r)
+    const int64_t orow0 = C::SEQ ? (int64_t)sq * C::SEQU + 2 * jq + kPad : 2 * p + kPad;
     constexpr int PUP = C::CUP / C::PW;
     constexpr int LDW = NC % 32 == 0 ? 32 : 16;
 #pragma unroll 1
@@ -596,19 +640,30 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = leaky(fmaf(vv[16 * h + j], sc[j], bj[j]));
             }
-            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
-            if (valid)
-                put16<C::PREC>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, 2 * p + r + kPad),
+            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid && inseq);
+            if (valid && inseq)
+                put16<C::PREC>(a.out + planar_off(e, co0 / C::PW, PUP, ROWS_O, orow0 + r),
                           (size_t)ROWS_O * 16, v, a.out_inv);
         }
     }
-    if (pads && p == 0) {
-        zero_planes(a.out, e, PUP, ROWS_O, 0);
-        zero_planes(a.out, e, PUP, ROWS_O, 1);
-    }
-    if (pads && p == C::L - 1) {
-        zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
-        zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
+    if constexpr (C::SEQ != 0) {     // each output sequence's zero rows
+        if (pads && valid && jq == 0) {
+            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU);
+            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU + 1);
+        }
+        if (pads && valid && jq == C::LSEQ - 1) {
+            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 2);
+            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 1);
+        }
+    } else {
+        if (pads && p == 0) {
+            zero_planes(a.out, e, PUP, ROWS_O, 0);
+            zero_planes(a.out, e, PUP, ROWS_O, 1);
+        }
+        if (pads && p == C::L - 1) {
+            zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
+            zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
+        }
     }
 }
 
@@ -627,7 +682,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
     const int wg = (warp - 2) >> 2;                 // epilogue warpgroup
     const uint32_t lane_field = (uint32_t)(q * 32) << 16;
     const uint32_t a2_lane = tmem + lane_field + C::A2_COL0;    // A2T: this warp's lanes of the A2 buffers
-    constexpr int64_t ROWS_P = C::L / 2 + 2 * kPad; // pooled tensor
+    constexpr int64_t ROWS_P = C::ROWS_P;           // pooled tensor
     constexpr bool ROLES = C::EPI == EPI_UP && C::EWG >= 2;
     const int ntiles = a.n_events * C::TPE;
     for (int i = 0;; ++i) {
@@ -649,6 +704,9 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         const int p = p0 + m;
         // rows past the stride belong to the next tile (and row 127 of a paired tile is incomplete)
         const bool valid = p >= 0 && p < C::L && m < C::ROWS_OK;
+        int sq, jq;                                 // per-interval layout: sequence, position
+        seq_pos<C>(p, sq, jq);
+        const bool inseq = !C::SEQ || (jq >= 0 && jq < C::LSEQ);
         const uint32_t dcol = tmem + lane_field + b * C::COLS_BUF;
         float *sx = reinterpret_cast<float *>(smem + C::OFF_X) + ab * 4 * C::COUT;
         if constexpr (ROLES) {
@@ -663,7 +721,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                         return false;
                 }
                 epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
-                                           valid, sx, a2_lane + ab * C::A2_COLS);
+                                           valid, sx, a2_lane + ab * C::A2_COLS, inseq);
                 if constexpr (C::A2T) tmem_st_wait();   // A2 in TMEM complete before the MMA reads it
                 else fence_proxy_async_smem();          // A2 writes -> visible to the tensor core
                 tc_fence_before();
@@ -700,10 +758,10 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                     lds16(scs, sc);
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    v[j] = valid ? leaky(fmaf(v[j], sc[j], bj[j])) : 0.0f;   // zero padding outside
+                for (int j = 0; j < 16; ++j)   // zero padding outside the event or its sequence
+                    v[j] = valid && inseq ? leaky(fmaf(v[j], sc[j], bj[j])) : 0.0f;
             }
-            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
+            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid && inseq);
 #pragma unroll
             for (int tp = 0; tp < 5; ++tp) {
                 float wf[16];
@@ -719,12 +777,16 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             // neighbours' partial sums: a bounded mbarrier among the 128 epilogue threads
             mbar_arrive(&gready[ab]);
             if (!mbar_wait(&gready[ab], ph_a, abort)) return false;
-            if (m >= kPad && m < kPad + C::STRIDE && valid) {
+            // per-interval layout: the logits of an interval's bins are its sequence's
+            // central positions [kIvPad, kIvPad + kSliceBins)
+            const bool out = !C::SEQ || (jq >= kIvPad && jq < kIvPad + kSliceBins);
+            if (m >= kPad && m < kPad + C::STRIDE && valid && out) {
                 // f(p) = b + sum_t g_t(p + t - 2), in tap order
                 float f = sfin[5 * kC0];
 #pragma unroll
                 for (int tp = 0; tp < 5; ++tp) f += sg[tp * kTileM + m + tp - 2];
-                a.logits[(size_t)e * C::L + p] = f;
+                if constexpr (C::SEQ != 0) a.logits[(size_t)e * kBins + sq * kSliceBins + jq - kIvPad] = f;
+                else a.logits[(size_t)e * C::L + p] = f;
             }
             continue;
         }
@@ -732,7 +794,8 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             if constexpr (C::PAIRED) {
                 if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
             }
-            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx, a2_lane + ab * C::A2_COLS);
+            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx, a2_lane + ab * C::A2_COLS,
+                                 inseq);
             if constexpr (C::A2T) tmem_st_wait();
             else fence_proxy_async_smem();
             tc_fence_before();
@@ -742,13 +805,21 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
         } else {                            // this warpgroup's conv columns
             static_assert(!C::PAIRED || C::EPI == EPI_UP || C::EPI == EPI_FINAL, "paired stores");
-            epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid);
+            epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid, nullptr, 0,
+                                     inseq);
             if (wg == 0 && (p == 0 || p == C::L - 1)) {
                 const int r0 = p == 0 ? 0 : C::L + kPad;
                 zero_planes(a.out, e, C::POUT, C::ROWS_E, r0);
                 zero_planes(a.out, e, C::POUT, C::ROWS_E, r0 + 1);
-                if constexpr (C::EPI == EPI_POOL) {
+                if constexpr (C::EPI == EPI_POOL && C::SEQ == 0) {
                     const int rp = p == 0 ? 0 : C::L / 2 + kPad;
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp);
+                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp + 1);
+                }
+            }
+            if constexpr (C::EPI == EPI_POOL && C::SEQ != 0) {   // each pooled sequence's zero rows
+                if (wg == 0 && valid && (jq == 0 || jq == C::LSEQ - 2)) {
+                    const int64_t rp = (int64_t)sq * C::SEQP + (jq == 0 ? 0 : C::SEQP - 2);
                     zero_planes(a.outp, e, C::POUT, ROWS_P, rp);
                     zero_planes(a.outp, e, C::POUT, ROWS_P, rp + 1);
                 }
@@ -905,6 +976,24 @@ template <int PREC> struct Net {
     using Dec2Up1 = Cfg<PREC, 32, 32, 32, 2000, EPI_UP, 16, 3, 2, 128, 3, conv_paired(4, PREC), false,
                         true>;                                                         // 2
     using Dec1Final = Cfg<PREC, 16, 16, 16, 4000, EPI_FINAL, 0, 3, 1, 64, 4, conv_paired(5, PREC)>; // 5
+};
+
+// The per-interval layout (§3's batch of 40 intervals, each its own sequence of kIvLen =
+// 104 positions): the same kernels over each event's 40 sequences laid end to end, with
+// levels of 104, 52, 26 and 13 positions per sequence (108, 56, 30 and 17 storage rows).
+template <int PREC> struct NetIv {
+    static constexpr int S0 = kIvLen + 2 * kPad, S1 = kIvLen / 2 + 2 * kPad, S2 = kIvLen / 4 + 2 * kPad,
+                         S3 = kIvLen / 8 + 2 * kPad;
+    static constexpr int L0 = kSlices * S0 - 2 * kPad, L1 = kSlices * S1 - 2 * kPad, L2 = kSlices * S2 - 2 * kPad,
+                         L3 = kSlices * S3 - 2 * kPad;
+    using Enc2 = Cfg<PREC, 16, 0, 32, L1, EPI_POOL, 0, 4, 1, 56, 2, false, true, false, S1>;
+    using Enc3 = Cfg<PREC, 32, 0, 64, L2, EPI_POOL, 0, 4, 1, 80, 2, false, true, false, S2>;
+    using Enc4Up3 = Cfg<PREC, 64, 0, 128, L3, EPI_UP, 64, is16(PREC) ? 2 : 4, is16(PREC) ? 2 : 4, 96, 3, false,
+                        false, true, S3>;
+    using Dec3Up2 = Cfg<PREC, 64, 64, 64, L2, EPI_UP, 32, 3, 2, 128, 3, conv_paired(3, PREC), false, true, S2>;
+    using Dec2Up1 = Cfg<PREC, 32, 32, 32, L1, EPI_UP, 16, 3, 2, 128, 3, conv_paired(4, PREC), false, true, S1>;
+    using Dec1Final = Cfg<PREC, 16, 16, 16, L0, EPI_FINAL, 0, 3, 1, 64, 4, conv_paired(5, PREC), false, false,
+                          S0>;
 };
 
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
@@ -1064,10 +1153,9 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
     return true;
 }
 
-template <int PREC>
+template <int PREC, class N>
 static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, const int32_t *n_dyn, int dyn_base,
                           cudaStream_t s, const ProfHook *prof) {
-    using N = Net<PREC>;
     const float *sc = n.act_scale;
     auto inv = [&](int i) { return is16(PREC) ? 1.0f : 1.0f / sc[i]; };
     auto cs = [&](int li) { return is16(PREC) ? nullptr : n.wscale[li]; };
@@ -1146,10 +1234,18 @@ cudaError_t launch_stall_test_tc(const TcNet &net, const UnetBuffers &b, int n, 
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, const int32_t *n_dyn, int dyn_base,
                            cudaStream_t s, const ProfHook *prof) {
     if (n <= 0) return cudaSuccess;
+    if (net.iv) {
+        switch (net.precision) {
+        case PVF_BF16: return run_tc<PVF_BF16, NetIv<PVF_BF16>>(net, b, n, n_dyn, dyn_base, s, prof);
+        case PVF_FP16: return run_tc<PVF_FP16, NetIv<PVF_FP16>>(net, b, n, n_dyn, dyn_base, s, prof);
+        case PVF_FP8_E4M3: return run_tc<PVF_FP8_E4M3, NetIv<PVF_FP8_E4M3>>(net, b, n, n_dyn, dyn_base, s, prof);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (net.precision) {
-    case PVF_BF16: return run_tc<PVF_BF16>(net, b, n, n_dyn, dyn_base, s, prof);
-    case PVF_FP16: return run_tc<PVF_FP16>(net, b, n, n_dyn, dyn_base, s, prof);
-    case PVF_FP8_E4M3: return run_tc<PVF_FP8_E4M3>(net, b, n, n_dyn, dyn_base, s, prof);
+    case PVF_BF16: return run_tc<PVF_BF16, Net<PVF_BF16>>(net, b, n, n_dyn, dyn_base, s, prof);
+    case PVF_FP16: return run_tc<PVF_FP16, Net<PVF_FP16>>(net, b, n, n_dyn, dyn_base, s, prof);
+    case PVF_FP8_E4M3: return run_tc<PVF_FP8_E4M3, Net<PVF_FP8_E4M3>>(net, b, n, n_dyn, dyn_base, s, prof);
     default: return cudaErrorInvalidValue;
     }
 }

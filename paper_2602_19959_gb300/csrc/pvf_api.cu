@@ -202,7 +202,7 @@ pvf_status check_config(const pvf_config *c) {
     if (c->unet_width != 0 && c->unet_width != kC0 && c->unet_width != kC0Max) return PVF_ERR_INVALID_ARG;
     if (c->unet_width == kC0Max && c->precision != PVF_FP32) return PVF_ERR_UNSUPPORTED;
     if (c->per_interval != 0 && c->per_interval != 1) return PVF_ERR_INVALID_ARG;
-    if (c->per_interval && (c->precision != PVF_FP32 || c->unet_width == kC0Max)) return PVF_ERR_UNSUPPORTED;
+    if (c->per_interval && c->unet_width == kC0Max) return PVF_ERR_UNSUPPORTED;
     if (c->schedule) {
         const pvf_schedule &q = *c->schedule;
         if (q.front_ctas_per_sm < 0 || q.tail_ctas_per_sm < 0) return PVF_ERR_INVALID_ARG;
@@ -366,6 +366,7 @@ pvf_status pvf_create(const void *blob, size_t blob_bytes, void *pool, size_t po
     h->cfg.schedule = nullptr;
     h->sched = cfg->schedule ? *cfg->schedule : pvf_schedule{};
     for (int k = 0; k < 6; ++k) h->tc.ctas_per_sm[k] = h->sched.conv_ctas_per_sm[k];
+    h->tc.iv = cfg->per_interval;
     h->plan = plan;
     h->pool = static_cast<unsigned char *>(pool);
     h->front_smem = front_smem_bytes(cfg->max_tracks_per_event, cfg->boundary_mm);

@@ -40,6 +40,7 @@ struct TcNet {
     int32_t *status;         // device status word
     int32_t *sched;          // 6 x 2 tile-scheduler counters (zero between launches)
     int32_t ctas_per_sm[6];  // launch schedule per conv kernel (0 = as many as fit)
+    int32_t iv;              // per-interval layout (kSlices sequences per event)
 };
 
 size_t tc_weight_bytes(int precision);

@@ -397,13 +397,6 @@ def test_per_interval_with_boundary_tracks_matches_oracle(lib, weights, ev16):
     assert a["max_dz"] <= 0.1 and a["exempt"] == 1.0 and a["strict"] >= 0.99
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
-def test_per_interval_tensor_core_forms_unsupported(lib, weights, precision):
-    from paper_2602_19959_gb300.pvf import PvfError, PVF_ERR_UNSUPPORTED
-    with pytest.raises(PvfError) as ei:
-        lib(weights, precision=precision, max_events=4, per_interval=True)
-    assert ei.value.code == PVF_ERR_UNSUPPORTED
-
 
 def test_end_to_end_closed_form(lib):
     """All four steps against hand-derived values (the oracle pin of the same name): zero
