@@ -89,6 +89,18 @@ def kernel_table(form, c0=16, iv=False):
         m, r, w = scaled(convT_io(L1, c2, c1)); t["up1"] = entry(m, (r + w) * es)
         m, r, w = scaled(conv_io(L0, 2 * c1, c1)); t["dec1"] = entry(m, (r + w) * es)
         t["tail"] = (0, 4000 * c1 * 5, q * c1 * (L0 + 4) * es + 16000)
+    elif c0 == 32 and not iv:
+        # the wide network: enc4 and dec3 split over CTAs store e4 and d3; up3 and up2 run
+        # as ConvT kernels of their own
+        m, r, w = conv_io(L3, c3, c4); t["enc4"] = entry(m, (r + w) * es)
+        m, r, w = convT_io(L3, c4, c3); t["up3"] = entry(m, (r + w) * es)
+        m, r, w = conv_io(L2, 2 * c3, c3); t["dec3"] = entry(m, (r + w) * es)
+        m, r, w = convT_io(L2, c3, c2); t["up2"] = entry(m, (r + w) * es)
+        m1, r1, _ = conv_io(L1, 2 * c2, c2); m2, _, w2 = convT_io(L1, c2, c1)
+        t["dec2_up1"] = entry(m1 + m2, (r1 + w2) * es)
+        m1, r1, _ = conv_io(L0, 2 * c1, c1)
+        t["dec1_final"] = entry(m1, r1 * es + 16000, alu_mac=L0 * c1 * 5)
+        t["tail"] = (0, 0, 16000)
     else:
         m1, r1, _ = conv_io(L3, c3, c4); m2, _, w2 = convT_io(L3, c4, c3)
         t["enc4_up3"] = entry(m1 + m2, (r1 + w2) * es)
@@ -698,7 +710,7 @@ def main():
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--max-pv", type=int, default=672)
     ap.add_argument("--unet-width", type=int, default=16, choices=[16, 32],
-                    help="UNet base width (32: the wide variant, float32 form only)")
+                    help="UNet base width (32: the wide variant)")
     ap.add_argument("--per-interval", action="store_true",
                     help="each interval runs the UNet as its own 104-bin sequence")
     ap.add_argument("--boundary-mm", type=float, default=0.0,
@@ -732,8 +744,6 @@ def main():
 
     import synth
     rank, world, local = dist_env()
-    if args.unet_width != 16 and args.precision != "fp32":
-        ap.error("--unet-width 32 exists in the fp32 form only")
     if args.per_interval and args.unet_width != 16:
         ap.error("--per-interval exists at width 16 only")
     weights = synth.he_weights(0, c0=args.unet_width)

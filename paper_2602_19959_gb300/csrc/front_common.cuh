@@ -38,6 +38,22 @@ __device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_
     }
 }
 
+// Channels [16 g, 16 g + 16) of storage row `row` of event e in a plane-major tensor of C0
+// channels (16-bit: planes 2 g and 2 g + 1 of C0 / 8; e4m3: plane g of C0 / 16).
+template <class T, int C0>
+__device__ __forceinline__ void store_seg16_pm(void *base, int64_t e, int64_t rows_e, int64_t row, int g,
+                                               const float v[16], float inv_scale) {
+    unsigned char *cb = reinterpret_cast<unsigned char *>(base);
+    if constexpr (sizeof(T) == 2) {
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 2 * g, C0 / 8, rows_e, row)) = pack8<T>(v);
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, 2 * g + 1, C0 / 8, rows_e, row)) = pack8<T>(v + 8);
+    } else {
+        uint4 pk;
+        pack_e4m3<16>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
+        *reinterpret_cast<uint4 *>(cb + planar_off(e, g, C0 / 16, rows_e, row)) = pk;
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void zero_row16(void *base, int64_t e, int64_t rows_e, int64_t row) {
     float z[kC0];
@@ -278,7 +294,7 @@ __device__ __forceinline__ void store_seg16_f32(void *base, int64_t e, int64_t r
 template <class T, int NT, bool AMAX, int C0>
 __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, int tid, const float *shist,
                                                    const float *senc) {
-    static_assert(C0 % 16 == 0 && (C0 == kC0 || sizeof(T) == 4), "wide networks are float32 only");
+    static_assert(C0 % 16 == 0, "16-channel segments");
     const int64_t rows1 = padded_rows(kBins), rows2 = padded_rows(kBins / 2);
     const float inv = a.e1_inv_scale;
     float vmax = 0.0f;
@@ -310,10 +326,14 @@ __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, in
                 store_row16<T>(a.e1, e, rows1, 2 * q + kPad, v0, inv);
                 store_row16<T>(a.e1, e, rows1, 2 * q + 1 + kPad, v1, inv);
                 store_row16<T>(a.p1, e, rows2, q + kPad, vp, inv);
-            } else {
+            } else if constexpr (sizeof(T) == 4) {
                 store_seg16_f32<C0>(a.e1, e, rows1, 2 * q + kPad, g, v0);
                 store_seg16_f32<C0>(a.e1, e, rows1, 2 * q + 1 + kPad, g, v1);
                 store_seg16_f32<C0>(a.p1, e, rows2, q + kPad, g, vp);
+            } else {   // the wide network in the tensor-core forms: plane-major segments
+                store_seg16_pm<T, C0>(a.e1, e, rows1, 2 * q + kPad, g, v0, inv);
+                store_seg16_pm<T, C0>(a.e1, e, rows1, 2 * q + 1 + kPad, g, v1, inv);
+                store_seg16_pm<T, C0>(a.p1, e, rows2, q + kPad, g, vp, inv);
             }
         }
     }
@@ -333,8 +353,13 @@ __device__ __forceinline__ void enc1_pool_shared_t(const FrontArgs &a, int e, in
 #pragma unroll
             for (int i = 0; i < 16; ++i) z[i] = 0.0f;
             for (int g = 0; g < C0 / 16; ++g) {
-                store_seg16_f32<C0>(a.e1, e, rows1, r, g, z);
-                store_seg16_f32<C0>(a.p1, e, rows2, rp, g, z);
+                if constexpr (sizeof(T) == 4) {
+                    store_seg16_f32<C0>(a.e1, e, rows1, r, g, z);
+                    store_seg16_f32<C0>(a.p1, e, rows2, rp, g, z);
+                } else {
+                    store_seg16_pm<T, C0>(a.e1, e, rows1, r, g, z, 1.0f);
+                    store_seg16_pm<T, C0>(a.p1, e, rows2, rp, g, z, 1.0f);
+                }
             }
         }
     }

@@ -38,7 +38,7 @@ struct TcSmem {
     static constexpr size_t img = 0;                                   // kFcImgBytes
     static constexpr size_t bias = img + kFcImgBytes;                  // kFcBTotal floats
     static constexpr size_t enc1 = bias + sizeof(float) * kFcBTotal;   // kEnc1Floats
-    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1Floats + 127) / 128 * 128;  // 2 planes x 256 rows
+    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1FloatsMax + 127) / 128 * 128;  // 2 planes x 256 rows
     static constexpr size_t h = x + 2 * kPlane;                        // 4 planes x 256 rows
     static constexpr size_t hist = h + 4 * kPlane;
     static constexpr size_t cnt = hist + sizeof(float) * kBins;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
     const int o_bin = lane < kFcOutPerWarp ? (warp & 3) * kFcOutPerWarp + lane : -1;
 
     // once per CTA: enc1 weights, FC operand images and biases, barrier, TMEM
-    for (int i = tid; i < kEnc1Floats; i += kT) senc[i] = a.enc1[i];
+    for (int i = tid; i < 6 * a.c0; i += kT) senc[i] = a.enc1[i];   // W[t][co] then b, c0 channels
     if (!a.hist_in) {
         for (int i = tid; i < kFcImgBytes / 16; i += kT)
             reinterpret_cast<uint4 *>(smem + TcSmem::img)[i] = reinterpret_cast<const uint4 *>(a.fc_img)[i];
@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
             for (int i = tid; i < kBins / 4; i += kT) dst[i] = src[i];
         }
         if (a.iv) enc1_pool<T, kT, true, kC0, true>(a, e, tid, shist, senc);
+        else if (a.c0 == kC0Max) enc1_pool<T, kT, false, kC0Max>(a, e, tid, shist, senc);   // the wide network
         else enc1_pool<T, kT>(a, e, tid, shist, senc);
         __syncthreads();                   // shist and the sort arrays are reused next event
     }
@@ -336,7 +337,7 @@ cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {
     if (a.n_events <= 0) return cudaSuccess;
-    if (a.c0 != kC0) return cudaErrorInvalidValue;   // tensor-core forms: width 16
+    if ((a.c0 != kC0 && a.c0 != kC0Max) || (a.iv && a.c0 != kC0)) return cudaErrorInvalidValue;
     switch (precision) {
     case PVF_BF16: return launch_front_tc_t<PVF_BF16>(a, s);
     case PVF_FP16: return launch_front_tc_t<PVF_FP16>(a, s);

@@ -61,7 +61,9 @@ using namespace tc;
 
 constexpr int kTileM = 128;
 
-enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2, EPI_FINAL = 3 };
+// EPI_CONVT: the kernel's GEMM is itself a ConvT k2 s2 (one "tap", N = r * CUP + co), for
+// the wide network's layers whose conv is split over CTAs and so cannot fuse its ConvT.
+enum { EPI_STORE = 0, EPI_POOL = 1, EPI_UP = 2, EPI_FINAL = 3, EPI_CONVT = 4 };
 
 __host__ __device__ constexpr int pow2ceil(int x) {
     int p = 32;
@@ -72,7 +74,7 @@ __host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / 
 
 template <int PREC_, int CA_, int CB_, int COUT_, int L_, int EPI_, int CUP_, int STAGES_, int EWG_ = 1,
           int MAXREG_ = 128, int NB_ = 2, bool PAIRED_ = false, bool DYN_ = false, bool A2T_ = false,
-          int SEQ_ = 0>
+          int SEQ_ = 0, int NSPLIT_ = 1>
 struct Cfg {
     static constexpr int PREC = PREC_;
     static constexpr int ES = is16(PREC) ? 2 : 1;            // bytes per element
@@ -92,8 +94,16 @@ struct Cfg {
     // A single input plane is half an MMA's K (32 bytes): pair taps (2j, 2j+1) in one MMA
     // by pointing the K-adjacent core matrix at the next row; a 6th zero tap pads.
     static constexpr bool PAIR = PIN == 1;
-    static constexpr int TAPS = PAIR ? 6 : 5;
+    static constexpr int TAPS = EPI == EPI_CONVT ? 1 : PAIR ? 6 : 5;
     static constexpr int ROWS = kTileM + TAPS - 1;           // halo'd tile rows
+    // the tile's first storage row relative to its first position: 0 for the k5 convs (the
+    // halo starts two rows before), kPad for the ConvT GEMM (row p + 2 holds position p)
+    static constexpr int ROW_OFF = EPI == EPI_CONVT ? kPad : 0;
+    // the layer's N split over NSPLIT groups of CTAs (CTA b computes part b % NSPLIT: COUT
+    // of the NSPLIT * COUT output channels, or of the N columns of a ConvT GEMM), for the
+    // wide network's layers whose whole weight image exceeds shared memory
+    static constexpr int NSPLIT = NSPLIT_;
+    static constexpr int POUT_TOT = NSPLIT * (COUT_ / (16 / (is16(PREC_) ? 2 : 1)));
     static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
     static constexpr bool PAIRED = PAIRED_;                 // taps stacked in pairs along N
     // per-interval layout: the event is kSlices sequences laid end to end, SEQ storage rows
@@ -130,7 +140,7 @@ struct Cfg {
     static constexpr int A2_COL0 = NB * COLS_BUF;            // A2 buffers after the accumulators
     static constexpr int TMEM_COLS = pow2ceil(NB * COLS_BUF + 2 * A2_COLS);
     // float parameters kept in shared memory: bias, bias2, column scales, final conv
-    static constexpr int NPAR = 2 * (COUT + N2) + (EPI == EPI_FINAL ? kFinalFloats : 0);
+    static constexpr int NPAR = 2 * (COUT + N2) + (EPI == EPI_FINAL ? 5 * COUT + 1 : 0);
     static constexpr int OFF_W = 0;
     static constexpr int OFF_W2 = align_up(OFF_W + W_BYTES, 128);
     static constexpr int OFF_PAR = align_up(OFF_W2 + W2_BYTES, 128);
@@ -151,7 +161,8 @@ struct Cfg {
     static_assert(N2 % 16 == 0 && N2 <= 256, "MMA N of the fused GEMM");
     static_assert(PIN % 2 == 0 || PAIR, "K planes come in pairs");
     static_assert(EPI != EPI_UP || P2 % 2 == 0, "fused GEMM K planes come in pairs");
-    static_assert(EPI != EPI_FINAL || COUT == kC0, "final conv reads c0 channels");
+    static_assert(EPI != EPI_FINAL || ((COUT == kC0 || COUT == kC0Max) && (!PAIRED || COUT == kC0)),
+                  "final conv reads c0 channels");
     static_assert(TMEM_COLS <= 512, "TMEM columns");
     static_assert(OFF_PAR % 16 == 0 && COUT % 4 == 0 && N2 % 4 == 0, "parameters read as float4");
     static_assert(OFF_X % 16 == 0, "paired exchange in float4");
@@ -161,6 +172,10 @@ struct Cfg {
                               (EWG <= 2 || EPI == EPI_UP)),
                   "tap pairing");
     static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(NSPLIT == 1 || ((EPI == EPI_STORE || EPI == EPI_CONVT) && !DYN && !SEQ && !PAIRED),
+                  "split layers: plain stores or the ConvT GEMM, static tiles, whole events");
+    static_assert(EPI != EPI_CONVT || (COUT % CUP == 0 && (2 / NSPLIT) * CUP == COUT && !PAIR && CB == 0),
+                  "ConvT GEMM: N = the part's r values x CUP");
     // the pool pairs lanes m, m + 1 as positions j, j + 1 of one sequence: even SEQ and LSEQ
     static_assert(!SEQ || (L == kSlices * SEQ - 2 * kPad &&
                            (EPI != EPI_POOL || (SEQ % 2 == 0 && LSEQ % 2 == 0))),
@@ -258,9 +273,10 @@ __device__ __forceinline__ void put16(unsigned char *p0, size_t plane_stride, co
     }
 }
 
-__device__ __forceinline__ void zero_planes(unsigned char *base, int64_t e, int planes, int64_t rows_e,
-                                            int64_t row) {
-    for (int k = 0; k < planes; ++k)
+// Zeroes storage row `row` of planes [k0, k0 + nk) of event e in a tensor of `planes` planes.
+__device__ __forceinline__ void zero_planes(unsigned char *base, int64_t e, int k0, int nk, int planes,
+                                            int64_t rows_e, int64_t row) {
+    for (int k = k0; k < k0 + nk; ++k)
         *reinterpret_cast<uint4 *>(base + planar_off(e, k, planes, rows_e, row)) = make_uint4(0, 0, 0, 0);
 }
 
@@ -272,12 +288,12 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
              *tide = bar + B::TIDE;
     const int ntiles = a.n_events * C::TPE;
     mbar_arrive_expect_tx(wbar, C::W_BYTES + C::W2_BYTES);
-    bulk_g2s(smem + C::OFF_W, a.w, C::W_BYTES, wbar);
+    bulk_g2s(smem + C::OFF_W, a.w + (size_t)((int)blockIdx.x % C::NSPLIT) * C::W_BYTES, C::W_BYTES, wbar);
     if (C::W2_BYTES) bulk_g2s(smem + C::OFF_W2, a.w2, C::W2_BYTES, wbar);
     int i = 0;
     bool ok = true;
     // DYN: one tile index ahead, so the atomic's latency overlaps a tile; else a stride
-    int t_next = C::DYN ? atomicAdd(a.sched, 1) : (int)blockIdx.x;
+    int t_next = C::DYN ? atomicAdd(a.sched, 1) : (int)blockIdx.x / C::NSPLIT;
     for (;; ++i) {
         const int t = t_next < ntiles ? t_next : -1;
         if constexpr (C::DYN) {   // next tile (or -1: none left) to the MMA thread and the epilogue
@@ -287,14 +303,14 @@ __device__ bool producer(const TcArgs &a, unsigned char *smem, uint64_t *bar, vo
             mbar_arrive(&tidf[r]);
         }
         if (t < 0) break;
-        t_next = C::DYN ? atomicAdd(a.sched, 1) : t + (int)gridDim.x;
+        t_next = C::DYN ? atomicAdd(a.sched, 1) : t + (int)gridDim.x / C::NSPLIT;
         const int s = i % C::STAGES;
         const uint32_t ph = (i / C::STAGES) & 1;
         if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
         int e, p0;
         tile_pos<C>(t, e, p0);
-        // tile row r <-> storage row p0 + r; rows before the event start are not copied
-        const int src0 = p0 > 0 ? p0 : 0, dst0 = src0 - p0;
+        // tile row r <-> storage row p0 + ROW_OFF + r; rows before the event start are not copied
+        const int src0 = p0 + C::ROW_OFF > 0 ? p0 + C::ROW_OFF : 0, dst0 = src0 - p0 - C::ROW_OFF;
         const int rows = min(C::ROWS - dst0, C::ROWS_E - src0);
         unsigned char *dst = smem + C::OFF_A + s * C::A_STAGE + dst0 * 16;
         if constexpr (C::PAIR) {
@@ -358,7 +374,7 @@ __device__ __forceinline__ void issue_conv(uint32_t d, uint32_t as, uint32_t w_b
         }
     } else {
 #pragma unroll
-        for (int tap = 0; tap < 5; ++tap)
+        for (int tap = 0; tap < C::TAPS; ++tap)
 #pragma unroll
             for (int kb = 0; kb < C::PIN / 2; ++kb) {
                 const uint64_t ad = smem_desc(as + 2 * kb * C::ROWS * 16 + tap * 16, C::ROWS * 16, 128);
@@ -424,7 +440,7 @@ __device__ bool mma_issuer(const TcArgs &a, unsigned char *smem, uint64_t *bar, 
             const int t = ring[r];
             mbar_arrive(&tide[r]);
             if (t < 0) break;
-        } else if ((int)blockIdx.x + i * (int)gridDim.x >= ntiles) {
+        } else if ((int)blockIdx.x / C::NSPLIT + i * ((int)gridDim.x / C::NSPLIT) >= ntiles) {
             break;
         }
         const int s = i % C::STAGES, b = i % C::NB;
@@ -587,8 +603,9 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
                 put16<C::PREC>(a2 + ((c0 / C::PW) * kTileM + m) * 16, (size_t)kTileM * 16, v, a.mid_inv);
             } else {
                 if (a.amax) amax_fold(a.amax, a.amax_out, v, valid);
-                if (valid)
-                    put16<C::PREC>(a.out + planar_off(e, c0 / C::PW, C::POUT, C::ROWS_E, p + kPad),
+                if (valid)   // a split layer's part writes its own planes of the output
+                    put16<C::PREC>(a.out + planar_off(e, ((int)blockIdx.x % C::NSPLIT) * C::POUT + c0 / C::PW,
+                                                      C::POUT_TOT, C::ROWS_E, p + kPad),
                               (size_t)C::ROWS_E * 16, v, a.out_inv);
                 if constexpr (C::EPI == EPI_POOL) {
                     float w[16];
@@ -605,9 +622,11 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
 
 // Fused ConvT columns [n_beg, n_beg + NC) (n = r * CUP + co: output row 2p + r, channel
 // co): bias, LeakyReLU, store; the thread of p = 0 / L - 1 (with pads) zeroes the pads.
+// r0: the first output-row parity of these columns (the ConvT GEMM split by r: its part).
 template <class C, int NC>
 __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, const float *scs2,
-                                       uint32_t dcol, int n_beg, int e, int p, bool valid, bool pads) {
+                                       uint32_t dcol, int n_beg, int e, int p, bool valid, bool pads,
+                                       int r0 = 0) {
     constexpr int LO = 2 * C::L;
     constexpr int64_t ROWS_O = C::ROWS_O;
     int sq, jq;
@@ -628,7 +647,7 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
 #pragma unroll
         for (int h = 0; h < LDW / 16; ++h) {
             const int c0 = n_beg + cc + 16 * h;
-            const int r = c0 / C::CUP, co0 = c0 % C::CUP;
+            const int r = r0 + c0 / C::CUP, co0 = c0 % C::CUP;
             float v[16], bj[16];
             lds16(sbias2 + co0, bj);
             if constexpr (is16(C::PREC)) {
@@ -648,21 +667,21 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
     }
     if constexpr (C::SEQ != 0) {     // each output sequence's zero rows
         if (pads && valid && jq == 0) {
-            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU);
-            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU + 1);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU + 1);
         }
         if (pads && valid && jq == C::LSEQ - 1) {
-            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 2);
-            zero_planes(a.out, e, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 1);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 2);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 1);
         }
     } else {
         if (pads && p == 0) {
-            zero_planes(a.out, e, PUP, ROWS_O, 0);
-            zero_planes(a.out, e, PUP, ROWS_O, 1);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, 0);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, 1);
         }
         if (pads && p == C::L - 1) {
-            zero_planes(a.out, e, PUP, ROWS_O, LO + kPad);
-            zero_planes(a.out, e, PUP, ROWS_O, LO + kPad + 1);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, LO + kPad);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, LO + kPad + 1);
         }
     }
 }
@@ -685,8 +704,9 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
     constexpr int64_t ROWS_P = C::ROWS_P;           // pooled tensor
     constexpr bool ROLES = C::EPI == EPI_UP && C::EWG >= 2;
     const int ntiles = a.n_events * C::TPE;
+    const int part = (int)blockIdx.x % C::NSPLIT;   // this CTA's part of a split layer
     for (int i = 0;; ++i) {
-        int t = (int)blockIdx.x + i * (int)gridDim.x;
+        int t = (int)blockIdx.x / C::NSPLIT + i * ((int)gridDim.x / C::NSPLIT);
         if constexpr (C::DYN) {
             const int r = i % kRing;
             if (!mbar_wait(&tidf[r], (i / kRing) & 1, abort)) return false;
@@ -737,39 +757,50 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
         }
         if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
         tc_fence_after();
+        if constexpr (C::EPI == EPI_CONVT) {   // the ConvT GEMM: this warpgroup's columns
+            epi_up<C, C::EPI_COLS>(a, sbias, scs, dcol, wg * C::EPI_COLS, e, p, valid, wg == 0 && part == 0,
+                                   part * (C::COUT / C::CUP));
+            tc_fence_before();
+            mbar_arrive(&tempty[b]);
+            continue;
+        }
         if constexpr (C::EPI == EPI_FINAL) {
-            float v[16];
+            constexpr int NCH = C::COUT / 16;       // 16-channel chunks of d1
+            float v[NCH][16];
             if constexpr (C::PAIRED) {
                 if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
-                paired_cols<C, 16>(dcol, 0, sx, q, lane, v);
+                paired_cols<C, 16>(dcol, 0, sx, q, lane, v[0]);
             } else {
-                tmem_ld16(dcol, v);
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) tmem_ld16(dcol + 16 * ch, v[ch]);
             }
             tc_fence_before();
             mbar_arrive(&tempty[b]);
-            float g[5];
-            {
+            float g[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
                 float bj[16], sc[16];
-                lds16(sbias, bj);
+                lds16(sbias + 16 * ch, bj);
                 if constexpr (is16(C::PREC)) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) sc[j] = 1.0f;
                 } else {
-                    lds16(scs, sc);
+                    lds16(scs + 16 * ch, sc);
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j)   // zero padding outside the event or its sequence
-                    v[j] = valid && inseq ? leaky(fmaf(v[j], sc[j], bj[j])) : 0.0f;
-            }
-            if (a.amax) amax_fold(a.amax, a.amax_out, v, valid && inseq);
+                    v[ch][j] = valid && inseq ? leaky(fmaf(v[ch][j], sc[j], bj[j])) : 0.0f;
+                if (a.amax) amax_fold(a.amax, a.amax_out, v[ch], valid && inseq);
+                // the final conv's partial sums over this chunk's channels, in channel order
 #pragma unroll
-            for (int tp = 0; tp < 5; ++tp) {
-                float wf[16];
-                lds16(sfin + tp * kC0, wf);
-                float acc = 0.0f;
+                for (int tp = 0; tp < 5; ++tp) {
+                    float wf[16];
+                    lds16(sfin + tp * C::COUT + 16 * ch, wf);
+                    float acc = g[tp];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc = fmaf(wf[j], v[j], acc);
-                g[tp] = acc;
+                    for (int j = 0; j < 16; ++j) acc = fmaf(wf[j], v[ch][j], acc);
+                    g[tp] = acc;
+                }
             }
             float *sg = reinterpret_cast<float *>(smem + C::OFF_G) + ab * 5 * kTileM;
 #pragma unroll
@@ -782,7 +813,7 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             const bool out = !C::SEQ || (jq >= kIvPad && jq < kIvPad + kSliceBins);
             if (m >= kPad && m < kPad + C::STRIDE && valid && out) {
                 // f(p) = b + sum_t g_t(p + t - 2), in tap order
-                float f = sfin[5 * kC0];
+                float f = sfin[5 * C::COUT];
 #pragma unroll
                 for (int tp = 0; tp < 5; ++tp) f += sg[tp * kTileM + m + tp - 2];
                 if constexpr (C::SEQ != 0) a.logits[(size_t)e * kBins + sq * kSliceBins + jq - kIvPad] = f;
@@ -809,19 +840,19 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                                      inseq);
             if (wg == 0 && (p == 0 || p == C::L - 1)) {
                 const int r0 = p == 0 ? 0 : C::L + kPad;
-                zero_planes(a.out, e, C::POUT, C::ROWS_E, r0);
-                zero_planes(a.out, e, C::POUT, C::ROWS_E, r0 + 1);
+                zero_planes(a.out, e, part * C::POUT, C::POUT, C::POUT_TOT, C::ROWS_E, r0);
+                zero_planes(a.out, e, part * C::POUT, C::POUT, C::POUT_TOT, C::ROWS_E, r0 + 1);
                 if constexpr (C::EPI == EPI_POOL && C::SEQ == 0) {
                     const int rp = p == 0 ? 0 : C::L / 2 + kPad;
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp);
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp + 1);
+                    zero_planes(a.outp, e, 0, C::POUT, C::POUT, ROWS_P, rp);
+                    zero_planes(a.outp, e, 0, C::POUT, C::POUT, ROWS_P, rp + 1);
                 }
             }
             if constexpr (C::EPI == EPI_POOL && C::SEQ != 0) {   // each pooled sequence's zero rows
                 if (wg == 0 && valid && (jq == 0 || jq == C::LSEQ - 2)) {
                     const int64_t rp = (int64_t)sq * C::SEQP + (jq == 0 ? 0 : C::SEQP - 2);
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp);
-                    zero_planes(a.outp, e, C::POUT, ROWS_P, rp + 1);
+                    zero_planes(a.outp, e, 0, C::POUT, C::POUT, ROWS_P, rp);
+                    zero_planes(a.outp, e, 0, C::POUT, C::POUT, ROWS_P, rp + 1);
                 }
             }
         }
@@ -843,11 +874,12 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
 
     // biases, column scales and the final conv in shared memory
     float *par = reinterpret_cast<float *>(smem + C::OFF_PAR);
+    const int part = (int)blockIdx.x % C::NSPLIT;   // this CTA's part of a split layer
     for (int k = threadIdx.x; k < C::NPAR; k += C::THREADS) {
         float v;
-        if (k < C::COUT) v = a.bias[k];
+        if (k < C::COUT) v = C::EPI == EPI_CONVT ? a.bias[k % C::CUP] : a.bias[part * C::COUT + k];
         else if (k < C::COUT + C::N2) v = a.bias2[(k - C::COUT) % (C::CUP > 0 ? C::CUP : 1)];
-        else if (k < 2 * C::COUT + C::N2) v = a.cs ? a.cs[k - C::COUT - C::N2] : 1.0f;
+        else if (k < 2 * C::COUT + C::N2) v = a.cs ? a.cs[part * C::COUT + k - C::COUT - C::N2] : 1.0f;
         else if (k < 2 * (C::COUT + C::N2)) v = a.cs2 ? a.cs2[k - 2 * C::COUT - C::N2] : 1.0f;
         else v = a.final_w[k - 2 * (C::COUT + C::N2)];
         par[k] = v;
@@ -951,7 +983,9 @@ cudaError_t launch_conv(const TcArgs &a, cudaStream_t s, const ProfHook *prof, c
     if (per_sm < 1) per_sm = 1;
     const int ntiles = a.n_events * C::TPE;
     int grid = sms * per_sm;
-    if (grid > ntiles) grid = ntiles;
+    if (grid > ntiles * C::NSPLIT) grid = ntiles * C::NSPLIT;
+    grid = grid / C::NSPLIT * C::NSPLIT;             // every part gets the same CTAs
+    if (grid < C::NSPLIT) grid = C::NSPLIT;
     ProfScope ps(prof, name, s);
     return launch_pdl(k_conv_tc<C>, dim3(grid), dim3(C::THREADS), (size_t)smem, s, a);
 }
@@ -996,6 +1030,25 @@ template <int PREC> struct NetIv {
                           S0>;
 };
 
+// The wide network (base width 32: 32/64/128/256 channels, §5's channel-count axis). The
+// enc4 (128 -> 256) and dec3 (256 -> 128) weight images (320 KB in 16 bits) exceed a CTA's
+// shared memory, so their output channels are split over CTA groups (parts of 64 or 32
+// channels in 16 bits, 128 or 64 in e4m3), they store e4 and d3, and their ConvTs run as
+// GEMM kernels of their own (up3 split by output-row parity r). dec2 + up1 has the shapes of
+// the narrow network's dec3 + up2.
+template <int PREC> struct Net32 {
+    static constexpr int SP = is16(PREC) ? 4 : 2;            // parts of enc4 and dec3
+    using Enc2 = Cfg<PREC, 32, 0, 64, 2000, EPI_POOL, 0, 4, 1, 80, 2, false, true>;
+    using Enc3 = Cfg<PREC, 64, 0, 128, 1000, EPI_POOL, 0, 3, 2, 128, 2, false, true>;
+    using Enc4 = Cfg<PREC, 128, 0, 256 / SP, 500, EPI_STORE, 0, 3, 1, 128, 2, false, false, false, 0, SP>;
+    using Up3 = Cfg<PREC, 256, 0, 128, 500, EPI_CONVT, 128, 2, 2, 128, 2, false, false, false, 0, 2>;
+    using Dec3 = Cfg<PREC, 128, 128, 128 / SP, 1000, EPI_STORE, 0, is16(PREC) ? 2 : 3, 1, 128, 2, false, false,
+                     false, 0, SP>;
+    using Up2 = Cfg<PREC, 128, 0, 128, 1000, EPI_CONVT, 64, 3, 2, 128, 2>;
+    using Dec2Up1 = Cfg<PREC, 64, 64, 64, 2000, EPI_UP, 32, 3, 2, 128, 3, conv_paired(3, PREC), false, true>;
+    using Dec1Final = Cfg<PREC, 32, 32, 32, 4000, EPI_FINAL, 0, 3, 1, 96, 4>;
+};
+
 // Index of each tensor-core layer in TcNet::w: enc2, enc3, enc4, dec3, dec2, dec1, up3, up2, up1
 const int kBlobIndex[9] = {7, 8, 9, 11, 13, 15, 10, 12, 14};
 
@@ -1032,9 +1085,10 @@ float fp8_scale(float amax) { return amax > 0.0f ? amax / 448.0f : 1.0f; }
 
 }  // namespace
 
-size_t tc_weight_bytes(int precision) {
+size_t tc_weight_bytes(int precision, int c0) {
     if (precision == PVF_FP32) return 0;
-    return 512 * 1024;   // packed weights (< 300 KB) + biases + fp8 column scales
+    // packed weights (< 300 KB; about 1.1 MB for the wide network) + biases + column scales
+    return c0 == kC0Max ? 2048 * 1024 : 512 * 1024;
 }
 
 bool tc_supported(int precision) { return is16(precision) || precision == PVF_FP8_E4M3; }
@@ -1045,6 +1099,12 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
                      std::vector<unsigned char> &out, TcNet *net, unsigned char *dev_base) {
     Packer pk{precision, is16(precision) ? 2 : 1, is16(precision) ? 8 : 16, {}};
     net->precision = precision;
+    // the base width from enc2's input channels; the wide network splits enc4 and dec3 into
+    // parts (each part's image contiguous) and runs up3 as a ConvT GEMM split by r
+    const int c0 = (int)layers[kBlobIndex[0]].shape[1];
+    net->c0 = c0;
+    const bool wide = c0 == kC0Max;
+    const int sp = is16(precision) ? 4 : 2;
     size_t off_w[9], off_b[9], off_s[9];
     for (int li = 0; li < 9; ++li) {
         const LayerF32 &Lw = layers[kBlobIndex[li]];
@@ -1074,10 +1134,16 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
                             const float w = Lw.w[((size_t)co * cin + ci) * 5 + t] / scale[co];
                             // paired: group g = t / 2 (N = 2 cout rows for taps 0-3, cout for
                             // tap 4), plane k, row (t % 2) * cout + co; else tap-major planes
+                            // wide enc4 / dec3: part co / (cout / sp) of the split, tap-major
+                            // planes of cout / sp rows inside the part
+                            const int cl = cout / sp;
                             const size_t row =
-                                conv_paired(li, precision) ? (size_t)(t / 2) * pin * 2 * cout +
-                                                      (size_t)k * (t < 4 ? 2 * cout : cout) + (t % 2) * cout + co
-                                                : ((size_t)t * pin + k) * cout + co;
+                                wide && (li == 2 || li == 3)
+                                    ? (size_t)(co / cl) * 5 * pin * cl + ((size_t)t * pin + k) * cl + co % cl
+                                : conv_paired(li, precision) && !(wide && li == 3)
+                                    ? (size_t)(t / 2) * pin * 2 * cout + (size_t)k * (t < 4 ? 2 * cout : cout) +
+                                          (t % 2) * cout + co
+                                    : ((size_t)t * pin + k) * cout + co;
                             pk.enc(w, &img[row * 16 + j * pk.es]);
                         }
         } else {
@@ -1101,7 +1167,10 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
                     for (int j = 0; j < pk.pw; ++j) {
                         const int ci = k * pk.pw + j, r = n / cup, co = n % cup;
                         const float w = Lw.w[((size_t)ci * cup + co) * 2 + r] / scale[n];
-                        pk.enc(w, &img[((size_t)k * n2 + n) * 16 + j * pk.es]);
+                        // the wide up3 (a ConvT GEMM split by r): part r's planes of cup rows
+                        const size_t row = wide && li == 6 ? (size_t)r * p2 * cup + (size_t)k * cup + co
+                                                           : (size_t)k * n2 + n;
+                        pk.enc(w, &img[row * 16 + j * pk.es]);
                     }
         }
         off_w[li] = pk.put_raw(img.data(), img.size());
@@ -1141,7 +1210,7 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
             }
     }
     const size_t off_fc = pk.put_raw(fcimg.data(), fcimg.size());
-    if (pk.bytes.size() > tc_weight_bytes(precision)) return false;
+    if (pk.bytes.size() > tc_weight_bytes(precision, c0)) return false;
     net->fc_img = dev_base + off_fc;
     for (int li = 0; li < 9; ++li) {
         net->w[li] = dev_base + off_w[li];
@@ -1201,6 +1270,63 @@ static cudaError_t run_tc(const TcNet &n, const UnetBuffers &b, int ne, const in
     return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final", n.ctas_per_sm[5]);
 }
 
+// The wide network (base width 32). Activation slots by liveness: e1 | e2 | e3 | deep = e4,
+// d3, u1 | up = u3, u2 | s0 = p1, p3 | s1 = p2.
+template <int PREC>
+static cudaError_t run_tc32(const TcNet &n, const UnetBuffers &b, int ne, const int32_t *n_dyn, int dyn_base,
+                            cudaStream_t s, const ProfHook *prof) {
+    using N = Net32<PREC>;
+    const float *sc = n.act_scale;
+    auto inv = [&](int i) { return is16(PREC) ? 1.0f : 1.0f / sc[i]; };
+    auto cs = [&](int li) { return is16(PREC) ? nullptr : n.wscale[li]; };
+    auto W = [&](int li) { return static_cast<const unsigned char *>(n.w[li]); };
+    auto U = [](void *p) { return static_cast<unsigned char *>(p); };
+    cudaError_t err;
+    TcArgs a{};
+    a.n_events = ne;
+    a.n_dyn = n_dyn;
+    a.dyn_base = dyn_base;
+    a.status = n.status;
+    a.amax = n.amax;
+    auto sched = [&](int k) { return n.sched + 2 * k; };
+    // enc2: p1 (s0) -> e2, p2 (s1)
+    a.sched = sched(0);
+    a.inA = U(b.s0); a.inB = nullptr; a.out = U(b.e2); a.outp = U(b.s1);
+    a.w = W(0); a.bias = n.b[0]; a.cs = cs(0); a.out_inv = inv(kScaleL2); a.amax_out = kScaleL2;
+    if ((err = launch_conv<typename N::Enc2>(a, s, prof, "enc2", n.ctas_per_sm[0])) != cudaSuccess) return err;
+    // enc3: p2 (s1) -> e3, p3 (s0)
+    a.inA = U(b.s1); a.out = U(b.e3); a.outp = U(b.s0); a.sched = sched(1);
+    a.w = W(1); a.bias = n.b[1]; a.cs = cs(1); a.out_inv = inv(kScaleL3); a.amax_out = kScaleL3;
+    if ((err = launch_conv<typename N::Enc3>(a, s, prof, "enc3", n.ctas_per_sm[1])) != cudaSuccess) return err;
+    // enc4 (split): p3 (s0) -> e4 (deep)
+    a.inA = U(b.s0); a.out = U(b.deep); a.outp = nullptr; a.sched = sched(2);
+    a.w = W(2); a.bias = n.b[2]; a.cs = cs(2); a.out_inv = inv(kScaleE4); a.amax_out = kScaleE4;
+    if ((err = launch_conv<typename N::Enc4>(a, s, prof, "enc4", n.ctas_per_sm[2])) != cudaSuccess) return err;
+    // up3 (ConvT GEMM, split by r): e4 (deep) -> u3 (up)
+    a.inA = U(b.deep); a.out = U(b.up);
+    a.w = W(6); a.bias = n.b[6]; a.cs = cs(6); a.out_inv = inv(kScaleL3); a.amax_out = kScaleL3;
+    if ((err = launch_conv<typename N::Up3>(a, s, prof, "up3", n.ctas_per_sm[2])) != cudaSuccess) return err;
+    // dec3 (split): [u3 (up), e3] -> d3 (deep)
+    a.inA = U(b.up); a.inB = U(b.e3); a.out = U(b.deep); a.sched = sched(3);
+    a.w = W(3); a.bias = n.b[3]; a.cs = cs(3); a.out_inv = inv(kScaleD3); a.amax_out = kScaleD3;
+    if ((err = launch_conv<typename N::Dec3>(a, s, prof, "dec3", n.ctas_per_sm[3])) != cudaSuccess) return err;
+    // up2 (ConvT GEMM): d3 (deep) -> u2 (up)
+    a.inA = U(b.deep); a.inB = nullptr; a.out = U(b.up);
+    a.w = W(7); a.bias = n.b[7]; a.cs = cs(7); a.out_inv = inv(kScaleL2); a.amax_out = kScaleL2;
+    if ((err = launch_conv<typename N::Up2>(a, s, prof, "up2", n.ctas_per_sm[3])) != cudaSuccess) return err;
+    // dec2 + up1: [u2 (up), e2] -> u1 (deep)
+    a.inA = U(b.up); a.inB = U(b.e2); a.out = U(b.deep); a.sched = sched(4);
+    a.w = W(4); a.bias = n.b[4]; a.cs = cs(4); a.w2 = W(8); a.bias2 = n.b[8]; a.cs2 = cs(8);
+    a.mid_inv = inv(kScaleD2); a.out_inv = inv(kScaleL1); a.amax_mid = kScaleD2; a.amax_out = kScaleL1;
+    if ((err = launch_conv<typename N::Dec2Up1>(a, s, prof, "dec2_up1", n.ctas_per_sm[4])) != cudaSuccess)
+        return err;
+    // dec1 + final conv: [u1 (deep), e1] -> logits (float32)
+    a.inA = U(b.deep); a.inB = U(b.e1); a.out = nullptr; a.w2 = nullptr; a.bias2 = nullptr; a.sched = sched(5);
+    a.cs2 = nullptr; a.logits = b.logits; a.final_w = n.final_w; a.amax_out = kScaleD1;
+    a.w = W(5); a.bias = n.b[5]; a.cs = cs(5);
+    return launch_conv<typename N::Dec1Final>(a, s, prof, "dec1_final", n.ctas_per_sm[5]);
+}
+
 // The enc2 kernel alone with its MMA thread stalled for stall_us (tests of the bounded waits).
 template <int PREC>
 static cudaError_t stall_tc(const TcNet &n, const UnetBuffers &b, int ne, uint32_t stall_us, cudaStream_t s) {
@@ -1234,6 +1360,14 @@ cudaError_t launch_stall_test_tc(const TcNet &net, const UnetBuffers &b, int n, 
 cudaError_t launch_unet_tc(const TcNet &net, const UnetBuffers &b, int n, const int32_t *n_dyn, int dyn_base,
                            cudaStream_t s, const ProfHook *prof) {
     if (n <= 0) return cudaSuccess;
+    if (net.c0 == kC0Max) {
+        switch (net.precision) {
+        case PVF_BF16: return run_tc32<PVF_BF16>(net, b, n, n_dyn, dyn_base, s, prof);
+        case PVF_FP16: return run_tc32<PVF_FP16>(net, b, n, n_dyn, dyn_base, s, prof);
+        case PVF_FP8_E4M3: return run_tc32<PVF_FP8_E4M3>(net, b, n, n_dyn, dyn_base, s, prof);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     if (net.iv) {
         switch (net.precision) {
         case PVF_BF16: return run_tc<PVF_BF16, NetIv<PVF_BF16>>(net, b, n, n_dyn, dyn_base, s, prof);

@@ -200,7 +200,6 @@ pvf_status check_config(const pvf_config *c) {
     if (c->chunk_events < 0 || c->chunk_events > c->max_events) return PVF_ERR_INVALID_ARG;
     if (!(c->boundary_mm >= 0.0f && c->boundary_mm < 5.0f)) return PVF_ERR_INVALID_ARG;
     if (c->unet_width != 0 && c->unet_width != kC0 && c->unet_width != kC0Max) return PVF_ERR_INVALID_ARG;
-    if (c->unet_width == kC0Max && c->precision != PVF_FP32) return PVF_ERR_UNSUPPORTED;
     if (c->per_interval != 0 && c->per_interval != 1) return PVF_ERR_INVALID_ARG;
     if (c->per_interval && c->unet_width == kC0Max) return PVF_ERR_UNSUPPORTED;
     if (c->schedule) {
@@ -239,7 +238,7 @@ Plan make_plan(const pvf_config *c) {
     p.ev_flag = o; o = align256(o + sizeof(int32_t) * (size_t)c->max_events);
     const int c0 = cfg_c0(c);
     p.f32w = o; o = align256(o + sizeof(float) * f32_layout(c0).total);
-    p.tcw = o; o = align256(o + tc_weight_bytes(c->precision));
+    p.tcw = o; o = align256(o + tc_weight_bytes(c->precision, c0));
     p.logits = o; o = align256(o + (c->precision != PVF_FP32 ? sizeof(float) * kBins * (size_t)p.chunk : 0));
     const size_t eb = elem_bytes(c->precision);
     // every activation tensor scales with the base width; the per-interval layout holds

@@ -41,9 +41,10 @@ struct TcNet {
     int32_t *sched;          // 6 x 2 tile-scheduler counters (zero between launches)
     int32_t ctas_per_sm[6];  // launch schedule per conv kernel (0 = as many as fit)
     int32_t iv;              // per-interval layout (kSlices sequences per event)
+    int32_t c0;              // UNet base width (16, or 32: the wide network)
 };
 
-size_t tc_weight_bytes(int precision);
+size_t tc_weight_bytes(int precision, int c0);
 bool tc_supported(int precision);
 // Packs the 9 tensor-core layers into host bytes destined for dev_base (offsets are
 // computed for that device address) and fills net with the device pointers.

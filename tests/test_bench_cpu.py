@@ -35,6 +35,13 @@ def test_fp32_kernel_table_macs_equal_the_layer_shapes(c0):
 
 
 @pytest.mark.parametrize("form", ["bf16", "fp16", "fp8"])
+def test_wide_tensor_core_kernel_table_covers_the_wide_macs(form):
+    t = bench.kernel_table(form, 32)
+    assert sum(v[0] + v[1] for v in t.values()) == unet_macs_from_shapes(32)
+    assert {"enc4", "up3", "dec3", "up2", "dec2_up1", "dec1_final"} <= set(t)
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp8"])
 def test_tensor_core_kernel_table_covers_the_same_macs(form):
     t = bench.kernel_table(form, 16)
     assert sum(v[0] + v[1] for v in t.values()) == unet_macs_from_shapes(16)

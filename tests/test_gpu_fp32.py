@@ -326,13 +326,6 @@ def test_wide_bitwise_reproducible_batch_invariant_and_chunked(lib, wide_pv, wid
         np.testing.assert_array_equal(rc[k], r1[k])
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
-def test_wide_unet_tensor_core_forms_unsupported(lib, wide_weights, precision):
-    from paper_2602_19959_gb300.pvf import PvfError, PVF_ERR_UNSUPPORTED
-    with pytest.raises(PvfError) as ei:
-        lib(wide_weights, precision=precision, max_events=4)
-    assert ei.value.code == PVF_ERR_UNSUPPORTED
-
 
 # ---------------------------------------------------------------- per-interval layout (§3)
 # Each of the 40 intervals runs the UNet as its own 104-bin sequence (two zero bins on each

@@ -62,12 +62,13 @@ def test_pool_bytes_required_and_config_validation(lib):
     assert 1.9 * fp32 < fp32w < 2.1 * fp32
     assert P.pool_bytes_required(precision="fp32", max_events=1000, unet_width=16) == fp32
     for prec in ("bf16", "fp16", "fp8"):
-        cfg, _ = P.make_config(precision=prec, max_events=10, unet_width=32)
+        # the wide network and the per-interval layout exist in every form, not combined
         out = ctypes.c_size_t(0)
+        for kw in (dict(unet_width=32), dict(per_interval=True)):
+            cfg, _ = P.make_config(precision=prec, max_events=10, **kw)
+            assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_OK
+        cfg, _ = P.make_config(precision=prec, max_events=10, unet_width=32, per_interval=True)
         assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
-        # the per-interval layout exists in every form
-        cfg, _ = P.make_config(precision=prec, max_events=10, per_interval=True)
-        assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_OK
     cfg, _ = P.make_config(precision="fp32", max_events=10, unet_width=32, per_interval=True)
     out = ctypes.c_size_t(0)
     assert lib.pvf_pool_bytes_required(ctypes.byref(cfg), ctypes.byref(out)) == P.PVF_ERR_UNSUPPORTED
