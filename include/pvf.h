@@ -102,16 +102,15 @@ typedef struct {
                                       slice 0 or above 39. Other values: INVALID_ARG.      */
     int32_t unet_width;            /* UNet base width c0 (levels c0, 2c0, 4c0, 8c0): 0 or 16
                                       = the 16/32/64/128 network; 32 = the wide 32/64/128/256
-                                      variant (§5's channel-count axis), PVF_FP32 only
-                                      (tensor-core forms: UNSUPPORTED). Must match the
-                                      blob's width (else pvf_create returns ERR_WEIGHTS).
-                                      Other values: INVALID_ARG.                            */
+                                      variant (§5's channel-count axis), every form. Must
+                                      match the blob's width (else pvf_create returns
+                                      ERR_WEIGHTS). Other values: INVALID_ARG.              */
     int32_t per_interval;          /* 0: the UNet runs over each event's 4000 bins. 1: the
                                       §3 per-interval layout -- each of the 40 intervals runs
                                       as its own 104-bin sequence (its 100 bins and two zero
                                       bins on each side) and its 100 central logits fill the
-                                      interval's bins. PVF_FP32 with width 16 only (other
-                                      forms: UNSUPPORTED). Other values: INVALID_ARG.       */
+                                      interval's bins. Every form, width 16 only (width 32:
+                                      UNSUPPORTED). Other values: INVALID_ARG.              */
     const float *fp8_act_scales;   /* host, PVF_FP8_E4M3 only: PVF_N_ACT_SCALES per-tensor
                                       input scales (amax / 448), or NULL to use
                                       pvf_calibrate before the first pvf_infer              */

@@ -260,9 +260,8 @@ class PVFinder:
     e.g. from calibrate() of a bf16 instance). max_events / max_tracks_per_event /
     max_pv_per_event / chunk_events: the frozen plan of pvf_config. boundary_mm: width of
     the band in which a track also fills the neighbouring slice (0: none).
-    per_interval: each interval runs the UNet as its own 104-bin sequence (float32 form,
-    width 16). Width 32 and per_interval are float32 only; other forms raise PvfError
-    with PVF_ERR_UNSUPPORTED. schedule: launch schedule (a dict of CTAs per SM per kernel
+    per_interval: each interval runs the UNet as its own 104-bin sequence (width 16; with
+    width 32 it raises PvfError with PVF_ERR_UNSUPPORTED). schedule: launch schedule (a dict of CTAs per SM per kernel
     family, e.g. the autotuner's table; None: the defaults)."""
 
     def __init__(self, weights: dict, precision="fp32", max_events=1024,
