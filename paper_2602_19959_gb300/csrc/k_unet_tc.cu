@@ -172,7 +172,7 @@ struct Cfg {
                               (EWG <= 2 || EPI == EPI_UP)),
                   "tap pairing");
     static_assert(SMEM <= 227 * 1024, "shared memory");
-    static_assert(NSPLIT == 1 || ((EPI == EPI_STORE || EPI == EPI_CONVT) && !DYN && !SEQ && !PAIRED),
+    static_assert(NSPLIT == 1 || ((EPI == EPI_STORE || EPI == EPI_CONVT) && !DYN && !SEQ),
                   "split layers: plain stores or the ConvT GEMM, static tiles, whole events");
     static_assert(EPI != EPI_CONVT || (COUT % CUP == 0 && (2 / NSPLIT) * CUP == COUT && !PAIR && CB == 0),
                   "ConvT GEMM: N = the part's r values x CUP");
@@ -835,8 +835,12 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             tc_fence_after();
             epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
         } else {                            // this warpgroup's conv columns
-            static_assert(!C::PAIRED || C::EPI == EPI_UP || C::EPI == EPI_FINAL, "paired stores");
-            epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid, nullptr, 0,
+            static_assert(!C::PAIRED || C::EPI == EPI_STORE, "paired stores");
+            if constexpr (C::PAIRED) {   // the wide network's split dec3: E[m] + O[m + 1]
+                if (!paired_publish<C, C::EPI_COLS>(dcol, wg * C::EPI_COLS, sx, q, lane, &xready[ab], ph_a, abort))
+                    return false;
+            }
+            epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid, sx, 0,
                                      inseq);
             if (wg == 0 && (p == 0 || p == C::L - 1)) {
                 const int r0 = p == 0 ? 0 : C::L + kPad;
@@ -1042,8 +1046,8 @@ template <int PREC> struct Net32 {
     using Enc3 = Cfg<PREC, 64, 0, 128, 1000, EPI_POOL, 0, 3, 2, 128, 2, false, true>;
     using Enc4 = Cfg<PREC, 128, 0, 256 / SP, 500, EPI_STORE, 0, 3, 1, 128, 2, false, false, false, 0, SP>;
     using Up3 = Cfg<PREC, 256, 0, 128, 500, EPI_CONVT, 128, 2, 2, 128, 2, false, false, false, 0, 2>;
-    using Dec3 = Cfg<PREC, 128, 128, 128 / SP, 1000, EPI_STORE, 0, is16(PREC) ? 2 : 3, 1, 128, 2, false, false,
-                     false, 0, SP>;
+    using Dec3 = Cfg<PREC, 128, 128, 128 / SP, 1000, EPI_STORE, 0, is16(PREC) ? 2 : 3, 1, 128, 2, is16(PREC),
+                     false, false, 0, SP>;
     using Up2 = Cfg<PREC, 128, 0, 128, 1000, EPI_CONVT, 64, 3, 2, 128, 2>;
     using Dec2Up1 = Cfg<PREC, 64, 64, 64, 2000, EPI_UP, 32, 3, 2, 128, 3, conv_paired(3, PREC), false, true>;
     using Dec1Final = Cfg<PREC, 32, 32, 32, 4000, EPI_FINAL, 0, 3, 1, 96, 4>;
@@ -1134,12 +1138,16 @@ bool tc_pack_weights(int precision, const std::vector<LayerF32> &layers, const f
                             const float w = Lw.w[((size_t)co * cin + ci) * 5 + t] / scale[co];
                             // paired: group g = t / 2 (N = 2 cout rows for taps 0-3, cout for
                             // tap 4), plane k, row (t % 2) * cout + co; else tap-major planes
-                            // wide enc4 / dec3: part co / (cout / sp) of the split, tap-major
-                            // planes of cout / sp rows inside the part
-                            const int cl = cout / sp;
+                            // wide enc4 / dec3: part co / (cout / sp) of the split; inside the
+                            // part tap-major planes of cout / sp rows (enc4, and dec3 in e4m3)
+                            // or the paired groups (16-bit dec3)
+                            const int cl = cout / sp, cp = co % cl;
                             const size_t row =
-                                wide && (li == 2 || li == 3)
-                                    ? (size_t)(co / cl) * 5 * pin * cl + ((size_t)t * pin + k) * cl + co % cl
+                                wide && li == 3 && is16(precision)
+                                    ? (size_t)(co / cl) * 5 * pin * cl + (size_t)(t / 2) * pin * 2 * cl +
+                                          (size_t)k * (t < 4 ? 2 * cl : cl) + (t % 2) * cl + cp
+                                : wide && (li == 2 || li == 3)
+                                    ? (size_t)(co / cl) * 5 * pin * cl + ((size_t)t * pin + k) * cl + cp
                                 : conv_paired(li, precision) && !(wide && li == 3)
                                     ? (size_t)(t / 2) * pin * 2 * cout + (size_t)k * (t < 4 ? 2 * cout : cout) +
                                           (t % 2) * cout + co
