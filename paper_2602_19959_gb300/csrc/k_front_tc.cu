@@ -1,24 +1,28 @@
 // Steps 1-2 of the path (§2) for the tensor-core forms: the per-track FC network on
 // tcgen05 (16-bit operands: f16 in the FP16 form, bf16 in the BF16 and FP8 forms; fp32
 // accumulation in TMEM), the deterministic histogram, and
-// enc1 + pool. A persistent grid (two CTAs per SM) walks the events, one event at a time
-// per CTA (§3: each event is processed by one thread block), so weights and TMEM are set
-// up once per CTA rather than once per event.
+// enc1 + pool. A persistent grid walks the events, one event at a time per CTA (§3: each
+// event is processed by one thread block), so weights and TMEM are set up once per CTA
+// rather than once per event. Two shapes: NT = 128 threads (one warpgroup, passes of 128
+// tracks, 128 TMEM columns; up to four CTAs per SM, the default) or NT = 256 (two
+// warpgroups, passes of 256 tracks, 256 columns; up to two per SM).
 //
-// Per pass of up to 256 slice-sorted tracks (two 128-row tiles, one per warpgroup, one
-// track per TMEM lane / thread in the hidden layers):
-//   X [256 x 16] (nine features, feature 2 slice-relative, zero padded) ->
+// Per pass of up to NT slice-sorted tracks (NT / 128 tiles of 128 rows, one per
+// warpgroup, one track per TMEM lane / thread in the hidden layers):
+//   X [NT x 16] (nine features, feature 2 slice-relative, zero padded) ->
 //   5 x { MMA per tile (M = 128 tracks, N = 32) -> TMEM -> bias + LeakyReLU -> 16-bit ->
-//         H [256 x 32] } ->
+//         H [NT x 32] } ->
 //   output layer as the transposed product Out^T = W6^T H^T (one MMA, M = 128 output
 //   lanes, N = tracks of the pass), so TMEM lane = output bin and column = sorted track ->
 //   each thread adds bias + softplus of its bin over the tracks in sorted order, flushing
 //   a slice's running sum into hist[100 s + j] when the slice's segment ends.
-// Warpgroup 0 takes the first half of the pass's tracks and warpgroup 1 the second;
-// warpgroup 1 adds its first segment's partial after warpgroup 0 has added its own, so
-// every bin is summed in one fixed order that depends only on the event's own sorted
-// track list: results are identical alone and in any batch. One thread issues the MMAs;
-// every wait on their completion is bounded.
+// With two warpgroups, warpgroup 0 takes the pass's first 128 tracks and warpgroup 1 the
+// rest; warpgroup 1 adds its first segment's partial after warpgroup 0 has added its own.
+// A bin's sum is thus split into partials at every multiple of 128 sorted tracks and
+// inside a partial runs in sorted order, in both shapes: every bin is summed in one fixed
+// order that depends only on the event's own sorted track list, so results are identical
+// alone, in any batch and under either shape. One thread issues the MMAs; every wait on
+// their completion is bounded.
 #include "front_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -28,18 +32,17 @@ namespace {
 using namespace front;
 using namespace tc;
 
-constexpr int kT = 256;                 // threads: two warpgroups, one 128-row tile each
 constexpr int kRows = 128;              // tile rows = TMEM lanes
-constexpr int kPass = 2 * kRows;        // tracks per pass
-constexpr int kPlane = kPass * 16;      // bytes of one K-major plane of X or H
-constexpr int kTmemCols = 256;          // hidden layers: tile g at column 128 g; output: [0, N)
 
-struct TcSmem {
+// NT threads = NT / 128 warpgroups, one 128-row tile each; a pass holds NT tracks.
+// TMEM: NT columns (hidden layers: tile g at column 128 g; output layer: [0, N)).
+template <int NT> struct TcSmem {
+    static constexpr int kPlane = NT * 16;   // bytes of one K-major plane of X or H
     static constexpr size_t img = 0;                                   // kFcImgBytes
     static constexpr size_t bias = img + kFcImgBytes;                  // kFcBTotal floats
     static constexpr size_t enc1 = bias + sizeof(float) * kFcBTotal;   // kEnc1Floats
-    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1FloatsMax + 127) / 128 * 128;  // 2 planes x 256 rows
-    static constexpr size_t h = x + 2 * kPlane;                        // 4 planes x 256 rows
+    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1FloatsMax + 127) / 128 * 128;  // 2 planes x NT rows
+    static constexpr size_t h = x + 2 * kPlane;                        // 4 planes x NT rows
     static constexpr size_t hist = h + 4 * kPlane;
     static constexpr size_t cnt = hist + sizeof(float) * kBins;
     static constexpr size_t seg = cnt + sizeof(int) * 48;
@@ -75,8 +78,11 @@ __device__ __forceinline__ float softplus_tc(float x) {
 
 // EDGE: boundary tracks fill a second slice (a.edge > 0); without them the sort and the
 // entry decoding compile to the one-slice form.
-template <int PREC, bool EDGE>
-__global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
+template <int PREC, bool EDGE, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_front_tc(FrontArgs a) {
+    static_assert(NT == 128 || NT == 256, "one or two warpgroups");
+    using TcSmem = pvf::TcSmem<NT>;
+    constexpr int kT = NT, kPass = NT, kPlane = TcSmem::kPlane, kTmemCols = NT;
     using T = typename Elem<PREC>::T;
     using FT = typename FcOp<PREC>::T;
     constexpr uint32_t FMT = FcOp<PREC>::FMT;
@@ -152,8 +158,8 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
             int nvalid;
             validate_sort<kT, EDGE>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
             if (failed) nvalid = 0;        // a timed-out MMA ends the tensor-core work
-            for (int c0 = 0; c0 < nvalid && !failed; c0 += 2 * kRows) {
-                const int ntile = nvalid - c0 > kRows ? 2 : 1;
+            for (int c0 = 0; c0 < nvalid && !failed; c0 += kPass) {
+                const int ntile = NT == 128 ? 1 : (nvalid - c0 > kRows ? 2 : 1);
                 const bool active = g < ntile;         // warpgroup has a tile in this pass
                 const int r = c0 + g * kRows + m;
                 const bool live = r < nvalid;
@@ -222,14 +228,14 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
                         continue;
                     }
                     // output layer: warpgroup g adds its bin over pass rows [cb, ce) in order
-                    const int half = min(nrow, (nrow + 63) / 64 * 32);   // a multiple of 32
+                    const int half = min(nrow, kRows);
                     const int cb = g == 0 ? 0 : half, ce = g == 0 ? min(half, nrow) : nrow;
                     float acc = 0.0f, held = 0.0f;
                     int held_s = -1;
                     if (cb < ce) {
                         int s = entry_slice<EDGE>(ssorted[c0 + cb], sslice);
                         int send = sseg[s + 1] - c0;           // first pass row past slice s
-                        bool hold = g == 1;                    // warpgroup 1 holds its first segment
+                        bool hold = NT == 256 && g == 1;       // warpgroup 1 holds its first segment
 #pragma unroll 1
                         for (int col = cb; col < ce; col += 32) {
                             float v[32];
@@ -311,28 +317,36 @@ __global__ void __launch_bounds__(kT, 2) k_front_tc(FrontArgs a) {
 
 }  // namespace
 
-template <int PREC, bool EDGE>
-cudaError_t launch_front_tc_k(const FrontArgs &a, cudaStream_t s) {
-    // persistent grid: as many CTAs as fit on the GPU at once (shared memory allows two
-    // per SM, which also fill the 512 TMEM columns), each walking events
-    const size_t smem = TcSmem::total(a.max_tracks, a.edge);
+template <int PREC, bool EDGE, int NT>
+cudaError_t launch_front_tc_k(const FrontArgs &a, int per_sm, cudaStream_t s) {
+    // persistent grid: up to per_sm CTAs per SM, as shared memory allows (NT TMEM columns
+    // each: 512 / NT CTAs fill an SM's 512 columns), each walking events
+    const size_t smem = TcSmem<NT>::total(a.max_tracks, a.edge);
     int sms = 0;
     cudaError_t err = current_device_sms(&sms);
-    if (err == cudaSuccess) err = prepare_kernel((const void *)k_front_tc<PREC, EDGE>, smem, nullptr);
+    if (err == cudaSuccess) err = prepare_kernel((const void *)k_front_tc<PREC, EDGE, NT>, smem, nullptr);
     if (err != cudaSuccess) return err;
-    int per_sm = (int)((228 * 1024) / (smem + 1024));
-    if (per_sm > 2) per_sm = 2;
-    if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
+    const int fit = (int)((228 * 1024) / (smem + 1024));
+    if (per_sm > fit) per_sm = fit;
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;
-    k_front_tc<PREC, EDGE><<<grid, kT, smem, s>>>(a);
+    k_front_tc<PREC, EDGE, NT><<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// CTAs per SM (the schedule's value, 0 = 4): 1 or 2 run the two-warpgroup shape, 3 or 4
+// (and larger values, clamped) the one-warpgroup shape.
+template <int PREC, bool EDGE>
+cudaError_t launch_front_tc_e(const FrontArgs &a, cudaStream_t s) {
+    const int per_sm = a.ctas_per_sm > 0 ? a.ctas_per_sm : 4;
+    if (per_sm <= 2) return launch_front_tc_k<PREC, EDGE, 256>(a, per_sm, s);
+    return launch_front_tc_k<PREC, EDGE, 128>(a, per_sm > 4 ? 4 : per_sm, s);
 }
 
 template <int PREC>
 cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
-    return a.edge > 0.0f ? launch_front_tc_k<PREC, true>(a, s) : launch_front_tc_k<PREC, false>(a, s);
+    return a.edge > 0.0f ? launch_front_tc_e<PREC, true>(a, s) : launch_front_tc_e<PREC, false>(a, s);
 }
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {
