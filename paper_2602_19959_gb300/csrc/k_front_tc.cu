@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_front_tc(FrontArgs a) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TcSmem::bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TcSmem::bar + 8);
     volatile int *never = reinterpret_cast<volatile int *>(smem + TcSmem::bar + 12);
+    int *snext = reinterpret_cast<int *>(smem + TcSmem::bar + 16);   // the CTA's next event
     uint16_t *ssorted = reinterpret_cast<uint16_t *>(smem + TcSmem::sorted);
     uint8_t *sslice = smem + TcSmem::slices(EDGE ? 2 * a.max_tracks : a.max_tracks);
 
@@ -145,8 +146,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_front_tc(FrontArgs a) {
     if (a.n_dyn_copy && blockIdx.x == 0 && tid == 0)
         *a.n_dyn_copy = *reinterpret_cast<const volatile int32_t *>(a.n_dyn);
 
-    // persistent: the CTA walks the launch's events
-    for (int e = blockIdx.x; e < n_ev; e += gridDim.x) {
+    // persistent: the CTA walks the launch's events, its first one blockIdx.x, then the
+    // next unclaimed one (a global ticket: CTAs that finish early take more events, and
+    // each event is still computed whole by one CTA, so results do not depend on which)
+    for (int e = blockIdx.x; e < n_ev;) {
         const int ge = a.ev_base + e;
         if (a.hist_in) {
             const float *src = a.hist_in + (size_t)ge * kBins;
@@ -301,7 +304,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_front_tc(FrontArgs a) {
         if (a.iv) enc1_pool<T, kT, true, kC0, true>(a, e, tid, shist, senc);
         else if (a.c0 == kC0Max) enc1_pool<T, kT, false, kC0Max>(a, e, tid, shist, senc);   // the wide network
         else enc1_pool<T, kT>(a, e, tid, shist, senc);
+        if (tid == 0) *snext = a.ev_ctr ? (int)gridDim.x + atomicAdd(a.ev_ctr, 1) : e + (int)gridDim.x;
         __syncthreads();                   // shist and the sort arrays are reused next event
+        e = *snext;
     }
     if (failed && tid == 0) {
         // the last MMAs still complete before TMEM is released
@@ -313,6 +318,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_front_tc(FrontArgs a) {
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (a.ev_ctr && tid == 0) {   // the last CTA to finish resets the tickets for the next launch
+        __threadfence();
+        if (atomicAdd(a.ev_ctr + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(a.ev_ctr, 0);
+            atomicExch(a.ev_ctr + 1, 0);
+        }
+    }
 }
 
 }  // namespace

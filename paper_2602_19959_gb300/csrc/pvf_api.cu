@@ -224,8 +224,10 @@ void slot_elems(int L0, int c0, int seqs, size_t *big, size_t *small) {
 }
 
 constexpr int kMaxIvChunk = 65535 / kSlices;
-// Byte offset, inside the 256-byte status block, of the device copy of a dynamic event
-// count (status word at 0, calibration maxima at 64, tile schedulers at 128..176).
+// Byte offsets, inside the 256-byte status block, of the front's event tickets and of the
+// device copy of a dynamic event count (status word at 0, calibration maxima at 64, tile
+// schedulers at 128..176).
+constexpr size_t kFrontCtrOff = 176;
 constexpr size_t kDynCountOff = 192;
 
 Plan make_plan(const pvf_config *c) {
@@ -535,6 +537,7 @@ static cudaError_t run_chunk(pvf_handle *h, const pvf_tracks_soa *tracks, const 
             err = launch_front(a, prec, h->front_smem, s);
         } else {
             a.fc_img = h->tc.fc_img;
+            a.ev_ctr = reinterpret_cast<int32_t *>(h->pool + h->plan.status + kFrontCtrOff);
             err = launch_front_tc(a, prec, s);
         }
         if (err != cudaSuccess) return err;
