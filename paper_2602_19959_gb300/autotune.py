@@ -5,8 +5,7 @@ A launch's schedule has two kinds of free parameters:
     keep a pass's activations resident in the 129 MB L2 and shrink the pool; large chunks
     give each layer kernel more tiles per SM and fewer launches;
   * the grids: how many CTAs per SM each persistent kernel family launches (pvf_schedule:
-    the front, whose grid sets the events each CTA walks and, in the tensor-core forms,
-    the FC tile (passes of 256 tracks at 1-2 CTAs per SM, 128 at 3-4), the six tensor-core conv
+    the front, whose grid sets the events each CTA walks, the six tensor-core conv
     kernels, whose grids set the tiles per CTA, and the peak finder). More resident CTAs
     hide latency; fewer leave each CTA more shared-memory and register headroom and
     shorten the tail of the last wave.
