@@ -90,6 +90,10 @@ struct Cfg {
     // TMEM accumulator buffers: the MMAs of tile i wait only for the epilogue of tile i - NB
     static constexpr int NB = NB_;
     static constexpr int EPI_COLS = COUT / EWG;              // conv columns per epilogue thread
+    // columns per TMEM load of the conv epilogue for nc columns, and (paired taps) the
+    // exchanges on xready per tile: one per load
+    static constexpr int ldw(int nc) { return nc % 32 == 0 && (EWG == 2 || EPI == EPI_UP) ? 32 : 16; }
+    static constexpr int xchunks(int nc) { return nc / ldw(nc); }
     static constexpr int PA = CA / PW, PB = CB / PW, PIN = PA + PB, POUT = COUT / PW;
     // A single input plane is half an MMA's K (32 bytes): pair taps (2j, 2j+1) in one MMA
     // by pointing the K-adjacent core matrix at the next row; a 6th zero tap pads.
@@ -174,7 +178,7 @@ struct Cfg {
     static_assert(SMEM <= 227 * 1024, "shared memory");
     static_assert(NSPLIT == 1 || ((EPI == EPI_STORE || EPI == EPI_CONVT) && !DYN && !SEQ),
                   "split layers: plain stores or the ConvT GEMM, static tiles, whole events");
-    static_assert(EPI != EPI_CONVT || (COUT % CUP == 0 && (2 / NSPLIT) * CUP == COUT && !PAIR && CB == 0),
+    static_assert(EPI != EPI_CONVT || (COUT % (CUP ? CUP : 1) == 0 && (2 / NSPLIT) * CUP == COUT && !PAIR && CB == 0),
                   "ConvT GEMM: N = the part's r values x CUP");
     // the pool pairs lanes m, m + 1 as positions j, j + 1 of one sequence: even SEQ and LSEQ
     static_assert(!SEQ || (L == kSlices * SEQ - 2 * kPad &&
@@ -491,14 +495,37 @@ __device__ __forceinline__ void lds16(const float *p, float (&v)[16]) {
     }
 }
 
-// Paired taps: conv columns [c0, c0 + W) of row m = E[m] + O[m + 1]. O[m + 1] comes from
-// the next lane, or for lane 31 from the next quarter's published first row (sx).
-template <class C, int W>
-__device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *sx, int q, int lane,
+// Paired taps: conv columns [c0, c0 + W) of row m = E[m] + O[m + 1]. The O columns are
+// loaded first: lane 0 of each quarter publishes its O row into sx and arrives on xready
+// (`use`: how many times this barrier completed before, for its parity); O[m + 1] then
+// comes from the next lane, or for lane 31 from the next quarter's published row. With
+// several column chunks per tile (MANY) the E columns load while the conv epilogue's
+// threads meet; with one, E and O load together after the meeting (each measured the
+// faster of the two orders: dec3_up2 96.1 -> 92.5 us, dec2_up1 74.8 vs 76.4 us).
+// Returns false on a timed-out wait.
+template <class C, int W, bool MANY>
+__device__ __forceinline__ bool paired_cols(uint32_t dcol, int c0, float *sx, int q, int lane,
+                                            uint64_t *xready, uint32_t use, volatile int *abort,
                                             float (&v)[W]) {
     float o[W];
-    if constexpr (W == 32) tmem_ld32x2(dcol + c0, dcol + C::COUT + c0, v, o);
-    else tmem_ld16x2(dcol + c0, dcol + C::COUT + c0, v, o);
+    if constexpr (W == 32) tmem_ld32(dcol + C::COUT + c0, o);
+    else tmem_ld16(dcol + C::COUT + c0, o);
+    if (lane == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(sx + q * C::COUT + c0);
+#pragma unroll
+        for (int j4 = 0; j4 < W / 4; ++j4)
+            d4[j4] = make_float4(o[4 * j4], o[4 * j4 + 1], o[4 * j4 + 2], o[4 * j4 + 3]);
+    }
+    mbar_arrive(xready);
+    if constexpr (MANY) {
+        if constexpr (W == 32) tmem_ld32(dcol + c0, v);
+        else tmem_ld16(dcol + c0, v);
+        if (!mbar_wait(xready, use & 1u, abort)) return false;
+    } else {
+        if (!mbar_wait(xready, use & 1u, abort)) return false;
+        if constexpr (W == 32) tmem_ld32x2(dcol + c0, dcol + C::COUT + c0, v, o);
+        else tmem_ld16x2(dcol + c0, dcol + C::COUT + c0, v, o);
+    }
 #pragma unroll
     for (int j = 0; j < W; ++j) o[j] = __shfl_down_sync(0xffffffffu, o[j], 1);
     if (lane == 31) {     // row 32 q + 31: its O[m + 1] is the next quarter's first row
@@ -511,52 +538,35 @@ __device__ __forceinline__ void paired_cols(uint32_t dcol, int c0, const float *
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) v[j] += o[j];
-}
-
-// Paired taps: lane 0 of each quarter publishes its O row (columns [c_beg, c_beg + NC))
-// into sx, then the threads of the conv epilogue meet on xready. Returns false on a
-// timed-out wait.
-template <class C, int NC>
-__device__ __forceinline__ bool paired_publish(uint32_t dcol, int c_beg, float *sx, int q, int lane,
-                                               uint64_t *xready, uint32_t parity, volatile int *abort) {
-    constexpr int W = NC % 32 == 0 ? 32 : 16;
-#pragma unroll 1
-    for (int c0 = c_beg; c0 < c_beg + NC; c0 += W) {
-        float o[W];
-        if constexpr (W == 32) tmem_ld32(dcol + C::COUT + c0, o);
-        else tmem_ld16(dcol + C::COUT + c0, o);
-        if (lane == 0) {
-            float4 *d4 = reinterpret_cast<float4 *>(sx + q * C::COUT + c0);
-#pragma unroll
-            for (int j4 = 0; j4 < W / 4; ++j4)
-                d4[j4] = make_float4(o[4 * j4], o[4 * j4 + 1], o[4 * j4 + 2], o[4 * j4 + 3]);
-        }
-    }
-    mbar_arrive(xready);
-    return mbar_wait(xready, parity, abort);
+    return true;
 }
 
 // Epilogue pieces, one TMEM lane (tile row m, position p) per thread.
 // Conv columns [c_beg, c_beg + NC) of accumulator dcol: bias, LeakyReLU, then either the
 // fused ConvT's shared-memory operand (A2) or the stored output (+ the 2:1 max-pool).
 // inseq: the row is a position of a sequence (false: a zero row between sequences of the
-// per-interval layout, stored as zeros).
+// per-interval layout, stored as zeros). Paired taps: the exchange of each column chunk
+// meets on xready, which completed xuse0 times before this tile (returns false on a
+// timed-out wait).
 template <class C, int NC>
-__device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
+__device__ __forceinline__ bool epi_conv(const TcArgs &a, unsigned char *smem, const float *sbias,
                                          const float *scs, uint32_t dcol, int c_beg, int ab, int e,
-                                         int p, int m, bool valid, const float *sx = nullptr,
-                                         uint32_t a2t = 0, bool inseq = true) {
+                                         int p, int m, bool valid, float *sx = nullptr,
+                                         uint32_t a2t = 0, bool inseq = true, uint64_t *xready = nullptr,
+                                         uint32_t xuse0 = 0, volatile int *abort = nullptr) {
     constexpr int64_t ROWS_P = C::ROWS_P;
     int sq, jq;
     seq_pos<C>(p, sq, jq);
     // pooled row: position j / 2 of sequence s (whole events: p / 2)
     const int64_t prow = C::SEQ ? (int64_t)sq * C::SEQP + jq / 2 + kPad : p / 2 + kPad;
-    constexpr int LDW = NC % 32 == 0 && (C::EWG == 2 || C::EPI == EPI_UP) ? 32 : 16;
+    constexpr int LDW = C::ldw(NC);
 #pragma unroll 1
     for (int cc = 0; cc < NC; cc += LDW) {
         float vv[LDW];
         if constexpr (C::PAIRED) {
-            paired_cols<C, LDW>(dcol, c_beg + cc, sx, m >> 5, m & 31, vv);
+            if (!paired_cols<C, LDW, (NC > LDW)>(dcol, c_beg + cc, sx, m >> 5, m & 31, xready, xuse0 + cc / LDW,
+                                                 abort, vv))
+                return false;
         } else if constexpr (LDW == 32) {
             tmem_ld32(dcol + c_beg + cc, vv);
         } else {
@@ -618,6 +628,7 @@ __device__ __forceinline__ void epi_conv(const TcArgs &a, unsigned char *smem, c
             }
         }
     }
+    return true;
 }
 
 // Fused ConvT columns [n_beg, n_beg + NC) (n = r * CUP + co: output row 2p + r, channel
@@ -735,13 +746,10 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             if (wg < PER) {     // conv accumulator -> ConvT operand
                 if (!mbar_wait(&tfull[b], ph_b, abort)) return false;
                 tc_fence_after();
-                if constexpr (C::PAIRED) {
-                    if (!paired_publish<C, C::COUT / PER>(dcol, part * (C::COUT / PER), sx, q, lane, &xready[ab],
-                                                          ph_a, abort))
-                        return false;
-                }
-                epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
-                                           valid, sx, a2_lane + ab * C::A2_COLS, inseq);
+                if (!epi_conv<C, C::COUT / PER>(a, smem, sbias, scs, dcol, part * (C::COUT / PER), ab, e, p, m,
+                                                valid, sx, a2_lane + ab * C::A2_COLS, inseq, &xready[ab],
+                                                (uint32_t)(i >> 1) * C::xchunks(C::COUT / PER), abort))
+                    return false;
                 if constexpr (C::A2T) tmem_st_wait();   // A2 in TMEM complete before the MMA reads it
                 else fence_proxy_async_smem();          // A2 writes -> visible to the tensor core
                 tc_fence_before();
@@ -768,8 +776,8 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             constexpr int NCH = C::COUT / 16;       // 16-channel chunks of d1
             float v[NCH][16];
             if constexpr (C::PAIRED) {
-                if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
-                paired_cols<C, 16>(dcol, 0, sx, q, lane, v[0]);
+                if (!paired_cols<C, 16, false>(dcol, 0, sx, q, lane, &xready[ab], (uint32_t)(i >> 1), abort, v[0]))
+                    return false;
             } else {
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) tmem_ld16(dcol + 16 * ch, v[ch]);
@@ -822,11 +830,10 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             continue;
         }
         if constexpr (C::EPI == EPI_UP) {   // one warpgroup: conv, then the ConvT
-            if constexpr (C::PAIRED) {
-                if (!paired_publish<C, C::COUT>(dcol, 0, sx, q, lane, &xready[ab], ph_a, abort)) return false;
-            }
-            epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx, a2_lane + ab * C::A2_COLS,
-                                 inseq);
+            if (!epi_conv<C, C::COUT>(a, smem, sbias, scs, dcol, 0, ab, e, p, m, valid, sx,
+                                      a2_lane + ab * C::A2_COLS, inseq, &xready[ab],
+                                      (uint32_t)(i >> 1) * C::xchunks(C::COUT), abort))
+                return false;
             if constexpr (C::A2T) tmem_st_wait();
             else fence_proxy_async_smem();
             tc_fence_before();
@@ -836,12 +843,10 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
             epi_up<C, C::N2>(a, sbias2, scs2, dcol, 0, e, p, valid, true);
         } else {                            // this warpgroup's conv columns
             static_assert(!C::PAIRED || C::EPI == EPI_STORE, "paired stores");
-            if constexpr (C::PAIRED) {   // the wide network's split dec3: E[m] + O[m + 1]
-                if (!paired_publish<C, C::EPI_COLS>(dcol, wg * C::EPI_COLS, sx, q, lane, &xready[ab], ph_a, abort))
-                    return false;
-            }
-            epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid, sx, 0,
-                                     inseq);
+            // paired taps (the wide network's split dec3): E[m] + O[m + 1]
+            if (!epi_conv<C, C::EPI_COLS>(a, smem, sbias, scs, dcol, wg * C::EPI_COLS, ab, e, p, m, valid, sx, 0,
+                                          inseq, &xready[ab], (uint32_t)(i >> 1) * C::xchunks(C::EPI_COLS), abort))
+                return false;
             if (wg == 0 && (p == 0 || p == C::L - 1)) {
                 const int r0 = p == 0 ? 0 : C::L + kPad;
                 zero_planes(a.out, e, part * C::POUT, C::POUT, C::POUT_TOT, C::ROWS_E, r0);
