@@ -102,14 +102,15 @@ def kernel_table(form, c0=16, iv=False):
         t["dec1_final"] = entry(m1, r1 * es + 16000, alu_mac=L0 * c1 * 5)
         t["tail"] = (0, 0, 16000)
     else:
-        m1, r1, _ = conv_io(L3, c3, c4); m2, _, w2 = convT_io(L3, c4, c3)
+        m1, r1, _ = scaled(conv_io(L3, c3, c4)); m2, _, w2 = scaled(convT_io(L3, c4, c3))
         t["enc4_up3"] = entry(m1 + m2, (r1 + w2) * es)
-        m1, r1, _ = conv_io(L2, 2 * c3, c3); m2, _, w2 = convT_io(L2, c3, c2)
+        m1, r1, _ = scaled(conv_io(L2, 2 * c3, c3)); m2, _, w2 = scaled(convT_io(L2, c3, c2))
         t["dec3_up2"] = entry(m1 + m2, (r1 + w2) * es)
-        m1, r1, _ = conv_io(L1, 2 * c2, c2); m2, _, w2 = convT_io(L1, c2, c1)
+        m1, r1, _ = scaled(conv_io(L1, 2 * c2, c2)); m2, _, w2 = scaled(convT_io(L1, c2, c1))
         t["dec2_up1"] = entry(m1 + m2, (r1 + w2) * es)
-        m1, r1, _ = conv_io(L0, 2 * c1, c1)
-        t["dec1_final"] = entry(m1, r1 * es + 16000, alu_mac=L0 * c1 * 5)   # final conv: fp32
+        m1, r1, _ = scaled(conv_io(L0, 2 * c1, c1))
+        # the final conv (fp32, CUDA cores) at the 4000 bins that get logits
+        t["dec1_final"] = entry(m1, r1 * es + 16000, alu_mac=4000 * c1 * 5)
         t["tail"] = (0, 0, 16000)
     return t
 
@@ -171,7 +172,7 @@ def roofline_of(name, launches, tot_ms, form, events_per_launch, tracks_per_laun
 # commands). Keyed by (form, kernel, events per launch); the value is (bytes, source). A
 # kernel changed since its capture has no entry and reports null.
 NCU_TRAFFIC = {
-    ("fp16", "dec3_up2", 1000): ((257.178880e6 + 90.632448e6),
+    ("fp16", "dec3_up2", 1000): ((257.183744e6 + 90.259456e6),
                                  "ncu --set full of one 1000-event launch (profiles/dec3_up2_fp16_1000ev.md)"),
 }
 

@@ -50,6 +50,21 @@ def test_tensor_core_kernel_table_covers_the_same_macs(form):
     assert sum(v[1] for v in t.values()) == 2 * 4000 * 16 * 5
 
 
+def test_per_interval_kernel_tables_count_every_sequence():
+    """The per-interval layout (§3): 40 sequences of 104 bins per event, each layer at
+    104 / 2^k positions per sequence; the final conv gives the 4000 central logits."""
+    shapes = synth.layer_shapes(16)
+    pos = {"enc1": 104, "enc2": 52, "enc3": 26, "enc4": 13, "dec3": 26, "dec2": 52, "dec1": 104}
+    want = sum(40 * L * shapes[n][0][0] * shapes[n][0][1] * shapes[n][0][2] for n, L in pos.items())
+    want += 4000 * 16 * 5                                       # final conv, 16 -> 1
+    for n, lin in {"up3": 13, "up2": 26, "up1": 52}.items():
+        cin, cout, k = shapes[n][0]
+        want += 40 * lin * cin * cout * k
+    for form in ("fp32", "bf16", "fp16", "fp8"):
+        t = bench.kernel_table(form, 16, iv=True)
+        assert sum(v[0] + v[1] for v in t.values()) == want, form
+
+
 def test_dominant_kernel_fraction_from_the_method_flops():
     """dec3_up2 (dec3 1000 x 64 x 640 plus up2 1000 x 64 x 64 MACs per event) at 100 us
     per 1000-event launch: 2 x 45.056e6 x 1000 FLOP / 100 us = 901 TFLOP/s."""
