@@ -225,6 +225,7 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
         bias[j] = senc[5 * kC0 + 8 * h + j];
     }
     float vmax = 0.0f;
+#pragma unroll 2   // two position pairs in flight per thread: front 81.6 -> 79.5 us (FP16)
     for (int qi = tid >> 1; qi < NQ; qi += NT / 2) {
         // the pair's sequence (IV) and first position; e1 rows r1, r1 + 1, p1 row r2
         const int sq = IV ? qi / (kIvLen / 2) : 0, q = IV ? qi % (kIvLen / 2) : qi;
