@@ -79,8 +79,11 @@ typedef enum {
  * parameters (the events per CTA of the front follow from its grid); results do not
  * depend on them. */
 typedef struct {
-    int32_t front_ctas_per_sm;     /* front kernel (steps 1-2 + enc1): 1..4 in the
-                                      tensor-core forms, 1..2 in the float32 form           */
+    int32_t front_ctas_per_sm;     /* front kernel (steps 1-2 + enc1), tensor-core forms:
+                                      1-2 run 256-thread CTAs (FC passes of 256 tracks), 3-4
+                                      128-thread CTAs (passes of 128 tracks); 0 = 2 for
+                                      launches of at most 4 events per SM, else 4. The
+                                      float32 front: 1..2                                   */
     int32_t conv_ctas_per_sm[6];   /* tensor-core forms: enc2, enc3, enc4_up3, dec3_up2,
                                       dec2_up1, dec1_final                                    */
     int32_t tail_ctas_per_sm;      /* peak finder: 1..8                                         */

@@ -5,7 +5,8 @@ A launch's schedule has two kinds of free parameters:
     keep a pass's activations resident in the 129 MB L2 and shrink the pool; large chunks
     give each layer kernel more tiles per SM and fewer launches;
   * the grids: how many CTAs per SM each persistent kernel family launches (pvf_schedule:
-    the front, whose grid sets the events each CTA walks, the six tensor-core conv
+    the front, whose grid sets the events each CTA walks and, in the tensor-core forms,
+    the FC tile (passes of 256 tracks at 1-2 CTAs per SM, 128 at 3-4), the six tensor-core conv
     kernels, whose grids set the tiles per CTA, and the peak finder). More resident CTAs
     hide latency; fewer leave each CTA more shared-memory and register headroom and
     shorten the tail of the last wave.
@@ -23,7 +24,7 @@ import os
 
 FAMILIES = ("front", "enc2", "enc3", "enc4_up3", "dec3_up2", "dec2_up1", "dec1_final", "tail")
 # CTAs per SM tried for each family (0 = as many as fit; the library clamps larger values)
-GRID_CANDIDATES = {"front": (1, 2, 3), "enc2": (2, 3, 4, 6), "enc3": (1, 2, 3, 4), "enc4_up3": (1,),
+GRID_CANDIDATES = {"front": (1, 2, 3, 4), "enc2": (2, 3, 4, 6), "enc3": (1, 2, 3, 4), "enc4_up3": (1,),
                    "dec3_up2": (1,), "dec2_up1": (1, 2), "dec1_final": (2, 3, 4, 5),
                    "tail": (1, 2, 4, 8)}
 TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")

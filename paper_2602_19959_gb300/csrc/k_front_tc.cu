@@ -1,24 +1,28 @@
 // Steps 1-2 of the path (§2) for the tensor-core forms: the per-track FC network on
 // tcgen05 (16-bit operands: f16 in the FP16 form, bf16 in the BF16 and FP8 forms; fp32
 // accumulation in TMEM), the deterministic histogram, and
-// enc1 + pool. A persistent grid (up to four 128-thread CTAs per SM, which fill the 512
-// TMEM columns) walks the events, one event at a time per CTA (§3: each event is
-// processed by one thread block), so weights and TMEM are set up once per CTA rather
-// than once per event.
+// enc1 + pool. A persistent grid walks the events, one event at a time per CTA (§3: each
+// event is processed by one thread block), so weights and TMEM are set up once per CTA
+// rather than once per event. Two shapes: NT = 128 threads (one warpgroup, passes of 128
+// tracks, 128 TMEM columns; up to four CTAs per SM, for large launches) or NT = 256 (two
+// warpgroups, passes of 256 tracks, 256 columns; up to two per SM, for small ones).
 //
-// Per pass of up to 128 slice-sorted tracks (one track per TMEM lane / thread in the
-// hidden layers):
-//   X [128 x 16] (nine features, feature 2 slice-relative, zero padded) ->
-//   5 x { MMA (M = 128 tracks, N = 32) -> TMEM -> bias + LeakyReLU -> 16-bit ->
-//         H [128 x 32] } ->
+// Per pass of up to NT slice-sorted tracks (NT / 128 tiles of 128 rows, one per
+// warpgroup, one track per TMEM lane / thread in the hidden layers):
+//   X [NT x 16] (nine features, feature 2 slice-relative, zero padded) ->
+//   5 x { MMA per tile (M = 128 tracks, N = 32) -> TMEM -> bias + LeakyReLU -> 16-bit ->
+//         H [NT x 32] } ->
 //   output layer as the transposed product Out^T = W6^T H^T (one MMA, M = 128 output
 //   lanes, N = tracks of the pass), so TMEM lane = output bin and column = sorted track ->
 //   each thread adds bias + softplus of its bin over the tracks in sorted order, flushing
-//   a slice's running sum into hist[100 s + j] when the slice's segment ends (and at the
-//   pass's last track).
-// Every bin is thus summed in one fixed order that depends only on the event's own
-// sorted track list: results are identical alone and in any batch. One thread issues the
-// MMAs; every wait on their completion is bounded.
+//   a slice's running sum into hist[100 s + j] when the slice's segment ends.
+// With two warpgroups, warpgroup 0 takes the pass's first 128 tracks and warpgroup 1 the
+// rest; warpgroup 1 adds its first segment's partial after warpgroup 0 has added its own.
+// A bin's sum is thus split into partials at every multiple of 128 sorted tracks and
+// inside a partial runs in sorted order, in both shapes: every bin is summed in one fixed
+// order that depends only on the event's own sorted track list, so results are identical
+// alone, in any batch and under either shape. One thread issues the MMAs; every wait on
+// their completion is bounded.
 #include "front_common.cuh"
 #include "tc_ptx.cuh"
 
@@ -28,22 +32,22 @@ namespace {
 using namespace front;
 using namespace tc;
 
-constexpr int kT = 128;                 // threads: one warpgroup
-constexpr int kRows = 128;              // tile rows = TMEM lanes = tracks per pass
-constexpr int kPlane = kRows * 16;      // bytes of one K-major plane of X or H
-constexpr int kTmemCols = 128;          // hidden layers: columns [0, 32); output: [0, N)
+constexpr int kRows = 128;              // tile rows = TMEM lanes
 
-struct TcSmem {
+// NT threads = NT / 128 warpgroups, one 128-row tile each; a pass holds NT tracks.
+// TMEM: NT columns (hidden layers: tile g at column 128 g; output layer: [0, N)).
+template <int NT> struct TcSmem {
+    static constexpr int kPlane = NT * 16;   // bytes of one K-major plane of X or H
     static constexpr size_t img = 0;                                   // kFcImgBytes
     static constexpr size_t bias = img + kFcImgBytes;                  // kFcBTotal floats
     static constexpr size_t enc1 = bias + sizeof(float) * kFcBTotal;   // kEnc1Floats
-    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1FloatsMax + 127) / 128 * 128;  // 2 planes x 128 rows
-    static constexpr size_t h = x + 2 * kPlane;                        // 4 planes x 128 rows
+    static constexpr size_t x = (enc1 + sizeof(float) * kEnc1FloatsMax + 127) / 128 * 128;  // 2 planes x NT rows
+    static constexpr size_t h = x + 2 * kPlane;                        // 4 planes x NT rows
     static constexpr size_t hist = h + 4 * kPlane;
     static constexpr size_t cnt = hist + sizeof(float) * kBins;
     static constexpr size_t seg = cnt + sizeof(int) * 48;
     static constexpr size_t run = seg + sizeof(int) * 48;
-    static constexpr size_t bar = (run + sizeof(int) * 48 + 15) / 16 * 16;   // mbarrier, TMEM slot, flag, next event
+    static constexpr size_t bar = (run + sizeof(int) * 48 + 15) / 16 * 16;   // mbarrier + slot + flag
     static constexpr size_t sorted = bar + 32;
     __host__ __device__ static size_t slices(int ne) { return sorted + 2 * (size_t)((ne + 7) / 8 * 8); }
     __host__ __device__ static size_t total(int mt, float edge) {
@@ -74,8 +78,11 @@ __device__ __forceinline__ float softplus_tc(float x) {
 
 // EDGE: boundary tracks fill a second slice (a.edge > 0); without them the sort and the
 // entry decoding compile to the one-slice form.
-template <int PREC, bool EDGE>
-__global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
+template <int PREC, bool EDGE, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_front_tc(FrontArgs a) {
+    static_assert(NT == 128 || NT == 256, "one or two warpgroups");
+    using TcSmem = pvf::TcSmem<NT>;
+    constexpr int kT = NT, kPass = NT, kPlane = TcSmem::kPlane, kTmemCols = NT;
     using T = typename Elem<PREC>::T;
     using FT = typename FcOp<PREC>::T;
     constexpr uint32_t FMT = FcOp<PREC>::FMT;
@@ -94,10 +101,11 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
     uint8_t *sslice = smem + TcSmem::slices(EDGE ? 2 * a.max_tracks : a.max_tracks);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = tid;                             // row of the pass = TMEM lane
-    const uint32_t lane_field = (uint32_t)(warp * 32) << 16;
+    const int g = warp >> 2;                       // tile of this warpgroup
+    const int m = tid & (kRows - 1);               // row within the tile = TMEM lane
+    const uint32_t lane_field = (uint32_t)((warp & 3) * 32) << 16;
     // output layer: this thread's TMEM lane holds output o (-1: a zero row)
-    const int o_bin = lane < kFcOutPerWarp ? warp * kFcOutPerWarp + lane : -1;
+    const int o_bin = lane < kFcOutPerWarp ? (warp & 3) * kFcOutPerWarp + lane : -1;
 
     // once per CTA: enc1 weights, FC operand images and biases, barrier, TMEM
     for (int i = tid; i < 6 * a.c0; i += kT) senc[i] = a.enc1[i];   // W[t][co] then b, c0 channels
@@ -125,9 +133,9 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
     grid_dep_launch();
     const uint32_t img = smem_u32(smem + TcSmem::img);
     const uint32_t sx = smem_u32(smem + TcSmem::x), sh = smem_u32(smem + TcSmem::h);
-    unsigned char *xrow = smem + TcSmem::x + (size_t)m * 16;   // + plane * kPlane
-    unsigned char *hrow = smem + TcSmem::h + (size_t)m * 16;
-    const uint32_t dcol = tmem + lane_field;
+    unsigned char *xrow = smem + TcSmem::x + (size_t)(g * kRows + m) * 16;   // + plane * kPlane
+    unsigned char *hrow = smem + TcSmem::h + (size_t)(g * kRows + m) * 16;
+    const uint32_t dcol = tmem + lane_field + (uint32_t)(g * 128);
     const float b6 = o_bin >= 0 ? sbias[5 * kFcHidden + o_bin] : 0.0f;
     bool failed = false;
     uint32_t phase = 0;
@@ -153,10 +161,12 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
             int nvalid;
             validate_sort<kT, EDGE>(a, ge, tid, scnt, sseg, srun, ssorted, sslice, t0, nvalid);
             if (failed) nvalid = 0;        // a timed-out MMA ends the tensor-core work
-            for (int c0 = 0; c0 < nvalid && !failed; c0 += kRows) {
-                const int r = c0 + m;
+            for (int c0 = 0; c0 < nvalid && !failed; c0 += kPass) {
+                const int ntile = NT == 128 ? 1 : (nvalid - c0 > kRows ? 2 : 1);
+                const bool active = g < ntile;         // warpgroup has a tile in this pass
+                const int r = c0 + g * kRows + m;
                 const bool live = r < nvalid;
-                {   // X row: the track's features in 16 bits, zero rows past the event
+                if (active) {   // X row: the track's features in 16 bits, zero rows past the event
                     float x[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) x[k] = 0.0f;
@@ -170,21 +180,25 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
                 fence_proxy_async_smem();
                 tc_fence_before();
                 __syncthreads();
-                const int nrow = min(nvalid - c0, kRows);
+                const int nrow = min(nvalid - c0, kPass);
                 const int n6 = (nrow + 15) / 16 * 16;          // output MMA: N = tracks, rounded
                 for (int l = 0; l < 6 && !failed; ++l) {
                     tc_fence_after();
                     if (tid == 0) {
                         if (l == 0) {
-                            mma_f16(tmem, smem_desc(sx, kPlane, 128), smem_desc(img, kFcHidden * 16, 128),
-                                    idesc_f32acc(kRows, kFcHidden, FMT), 0);
+                            for (int tg = 0; tg < ntile; ++tg)
+                                mma_f16(tmem + (uint32_t)(tg * 128), smem_desc(sx + tg * kRows * 16, kPlane, 128),
+                                        smem_desc(img, kFcHidden * 16, 128), idesc_f32acc(kRows, kFcHidden, FMT), 0);
                         } else if (l < 5) {
                             const uint32_t w = img + fc_img_off(l);
+                            for (int tg = 0; tg < ntile; ++tg) {
 #pragma unroll
-                            for (int kb = 0; kb < 2; ++kb)
-                                mma_f16(tmem, smem_desc(sh + 2 * kb * kPlane, kPlane, 128),
-                                        smem_desc(w + 2 * kb * kFcHidden * 16, kFcHidden * 16, 128),
-                                        idesc_f32acc(kRows, kFcHidden, FMT), kb);
+                                for (int kb = 0; kb < 2; ++kb)
+                                    mma_f16(tmem + (uint32_t)(tg * 128),
+                                            smem_desc(sh + tg * kRows * 16 + 2 * kb * kPlane, kPlane, 128),
+                                            smem_desc(w + 2 * kb * kFcHidden * 16, kFcHidden * 16, 128),
+                                            idesc_f32acc(kRows, kFcHidden, FMT), kb);
+                            }
                         } else {   // Out^T [128 lanes x n6] = W6^T (A) x H^T (B = H, K-major)
                             const uint32_t w = img + fc_img_off(5);
 #pragma unroll
@@ -200,66 +214,79 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
                     if (__syncthreads_or(!ok)) { failed = true; break; }
                     tc_fence_after();
                     if (l < 5) {
-                        float v[32];
-                        tmem_ld16(dcol, *reinterpret_cast<float(*)[16]>(v));
-                        tmem_ld16(dcol + 16, *reinterpret_cast<float(*)[16]>(v + 16));
-                        const float *b = sbias + l * kFcHidden;
+                        if (active) {
+                            float v[32];
+                            tmem_ld16(dcol, *reinterpret_cast<float(*)[16]>(v));
+                            tmem_ld16(dcol + 16, *reinterpret_cast<float(*)[16]>(v + 16));
+                            const float *b = sbias + l * kFcHidden;
 #pragma unroll
-                        for (int o = 0; o < kFcHidden; ++o) v[o] = leaky(v[o] + b[o]);
+                            for (int o = 0; o < kFcHidden; ++o) v[o] = leaky(v[o] + b[o]);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            *reinterpret_cast<uint4 *>(hrow + k * kPlane) = pack8<FT>(v + 8 * k);
+                            for (int k = 0; k < 4; ++k)
+                                *reinterpret_cast<uint4 *>(hrow + k * kPlane) = pack8<FT>(v + 8 * k);
+                        }
                         fence_proxy_async_smem();
                         tc_fence_before();
                         __syncthreads();
                         continue;
                     }
-                    // output layer: this thread adds its bin over the pass's tracks in order,
-                    // 32 at a time, flushing slice s's running sum when its segment ends
-                    float acc = 0.0f;
-                    int s = entry_slice<EDGE>(ssorted[c0], sslice);
-                    int send = sseg[s + 1] - c0;               // first pass row past slice s
+                    // output layer: warpgroup g adds its bin over pass rows [cb, ce) in order
+                    const int half = min(nrow, kRows);
+                    const int cb = g == 0 ? 0 : half, ce = g == 0 ? min(half, nrow) : nrow;
+                    float acc = 0.0f, held = 0.0f;
+                    int held_s = -1;
+                    if (cb < ce) {
+                        int s = entry_slice<EDGE>(ssorted[c0 + cb], sslice);
+                        int send = sseg[s + 1] - c0;           // first pass row past slice s
+                        bool hold = NT == 256 && g == 1;       // warpgroup 1 holds its first segment
 #pragma unroll 1
-                    for (int col = 0; col < nrow; col += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_field + (uint32_t)col, v);
+                        for (int col = cb; col < ce; col += 32) {
+                            float v[32];
+                            tmem_ld32(tmem + lane_field + (uint32_t)col, v);
 #pragma unroll
-                        for (int t = 0; t < 32; ++t) v[t] = softplus_tc(v[t] + b6);
-                        if (col + 32 <= min(nrow, send)) {     // one slice throughout
+                            for (int t = 0; t < 32; ++t) v[t] = softplus_tc(v[t] + b6);
+                            if (col + 32 <= min(ce, send)) {   // one slice throughout
 #pragma unroll
-                            for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, v[t]);
-                            continue;
-                        }
-                        // several segments in this chunk: one branch-free masked pass per
-                        // segment, in row order (adding zeros leaves the sum bit-identical,
-                        // and the loop body stays small enough for the instruction cache;
-                        // an unrolled loop with a flush per segment end measured slower)
-                        const int cnt = min(32, nrow - col);
-                        int t0 = 0;
-#pragma unroll 1
-                        while (t0 < cnt) {
-                            const int t1 = min(cnt, send - col);
-                            const uint32_t hi = t1 >= 32 ? 0xFFFFFFFFu : ((1u << t1) - 1u);
-                            const uint32_t msk = hi & ~((1u << t0) - 1u);
-#pragma unroll
-                            for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, ((msk >> t) & 1u) ? v[t] : 0.0f);
-                            if (t1 < cnt) {                    // slice s ends at row col + t1
-                                if (o_bin >= 0) {
-                                    float *hp = shist + s * kSliceBins + o_bin;
-                                    *hp = __fadd_rn(*hp, acc);
-                                }
-                                acc = 0.0f;
-                                s = entry_slice<EDGE>(ssorted[c0 + col + t1], sslice);
-                                send = sseg[s + 1] - c0;
+                                for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, v[t]);
+                                continue;
                             }
-                            t0 = t1;
+                            // several segments in this chunk: one branch-free masked pass per
+                            // segment, in row order (adding zeros leaves the sum bit-identical,
+                            // and the loop body stays small enough for the instruction cache)
+                            const int cnt = min(32, ce - col);
+                            int t0 = 0;
+#pragma unroll 1
+                            while (t0 < cnt) {
+                                const int t1 = min(cnt, send - col);
+                                const uint32_t hi = t1 >= 32 ? 0xFFFFFFFFu : ((1u << t1) - 1u);
+                                const uint32_t msk = hi & ~((1u << t0) - 1u);
+#pragma unroll
+                                for (int t = 0; t < 32; ++t) acc = __fadd_rn(acc, ((msk >> t) & 1u) ? v[t] : 0.0f);
+                                if (t1 < cnt) {                // slice s ends at row col + t1
+                                    if (hold) { held = acc; held_s = s; hold = false; }
+                                    else if (o_bin >= 0) {
+                                        float *hp = shist + s * kSliceBins + o_bin;
+                                        *hp = __fadd_rn(*hp, acc);
+                                    }
+                                    acc = 0.0f;
+                                    s = entry_slice<EDGE>(ssorted[c0 + col + t1], sslice);
+                                    send = sseg[s + 1] - c0;
+                                }
+                                t0 = t1;
+                            }
                         }
-                    }
-                    if (o_bin >= 0) {   // the pass's last segment (its slice may continue next pass)
-                        float *hp = shist + s * kSliceBins + o_bin;
-                        *hp = __fadd_rn(*hp, acc);
+                        if (hold) { held = acc; held_s = s; }
+                        else if (o_bin >= 0) {
+                            float *hp = shist + s * kSliceBins + o_bin;
+                            *hp = __fadd_rn(*hp, acc);
+                        }
                     }
                     tc_fence_before();
+                    __syncthreads();
+                    if (held_s >= 0 && o_bin >= 0) {
+                        float *hp = shist + held_s * kSliceBins + o_bin;
+                        *hp = __fadd_rn(*hp, held);
+                    }
                     __syncthreads();
                 }
             }
@@ -277,7 +304,18 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
         if (a.iv) enc1_pool<T, kT, true, kC0, true>(a, e, tid, shist, senc);
         else if (a.c0 == kC0Max) enc1_pool<T, kT, false, kC0Max>(a, e, tid, shist, senc);   // the wide network
         else enc1_pool<T, kT>(a, e, tid, shist, senc);
-        if (tid == 0) *snext = a.ev_ctr ? (int)gridDim.x + atomicAdd(a.ev_ctr, 1) : e + (int)gridDim.x;
+        if (tid == 0) {
+            int next = e + (int)gridDim.x;
+            if (a.ev_ctr) {
+                // one ticket per processed event: the ticket n_ev - 1 is the launch's last,
+                // and its taker resets the counter for the next launch (CTAs without an
+                // event never touch it)
+                const int k = atomicAdd(a.ev_ctr, 1);
+                if (k == n_ev - 1) atomicExch(a.ev_ctr, 0);
+                next = (int)gridDim.x + k;
+            }
+            *snext = next;
+        }
         __syncthreads();                   // shist and the sort arrays are reused next event
         e = *snext;
     }
@@ -291,39 +329,49 @@ __global__ void __launch_bounds__(kT, 4) k_front_tc(FrontArgs a) {
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
-    if (a.ev_ctr && tid == 0) {   // the last CTA to finish resets the tickets for the next launch
-        __threadfence();
-        if (atomicAdd(a.ev_ctr + 1, 1) == (int)gridDim.x - 1) {
-            atomicExch(a.ev_ctr, 0);
-            atomicExch(a.ev_ctr + 1, 0);
-        }
-    }
 }
 
 }  // namespace
 
-// Persistent grid: the schedule's CTAs per SM (0 = 4, which fill the SM's 512 TMEM
-// columns), as shared memory allows, each walking events.
-template <int PREC, bool EDGE>
-cudaError_t launch_front_tc_k(const FrontArgs &a, cudaStream_t s) {
-    const size_t smem = TcSmem::total(a.max_tracks, a.edge);
+template <int PREC, bool EDGE, int NT>
+cudaError_t launch_front_tc_k(const FrontArgs &a, int per_sm, cudaStream_t s) {
+    // persistent grid: up to per_sm CTAs per SM, as shared memory allows (NT TMEM columns
+    // each: 512 / NT CTAs fill an SM's 512 columns), each walking events
+    const size_t smem = TcSmem<NT>::total(a.max_tracks, a.edge);
     int sms = 0;
     cudaError_t err = current_device_sms(&sms);
-    if (err == cudaSuccess) err = prepare_kernel((const void *)k_front_tc<PREC, EDGE>, smem, nullptr);
+    if (err == cudaSuccess) err = prepare_kernel((const void *)k_front_tc<PREC, EDGE, NT>, smem, nullptr);
     if (err != cudaSuccess) return err;
-    int per_sm = (int)((228 * 1024) / (smem + 1024));
-    if (per_sm > 4) per_sm = 4;
-    if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
+    const int fit = (int)((228 * 1024) / (smem + 1024));
+    if (per_sm > fit) per_sm = fit;
     if (per_sm < 1) per_sm = 1;
     int grid = sms * per_sm;
     if (grid > a.n_events) grid = a.n_events;
-    k_front_tc<PREC, EDGE><<<grid, kT, smem, s>>>(a);
+    k_front_tc<PREC, EDGE, NT><<<grid, NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// CTAs per SM (the schedule's value): 1 or 2 run the two-warpgroup shape, 3 or 4 (and
+// larger values, clamped) the one-warpgroup shape. 0: a launch of at most four events per
+// SM (a serving batch) takes two 256-thread CTAs per SM, which halve each event's latency;
+// a larger one four 128-thread CTAs per SM, which process more events at once. The
+// shapes give bit-identical results.
+template <int PREC, bool EDGE>
+cudaError_t launch_front_tc_e(const FrontArgs &a, cudaStream_t s) {
+    int per_sm = a.ctas_per_sm;
+    if (per_sm <= 0) {
+        int sms = 0;
+        const cudaError_t err = current_device_sms(&sms);
+        if (err != cudaSuccess) return err;
+        per_sm = a.n_events <= 4 * sms ? 2 : 4;
+    }
+    if (per_sm <= 2) return launch_front_tc_k<PREC, EDGE, 256>(a, per_sm, s);
+    return launch_front_tc_k<PREC, EDGE, 128>(a, per_sm > 4 ? 4 : per_sm, s);
 }
 
 template <int PREC>
 cudaError_t launch_front_tc_t(const FrontArgs &a, cudaStream_t s) {
-    return a.edge > 0.0f ? launch_front_tc_k<PREC, true>(a, s) : launch_front_tc_k<PREC, false>(a, s);
+    return a.edge > 0.0f ? launch_front_tc_e<PREC, true>(a, s) : launch_front_tc_e<PREC, false>(a, s);
 }
 
 cudaError_t launch_front_tc(const FrontArgs &a, int precision, cudaStream_t s) {

@@ -224,7 +224,7 @@ void slot_elems(int L0, int c0, int seqs, size_t *big, size_t *small) {
 }
 
 constexpr int kMaxIvChunk = 65535 / kSlices;
-// Byte offsets, inside the 256-byte status block, of the front's event tickets and of the
+// Byte offsets, inside the 256-byte status block, of the front's event ticket and of the
 // device copy of a dynamic event count (status word at 0, calibration maxima at 64, tile
 // schedulers at 128..176).
 constexpr size_t kFrontCtrOff = 176;

@@ -211,8 +211,8 @@ struct FrontArgs {
     int32_t *n_dyn_copy;         // with n_dyn: pool word that receives *n_dyn, which the
                                  // later kernels of the call read from device memory
     int32_t ctas_per_sm;         // launch schedule: 0 = as many as fit
-    int32_t *ev_ctr;             // tensor-core front: two pool words, zero between launches
-                                 // (next-event ticket, finished CTAs); null: static stride
+    int32_t *ev_ctr;             // tensor-core front: the next-event ticket, a pool word
+                                 // that is zero between launches; null: static stride
 };
 
 struct TailArgs {

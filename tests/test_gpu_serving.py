@@ -68,12 +68,14 @@ def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, pr
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_launch_schedule_changes_nothing_but_the_grids(PVFinder, weights, precision):
     """Every kernel walks its work whatever its grid, and no sum depends on which CTA takes
-    which event or tile: results are bit for bit the same under any launch schedule."""
+    which event or tile: results are bit for bit the same under any launch schedule,
+    including both shapes of the front (256-thread CTAs at 1-2 per SM, 128-thread CTAs at
+    3-4), which split every bin's sum at the same multiples of 128 sorted tracks."""
     b = synth.generate_uneven(96, 17)
     feats, offs = to_cuda(b)
     outs = []
     for sched in (None, {"front": 1, "enc2": 2, "enc3": 1, "dec2_up1": 1, "dec1_final": 2, "tail": 1},
-                  {"front": 2, "enc2": 99, "dec1_final": 3, "tail": 4}):
+                  {"front": 2, "enc2": 99, "dec1_final": 3, "tail": 4}, {"front": 3}, {"front": 4}):
         pv = PVFinder(weights, precision=precision, max_events=96, max_pv_per_event=96, schedule=sched)
         hist = torch.zeros((96, 4000), device="cuda")
         logit = torch.zeros((96, 4000), device="cuda")
