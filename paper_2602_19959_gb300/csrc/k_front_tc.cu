@@ -47,7 +47,7 @@ template <int NT> struct TcSmem {
     static constexpr size_t cnt = hist + sizeof(float) * kBins;
     static constexpr size_t seg = cnt + sizeof(int) * 48;
     static constexpr size_t run = seg + sizeof(int) * 48;
-    static constexpr size_t bar = (run + sizeof(int) * 48 + 15) / 16 * 16;   // mbarrier + slot + flag
+    static constexpr size_t bar = (run + sizeof(int) * 48 + 15) / 16 * 16;   // mbarrier, TMEM slot, flag, next event
     static constexpr size_t sorted = bar + 32;
     __host__ __device__ static size_t slices(int ne) { return sorted + 2 * (size_t)((ne + 7) / 8 * 8); }
     __host__ __device__ static size_t total(int mt, float edge) {
