@@ -32,7 +32,7 @@ __device__ __forceinline__ void store_row16(void *base, int64_t e, int64_t rows_
         *reinterpret_cast<uint4 *>(cb + planar_off(e, 1, 2, rows_e, row)) = pack8<T>(v + 8);
     } else {
         uint4 pk;
-        pack_e4m3<16>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
+        pack_e4m3<16>(v, inv_scale, reinterpret_cast<uint32_t *>(&pk));
         unsigned char *cb = reinterpret_cast<unsigned char *>(base);
         *reinterpret_cast<uint4 *>(cb + planar_off(e, 0, 1, rows_e, row)) = pk;
     }
@@ -49,7 +49,7 @@ __device__ __forceinline__ void store_seg16_pm(void *base, int64_t e, int64_t ro
         *reinterpret_cast<uint4 *>(cb + planar_off(e, 2 * g + 1, C0 / 8, rows_e, row)) = pack8<T>(v + 8);
     } else {
         uint4 pk;
-        pack_e4m3<16>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
+        pack_e4m3<16>(v, inv_scale, reinterpret_cast<uint32_t *>(&pk));
         *reinterpret_cast<uint4 *>(cb + planar_off(e, g, C0 / 16, rows_e, row)) = pk;
     }
 }
@@ -194,7 +194,7 @@ __device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_
             pack8<T>(v);
     } else {
         uint2 pk;
-        pack_e4m3<8>(v, inv_scale, reinterpret_cast<unsigned char *>(&pk));
+        pack_e4m3<8>(v, inv_scale, reinterpret_cast<uint32_t *>(&pk));
         *reinterpret_cast<uint2 *>(reinterpret_cast<unsigned char *>(base) + planar_off(e, 0, 1, rows_e, row) + 8 * h) = pk;
     }
 }

@@ -272,7 +272,7 @@ __device__ __forceinline__ void put16(unsigned char *p0, size_t plane_stride, co
         *reinterpret_cast<uint4 *>(p0 + plane_stride) = pack8<T>(v + 8);
     } else {
         uint4 pk;
-        pack_e4m3<16>(v, inv, reinterpret_cast<unsigned char *>(&pk));
+        pack_e4m3<16>(v, inv, reinterpret_cast<uint32_t *>(&pk));
         *reinterpret_cast<uint4 *>(p0) = pk;
     }
 }
@@ -604,7 +604,7 @@ __device__ __forceinline__ bool epi_conv(const TcArgs &a, unsigned char *smem, c
                     tmem_st<8>(a2t + c0 / 2, r);
                 } else {
                     uint32_t r[4];
-                    pack_e4m3<16>(v, a.mid_inv, reinterpret_cast<unsigned char *>(r));
+                    pack_e4m3<16>(v, a.mid_inv, r);
                     tmem_st<4>(a2t + c0 / 4, r);
                 }
             } else if constexpr (C::EPI == EPI_UP) {

@@ -166,17 +166,20 @@ __host__ __device__ __forceinline__ size_t planar_off(int64_t e, int k, int plan
     return ((size_t)(e * planes + k) * (size_t)rows_e + (size_t)row) * 16;
 }
 
-// e4m3 codes of v[0..N) * inv_scale packed into bytes, two per conversion instruction
-// (round to nearest even, saturating to the largest finite value, as __nv_fp8_e4m3(float)).
+// e4m3 codes of v[0..N) * inv_scale packed four to a word (v[4 i] in the low byte of
+// out[i]), two per conversion instruction (round to nearest even, saturating to the
+// largest finite value, as __nv_fp8_e4m3(float)).
 template <int N>
-__device__ __forceinline__ void pack_e4m3(const float *v, float inv_scale, unsigned char *out) {
-    static_assert(N % 2 == 0, "pairs");
+__device__ __forceinline__ void pack_e4m3(const float *v, float inv_scale, uint32_t *out) {
+    static_assert(N % 4 == 0, "whole words");
 #pragma unroll
-    for (int i = 0; i < N; i += 2) {
-        const __nv_fp8x2_storage_t pk =
+    for (int i = 0; i < N; i += 4) {
+        const __nv_fp8x2_storage_t lo =
             __nv_cvt_float2_to_fp8x2(make_float2(v[i] * inv_scale, v[i + 1] * inv_scale), __NV_SATFINITE, __NV_E4M3);
-        out[i] = (unsigned char)(pk & 0xFF);
-        out[i + 1] = (unsigned char)(pk >> 8);
+        const __nv_fp8x2_storage_t hi =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[i + 2] * inv_scale, v[i + 3] * inv_scale), __NV_SATFINITE,
+                                     __NV_E4M3);
+        out[i / 4] = (uint32_t)lo | ((uint32_t)hi << 16);
     }
 }
 

@@ -65,8 +65,8 @@ def test_graph_launch_matches_infer_and_follows_new_inputs(PVFinder, weights, pr
     g.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
-def test_launch_schedule_changes_nothing_but_the_grids(PVFinder, weights, precision):
+@pytest.mark.parametrize("precision,boundary_mm", [("fp32", 0.0), ("bf16", 0.0), ("fp16", 0.0), ("fp16", 0.5)])
+def test_launch_schedule_changes_nothing_but_the_grids(PVFinder, weights, precision, boundary_mm):
     """Every kernel walks its work whatever its grid, and no sum depends on which CTA takes
     which event or tile: results are bit for bit the same under any launch schedule,
     including both shapes of the front (256-thread CTAs at 1-2 per SM, 128-thread CTAs at
@@ -76,7 +76,8 @@ def test_launch_schedule_changes_nothing_but_the_grids(PVFinder, weights, precis
     outs = []
     for sched in (None, {"front": 1, "enc2": 2, "enc3": 1, "dec2_up1": 1, "dec1_final": 2, "tail": 1},
                   {"front": 2, "enc2": 99, "dec1_final": 3, "tail": 4}, {"front": 3}, {"front": 4}):
-        pv = PVFinder(weights, precision=precision, max_events=96, max_pv_per_event=96, schedule=sched)
+        pv = PVFinder(weights, precision=precision, max_events=96, max_pv_per_event=96, schedule=sched,
+                      boundary_mm=boundary_mm)
         hist = torch.zeros((96, 4000), device="cuda")
         logit = torch.zeros((96, 4000), device="cuda")
         z, c = pv.infer(feats, offs, hist=hist, logit=logit)
