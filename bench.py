@@ -687,14 +687,14 @@ def run_serve(args, weights):
     import synth
     from paper_2602_19959_gb300 import build
     build()
-    store = synth.generate_uneven(20000, 55)
+    store = synth.generate_uneven(args.serve_store, 55)
     pv = make_finder(args, weights, args.precision, args.serve_batch, max_pv_per_event=args.max_pv)
     for rate in args.rates:
         r = serve_sample(pv, store, rate, args.serve_seconds_full, 100 + int(rate // 1000),
                          args.serve_batch, args.serve_inflight, copy=args.serve_copy,
                          lead_us=args.serve_lead_us)
         r.update({"metric": "serving latency", "dtype": args.precision,
-                  "workload": "Poisson arrivals over 20000 stored uneven events (cycled)",
+                  "workload": f"Poisson arrivals over {args.serve_store} stored uneven events (cycled)",
                   "pool_bytes": pv.pool_bytes})
         print(json.dumps(r), flush=True)
     pv.close()
@@ -735,6 +735,8 @@ def main():
                     help="serving: admit the next batch only when the running one is predicted "
                          "to end within this many us (0: whenever a slot is free)")
     ap.add_argument("--serve-seconds-full", type=float, default=10.0)
+    ap.add_argument("--serve-store", type=int, default=200000,
+                    help="serve mode: distinct stored events the requests cycle through")
     ap.add_argument("--retune", action="store_true",
                     help="batch mode: run the autotuner even if its table exists")
     ap.add_argument("--tune-out", default=None, help="batch mode: where to write / read the table")
