@@ -214,7 +214,10 @@ def aggregate_value(events_per_rank: int, world: int, steps: int, max_ms: float)
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms around the timed region:
+    the sampler is running (its first sample taken) before the warm-up steps start, and the
+    caller keeps the GPU busy with the same steps for a while after the timed ones, so the
+    samples come from the GPU under this load even when the timed steps last a few ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -236,6 +239,15 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def wait_first(self, timeout_s=5.0):
+        """Returns once nvidia-smi has written its first sample (or after timeout_s)."""
+        t0 = time.perf_counter()
+        while self.proc and time.perf_counter() - t0 < timeout_s:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
@@ -265,7 +277,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "nvidia-smi every 200 ms from before the warm-up steps "
+                                              "through the timed steps and 0.6 s of further steps"}
 
 
 def oracle_cpu_baseline(weights, batch, target_s=10.0, max_events=None, **variant):
@@ -501,20 +514,28 @@ def measure_form(args, weights, batch, precision, feats, offs, feats_h, offs_h, 
     def step_device():
         pv.infer(feats, offs, out=(z, c))
 
+    sampler = ClockSampler(local) if clocks_too else None
+    if sampler:
+        sampler.start()
+        sampler.wait_first()
     for _ in range(args.warmup):
         flush.fill_(1)
         step_device()
     torch.cuda.synchronize()
     status = pv.device_status()
 
-    sampler = ClockSampler(local) if clocks_too else None
-    if sampler:
-        sampler.start()
     # whole steps only (per-kernel events between launches would also stop the kernels'
     # dependent launches from overlapping one kernel's tail with the next one's prologue);
     # then the same steps again with per-kernel events for the breakdown
     dev_ms, wall, _ = time_steps(pv, step_device, flush, args.steps, world, False)
-    clocks = sampler.stop() if sampler else None
+    clocks = None
+    if sampler:
+        t_busy = time.perf_counter()
+        while time.perf_counter() - t_busy < 0.6:     # the same load, untimed, for the sampler
+            flush.fill_(1)
+            step_device()
+            torch.cuda.synchronize()
+        clocks = sampler.stop()
     prof_ms, _, prof = time_steps(pv, step_device, flush, args.steps, world, True)
     e2e_ms = time_e2e_pipelined(pv, feats_h, offs_h, args.events, args.steps, world)
 
