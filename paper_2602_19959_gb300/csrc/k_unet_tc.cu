@@ -799,15 +799,25 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                 for (int j = 0; j < 16; ++j)   // zero padding outside the event or its sequence
                     v[ch][j] = valid && inseq ? leaky(fmaf(v[ch][j], sc[j], bj[j])) : 0.0f;
                 if (a.amax) amax_fold(a.amax, a.amax_out, v[ch], valid && inseq);
-                // the final conv's partial sums over this chunk's channels, in channel order
+                // the final conv's partial sums over this chunk's channels, in channel order:
+                // taps (0, 1) and (2, 3) as packed two-lane FMAs (each lane an fmaf), from
+                // weights stored per channel as (w0, w1, w2, w3), then tap 4
+                float2 g01 = make_float2(g[0], g[1]), g23 = make_float2(g[2], g[3]);
 #pragma unroll
-                for (int tp = 0; tp < 5; ++tp) {
+                for (int j = 0; j < 16; ++j) {
+                    const float4 w4 = reinterpret_cast<const float4 *>(sfin)[16 * ch + j];
+                    const float2 vv = make_float2(v[ch][j], v[ch][j]);
+                    g01 = __ffma2_rn(make_float2(w4.x, w4.y), vv, g01);
+                    g23 = __ffma2_rn(make_float2(w4.z, w4.w), vv, g23);
+                }
+                g[0] = g01.x; g[1] = g01.y; g[2] = g23.x; g[3] = g23.y;
+                {
                     float wf[16];
-                    lds16(sfin + tp * C::COUT + 16 * ch, wf);
-                    float acc = g[tp];
+                    lds16(sfin + 4 * C::COUT + 16 * ch, wf);
+                    float acc = g[4];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) acc = fmaf(wf[j], v[ch][j], acc);
-                    g[tp] = acc;
+                    g[4] = acc;
                 }
             }
             float *sg = reinterpret_cast<float *>(smem + C::OFF_G) + ab * 5 * kTileM;
@@ -890,7 +900,10 @@ __global__ void __launch_bounds__(C::THREADS) __maxnreg__(C::MAXREG) k_conv_tc(T
         else if (k < C::COUT + C::N2) v = a.bias2[(k - C::COUT) % (C::CUP > 0 ? C::CUP : 1)];
         else if (k < 2 * C::COUT + C::N2) v = a.cs ? a.cs[part * C::COUT + k - C::COUT - C::N2] : 1.0f;
         else if (k < 2 * (C::COUT + C::N2)) v = a.cs2 ? a.cs2[k - 2 * C::COUT - C::N2] : 1.0f;
-        else v = a.final_w[k - 2 * (C::COUT + C::N2)];
+        else {   // the final conv: (w0, w1, w2, w3) per channel, then w4 per channel, then b
+            const int f = k - 2 * (C::COUT + C::N2);
+            v = f < 4 * C::COUT ? a.final_w[(f & 3) * C::COUT + (f >> 2)] : a.final_w[f];
+        }
         par[k] = v;
     }
     if (threadIdx.x == 0) {
