@@ -206,14 +206,15 @@ __device__ __forceinline__ void store_half8(void *base, int64_t e, int64_t rows_
 // from shared memory; the two threads of a pair write the two halves of each row.
 // IV: the per-interval layout of the tensor-core forms: e1 and p1 hold the event's kSlices
 // sequences end to end, each the conv of the interval's kIvLen-bin window (its bins with
-// kIvPad zero bins on each side) with its own two zero rows on each side.
+// kIvPad zero bins on each side), two zero rows before each sequence and two after the
+// last (neighbouring sequences share the two between them).
 template <class T, int NT, bool AMAX, bool IV = false>
 __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, const float *shist,
                                             const float *senc) {
     static_assert(NT % 2 == 0, "thread pairs");
-    constexpr int S1 = kIvLen + 2 * kPad, S2 = kIvLen / 2 + 2 * kPad;   // rows per sequence
-    const int64_t rows1 = IV ? (int64_t)kSlices * S1 : padded_rows(kBins);
-    const int64_t rows2 = IV ? (int64_t)kSlices * S2 : padded_rows(kBins / 2);
+    constexpr int S1 = kIvLen + kPad, S2 = kIvLen / 2 + kPad;   // rows per sequence
+    const int64_t rows1 = IV ? (int64_t)kSlices * S1 + kPad : padded_rows(kBins);
+    const int64_t rows2 = IV ? (int64_t)kSlices * S2 + kPad : padded_rows(kBins / 2);
     constexpr int NQ = IV ? kSlices * (kIvLen / 2) : kBins / 2;         // position pairs
     const float inv = a.e1_inv_scale;
     const int h = tid & 1;
@@ -270,11 +271,11 @@ __device__ __forceinline__ void enc1_pool_t(const FrontArgs &a, int e, int tid, 
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if ((tid & 31) == 0) atomicMax(reinterpret_cast<int *>(a.amax), __float_as_int(vmax));
     }
-    if constexpr (IV) {     // each sequence's rows 0, 1 and L + 2, L + 3
-        for (int idx = tid; idx < kSlices * 4; idx += NT) {
-            const int sq = idx >> 2, k = idx & 3;
-            zero_row16<T>(a.e1, e, rows1, (int64_t)sq * S1 + (k < 2 ? k : S1 - 4 + k));
-            zero_row16<T>(a.p1, e, rows2, (int64_t)sq * S2 + (k < 2 ? k : S2 - 4 + k));
+    if constexpr (IV) {     // the two rows before each sequence and the two after the last
+        for (int idx = tid; idx < (kSlices + 1) * 2; idx += NT) {
+            const int sq = idx >> 1, k = idx & 1;
+            zero_row16<T>(a.e1, e, rows1, (int64_t)sq * S1 + k);
+            zero_row16<T>(a.p1, e, rows2, (int64_t)sq * S2 + k);
         }
     } else if (tid < 4) {
         const int r = tid < 2 ? tid : kBins + tid;             // rows 0,1 and L+2, L+3

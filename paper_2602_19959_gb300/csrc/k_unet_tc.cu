@@ -111,14 +111,16 @@ struct Cfg {
     static constexpr int ROWS_E = L + 2 * kPad;              // storage rows per event
     static constexpr bool PAIRED = PAIRED_;                 // taps stacked in pairs along N
     // per-interval layout: the event is kSlices sequences laid end to end, SEQ storage rows
-    // each (its LSEQ positions and two zero rows on each side), so the event's L = kSlices
-    // SEQ - 4 positions include the zero rows between sequences; 0: one sequence of L
+    // each (two zero rows, then its LSEQ positions), and two more zero rows after the last;
+    // neighbouring sequences share the two zero rows between them (the k5 conv's padding on
+    // either side), so the event's L = kSlices SEQ - 2 positions include those rows;
+    // 0: one sequence of L
     static constexpr int SEQ = SEQ_;
-    static constexpr int LSEQ = SEQ ? SEQ - 2 * kPad : L_;
-    static constexpr int SEQP = SEQ ? LSEQ / 2 + 2 * kPad : 0;   // after the 2:1 pool
-    static constexpr int SEQU = SEQ ? 2 * LSEQ + 2 * kPad : 0;   // after the ConvT
-    static constexpr int64_t ROWS_P = SEQ ? (int64_t)kSlices * SEQP : L_ / 2 + 2 * kPad;  // pooled rows per event
-    static constexpr int64_t ROWS_O = SEQ ? (int64_t)kSlices * SEQU : 2 * L_ + 2 * kPad;  // ConvT rows per event
+    static constexpr int LSEQ = SEQ ? SEQ - kPad : L_;
+    static constexpr int SEQP = SEQ ? LSEQ / 2 + kPad : 0;   // after the 2:1 pool
+    static constexpr int SEQU = SEQ ? 2 * LSEQ + kPad : 0;   // after the ConvT
+    static constexpr int64_t ROWS_P = SEQ ? (int64_t)kSlices * SEQP + kPad : L_ / 2 + 2 * kPad;  // pooled rows per event
+    static constexpr int64_t ROWS_O = SEQ ? (int64_t)kSlices * SEQU + kPad : 2 * L_ + 2 * kPad;  // ConvT rows per event
     static constexpr bool DYN = DYN_;                       // tiles from the global counter
     // output rows per tile: row 127 of a paired tile lacks O[128]; the fused final conv
     // also needs two rows on each side
@@ -181,7 +183,7 @@ struct Cfg {
     static_assert(EPI != EPI_CONVT || (COUT % (CUP ? CUP : 1) == 0 && (2 / NSPLIT) * CUP == COUT && !PAIR && CB == 0),
                   "ConvT GEMM: N = the part's r values x CUP");
     // the pool pairs lanes m, m + 1 as positions j, j + 1 of one sequence: even SEQ and LSEQ
-    static_assert(!SEQ || (L == kSlices * SEQ - 2 * kPad &&
+    static_assert(!SEQ || (L == kSlices * SEQ - kPad &&
                            (EPI != EPI_POOL || (SEQ % 2 == 0 && LSEQ % 2 == 0))),
                   "per-interval geometry");
     static_assert(EPI != EPI_UP || CUP % 16 == 0, "16-column epilogue chunks");
@@ -250,7 +252,7 @@ __device__ __forceinline__ void tile_pos(int t, int &e, int &p0) {
 }
 
 // Per-interval layout: position p of the event lies in sequence s at position j of it;
-// j outside [0, LSEQ) is one of the zero rows between sequences. Whole events: s = 0, j = p.
+// j = -2 or -1 is one of the two zero rows before sequence s. Whole events: s = 0, j = p.
 template <class C>
 __device__ __forceinline__ void seq_pos(int p, int &s, int &j) {
     if constexpr (C::SEQ != 0) {
@@ -681,9 +683,9 @@ __device__ __forceinline__ void epi_up(const TcArgs &a, const float *sbias2, con
             zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU);
             zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU + 1);
         }
-        if (pads && valid && jq == C::LSEQ - 1) {
-            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 2);
-            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)sq * C::SEQU + C::SEQU - 1);
+        if (pads && valid && jq == C::LSEQ - 1 && sq == kSlices - 1) {   // the event's last two rows
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)kSlices * C::SEQU);
+            zero_planes(a.out, e, 0, PUP, PUP, ROWS_O, (int64_t)kSlices * C::SEQU + 1);
         }
     } else {
         if (pads && p == 0) {
@@ -868,8 +870,9 @@ __device__ bool epilogue(const TcArgs &a, unsigned char *smem, uint64_t *bar, ui
                 }
             }
             if constexpr (C::EPI == EPI_POOL && C::SEQ != 0) {   // each pooled sequence's zero rows
-                if (wg == 0 && valid && (jq == 0 || jq == C::LSEQ - 2)) {
-                    const int64_t rp = (int64_t)sq * C::SEQP + (jq == 0 ? 0 : C::SEQP - 2);
+                // (the two before it; after the last sequence also the event's last two)
+                if (wg == 0 && valid && (jq == 0 || (jq == C::LSEQ - 2 && sq == kSlices - 1))) {
+                    const int64_t rp = jq == 0 ? (int64_t)sq * C::SEQP : (int64_t)kSlices * C::SEQP;
                     zero_planes(a.outp, e, 0, C::POUT, C::POUT, ROWS_P, rp);
                     zero_planes(a.outp, e, 0, C::POUT, C::POUT, ROWS_P, rp + 1);
                 }
@@ -1038,10 +1041,10 @@ template <int PREC> struct Net {
 // 104 positions): the same kernels over each event's 40 sequences laid end to end, with
 // levels of 104, 52, 26 and 13 positions per sequence (108, 56, 30 and 17 storage rows).
 template <int PREC> struct NetIv {
-    static constexpr int S0 = kIvLen + 2 * kPad, S1 = kIvLen / 2 + 2 * kPad, S2 = kIvLen / 4 + 2 * kPad,
-                         S3 = kIvLen / 8 + 2 * kPad;
-    static constexpr int L0 = kSlices * S0 - 2 * kPad, L1 = kSlices * S1 - 2 * kPad, L2 = kSlices * S2 - 2 * kPad,
-                         L3 = kSlices * S3 - 2 * kPad;
+    static constexpr int S0 = kIvLen + kPad, S1 = kIvLen / 2 + kPad, S2 = kIvLen / 4 + kPad,
+                         S3 = kIvLen / 8 + kPad;
+    static constexpr int L0 = kSlices * S0 - kPad, L1 = kSlices * S1 - kPad, L2 = kSlices * S2 - kPad,
+                         L3 = kSlices * S3 - kPad;
     using Enc2 = Cfg<PREC, 16, 0, 32, L1, EPI_POOL, 0, 4, 1, 56, 2, false, true, false, S1>;
     using Enc3 = Cfg<PREC, 32, 0, 64, L2, EPI_POOL, 0, 4, 1, 80, 2, false, true, false, S2>;
     using Enc4Up3 = Cfg<PREC, 64, 0, 128, L3, EPI_UP, 64, is16(PREC) ? 2 : 4, is16(PREC) ? 2 : 4, 96, 3, false,
