@@ -130,3 +130,27 @@ def test_per_interval_deterministic_and_batch_invariant(PVFinder, weights, ev16,
     rs = run_full(pv, ev16.subset(5, 9))
     for k in ("hist", "logit", "count"):
         np.testing.assert_array_equal(rs[k], r1[k][5:9])
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_per_interval_chunked_dirty_pool_and_front_shapes(PVFinder, weights, precision):
+    """Every zero row of the layout (between sequences, at both event ends, in e1, p1, the
+    pooled and the upsampled tensors) is written each time: 48 uneven events in chunks of
+    7 (a partial last chunk), on a pool first filled by another batch, under both front
+    shapes, give bit for bit the results of one unchunked launch on a fresh pool."""
+    b = synth.generate_uneven(48, 13)
+    other = synth.generate_uneven(48, 21)
+    pv = PVFinder(weights, precision=precision, max_events=48, max_pv_per_event=MAX_PV, per_interval=True)
+    want = run_full(pv, b)
+    pv.close()
+    for sched in ({"front": 2}, {"front": 4}):
+        pc = PVFinder(weights, precision=precision, max_events=48, chunk_events=7, max_pv_per_event=MAX_PV,
+                      per_interval=True, schedule=sched)
+        run_full(pc, other)                      # leaves other events' activations in every slot
+        got = run_full(pc, b)
+        pc.close()
+        for k in ("hist", "logit", "count"):
+            np.testing.assert_array_equal(got[k], want[k])
+        for e in range(48):
+            k = min(int(want["count"][e]), MAX_PV)
+            np.testing.assert_array_equal(got["z"][e, :k], want["z"][e, :k])
