@@ -119,3 +119,22 @@ def test_wide_deterministic_and_batch_invariant(PVFinder, wide_weights, ev8, fp8
     rs = run_full(pv, ev8.subset(2, 6))
     for k in ("hist", "logit", "count"):
         np.testing.assert_array_equal(rs[k], r1[k][2:6])
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_wide_chunked_on_a_dirty_pool_equals_one_launch(PVFinder, wide_weights, precision):
+    """The wide network's split layers and ConvT GEMM kernels write every row they own
+    (the zero rows at both event ends included) each time: 24 uneven events in chunks of
+    5, on a pool first filled by another batch, give bit for bit the results of one
+    launch on a fresh pool."""
+    b = synth.generate_uneven(24, 13)
+    other = synth.generate_uneven(24, 21)
+    pv = PVFinder(wide_weights, precision=precision, max_events=24, max_pv_per_event=MAX_PV)
+    want = run_full(pv, b)
+    pv.close()
+    pc = PVFinder(wide_weights, precision=precision, max_events=24, chunk_events=5, max_pv_per_event=MAX_PV)
+    run_full(pc, other)
+    got = run_full(pc, b)
+    pc.close()
+    for k in ("hist", "logit", "count"):
+        np.testing.assert_array_equal(got[k], want[k])
